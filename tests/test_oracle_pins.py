@@ -1,0 +1,439 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: lattice
+identities, closed forms, conservation laws, an independent brute-force
+stream-collide on a tiny lattice, limits of the lubrication functions,
+frame indifference, Onsager reciprocity and the protocol of Eq. 16.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+C, W, OPP = O.lattice()
+CF = C.astype(np.float64)
+
+
+# ---------------------------------------------------------------- lattice
+def test_d3q19_weights_and_isotropy():
+    """Appendix A: C^q = 1/3, 1/18, 1/36; c_s^2 = 1/3; 4th-order isotropy."""
+    assert len({tuple(c) for c in C}) == 19
+    assert math.isclose(W.sum(), 1.0, abs_tol=1e-15)
+    assert W[0] == pytest.approx(1 / 3)
+    assert sorted(set(np.round(W, 12))) == sorted({round(1 / 3, 12), round(1 / 18, 12),
+                                                   round(1 / 36, 12)})
+    np.testing.assert_allclose(W @ CF, 0, atol=1e-16)
+    second = np.einsum("q,qa,qb->ab", W, CF, CF)
+    np.testing.assert_allclose(second, np.eye(3) / 3, atol=1e-15)
+    fourth = np.einsum("q,qa,qb,qc,qd->abcd", W, CF, CF, CF, CF)
+    d = np.eye(3)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9
+    np.testing.assert_allclose(fourth, iso, atol=1e-15)
+    for q in range(19):
+        np.testing.assert_array_equal(C[OPP[q]], -C[q])
+
+
+def test_equilibrium_moments():
+    """Eq. 4 moments of n^eq: rho, j and rho c_s^2 delta + j j / rho."""
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        rho = 0.8 + 0.4 * rng.random()
+        j = 0.05 * rng.standard_normal(3)
+        f = O.equilibrium(rho, j)
+        assert f.sum() == pytest.approx(rho, rel=1e-14)
+        np.testing.assert_allclose(f @ CF, j, atol=1e-15)
+        pi = np.einsum("q,qa,qb->ab", f, CF, CF)
+        np.testing.assert_allclose(pi, rho / 3 * np.eye(3) + np.outer(j, j) / rho, atol=1e-14)
+
+
+# --------------------------------------------------------- fluid, periodic
+def _numpy_bgk_periodic(f, tau, steps):
+    """Independent brute force: np.roll streaming + BGK, all periodic."""
+    f = f.copy()
+    for _ in range(steps):
+        g = np.empty_like(f)
+        for q in range(19):
+            # pull: n_q(r) = n*_q(r - c_q); axes of f are (q, z, y, x)
+            g[q] = np.roll(f[q], shift=(C[q][2], C[q][1], C[q][0]), axis=(0, 1, 2))
+        rho = g.sum(0)
+        j = np.einsum("qa,qzyx->azyx", CF, g)
+        jc = np.einsum("qa,azyx->qzyx", CF, j)
+        jj = (j * j).sum(0)
+        feq = W[:, None, None, None] * (rho + 3 * jc + 4.5 * jc ** 2 / rho - 1.5 * jj / rho)
+        f = g - (g - feq) / tau
+    return f
+
+
+def test_stream_collide_matches_brute_force_periodic():
+    """With zero shear the Lees-Edwards planes reduce to plain periodicity."""
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(2)
+    f0 = W[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19, nz, ny, nx)))
+    s = O.Oracle(nx, ny, nz, tau=0.7)
+    s.set_populations(f0)
+    s.step(3, O.shear(0, rate=0.0))
+    np.testing.assert_allclose(s.populations(), _numpy_bgk_periodic(f0, 0.7, 3),
+                               rtol=0, atol=1e-15)
+
+
+def test_mass_momentum_conserved_periodic():
+    nx, ny, nz = 8, 8, 8
+    rng = np.random.default_rng(3)
+    f0 = W[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19, nz, ny, nx)))
+    s = O.Oracle(nx, ny, nz, tau=0.6)
+    s.set_populations(f0)
+    s.step(20)
+    f = s.populations()
+    assert abs(f.sum() - f0.sum()) < 1e-13 * f0.sum()
+    np.testing.assert_allclose(np.einsum("qa,qzyx->a", CF, f),
+                               np.einsum("qa,qzyx->a", CF, f0), atol=1e-13)
+
+
+def test_lees_edwards_conserves_mass():
+    """Interpolation weights sum to one and the Galilean correction is mass
+    neutral over a plane, so total mass is exact with a fractional offset."""
+    nx, ny, nz = 10, 8, 4
+    rng = np.random.default_rng(4)
+    f0 = W[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19, nz, ny, nx)))
+    s = O.Oracle(nx, ny, nz, tau=0.9)
+    s.set_populations(f0)
+    s.step(37, O.shear(0, rate=3.7e-3))
+    assert 0 < s.delta < nx and abs(s.delta - (37 * 3.7e-3 * ny) % nx) < 1e-12
+    assert abs(s.populations().sum() - f0.sum()) < 1e-12 * f0.sum()
+
+
+def _couette_state(nx, ny, nz, tau, rate, rho0=1.0):
+    """Linear profile u_x = rate (y - y0) plus its first-order non-equilibrium
+    part -tau C^q 3 rho c_x c_y rate, stored post-collision."""
+    y0 = (ny - 1) / 2
+    f = np.zeros((19, nz, ny, nx))
+    neq = -tau * W * 3 * rho0 * C[:, 0] * C[:, 1] * rate
+    for y in range(ny):
+        feq = O.equilibrium(rho0, [rho0 * rate * (y - y0), 0, 0])
+        f[:, :, y, :] = (feq + (1 - 1 / tau) * neq)[:, None, None]
+    return f
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_couette_fixed_point_and_viscous_stress(tau):
+    """P3: under Lees-Edwards shear the linear profile's rho and j are kept to
+    round-off for every cell, across the shifted planes, and the viscous
+    stress equals eta0 * rate with eta0 = rho0 (tau - 1/2) / 3."""
+    nx, ny, nz, rate = 8, 16, 4, 2e-3
+    f0 = _couette_state(nx, ny, nz, tau, rate)
+    s = O.Oracle(nx, ny, nz, tau=tau)
+    s.set_populations(f0)
+    s.step(60, O.shear(0, rate=rate))
+    f = s.populations()
+    np.testing.assert_allclose(f.sum(0), f0.sum(0), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(np.einsum("qa,qzyx->azyx", CF, f),
+                               np.einsum("qa,qzyx->azyx", CF, f0), rtol=0, atol=1e-13)
+    sig, _ = s.stress(O.VISCOUS)
+    eta0 = (tau - 0.5) / 3
+    assert sig[0, 1] == pytest.approx(eta0 * rate, rel=1e-12)
+    assert sig[1, 0] == pytest.approx(eta0 * rate, rel=1e-12)
+
+
+def test_couette_develops_from_rest():
+    """Started at rest, the Lees-Edwards boundary drives the linear profile
+    (diffusive time Ly^2 / nu); slope -> rate, sign pinned by the image
+    velocity convention."""
+    nx, ny, nz, rate = 4, 12, 4, 1e-3
+    s = O.Oracle(nx, ny, nz, tau=1.0)
+    s.step(6000, O.shear(0, rate=rate))
+    f = s.populations()
+    ux = (np.einsum("q,qzyx->zyx", CF[:, 0], f) / f.sum(0)).mean(axis=(0, 2))
+    slope = np.polyfit(np.arange(ny), ux, 1)[0]
+    assert slope == pytest.approx(rate, rel=1e-3)
+    assert np.abs(ux - np.polyval(np.polyfit(np.arange(ny), ux, 1), np.arange(ny))).max() < 1e-3 * rate * ny
+
+
+# ----------------------------------------------------------- bounce-back
+def test_rest_state_with_held_sphere_is_exact():
+    """A sphere at rest in fluid at rest: bounce-back of the rest state is the
+    rest state (Eq. 7 with u_b = 0); no force, populations unchanged."""
+    s = O.Oracle(16, 16, 16, radius=[4.0], pos=[[8.2, 7.9, 8.1]], move_particles=False)
+    s.step(5)
+    own = s.owner()
+    f = s.populations()
+    fluid = own < 0
+    np.testing.assert_allclose(f[:, fluid], np.broadcast_to(W[:, None], f[:, fluid].shape),
+                               atol=1e-16)
+    F, T = s.hydro()
+    np.testing.assert_allclose(F, 0, atol=1e-14)
+    np.testing.assert_allclose(T, 0, atol=1e-14)
+    assert (~fluid).sum() == pytest.approx(4 / 3 * math.pi * (0.95 * 4) ** 3, rel=0.15)
+
+
+def test_moving_sphere_feels_drag_and_drives_fluid():
+    """Eq. 7/8 sign: a sphere held at velocity U in fluid at rest receives a
+    force against U and gives the fluid momentum along U; a sphere held at
+    spin Omega receives a torque against Omega."""
+    U = np.array([[0.01, -0.004, 0.002]])
+    s = O.Oracle(20, 20, 20, radius=[4.0], pos=[[10.0, 10.0, 10.0]], vel=U,
+                 move_particles=False)
+    s.step(20)
+    F, _ = s.hydro()
+    assert (F[0] @ U[0]) < 0
+    f = s.populations()
+    fluid = s.owner() < 0
+    jf = np.einsum("qa,qn->a", CF, f[:, fluid])
+    assert jf @ U[0] > 0
+    Om = np.array([[0.0, 0.0, 0.003]])
+    s2 = O.Oracle(20, 20, 20, radius=[4.0], pos=[[10.0, 10.0, 10.0]], omega=Om,
+                  move_particles=False)
+    s2.step(20)
+    _, T = s2.hydro()
+    assert T[0, 2] < 0 and abs(T[0, 0]) < 1e-3 * abs(T[0, 2])
+
+
+def test_momentum_conserved_with_moving_particles():
+    """P1: fluid + particle momentum + pending covering impulses is constant
+    to round-off while spheres move, cover and uncover nodes and touch."""
+    rad = [3.0, 3.0, 3.5]
+    pos = [[6.0, 8.0, 8.0], [12.4, 8.5, 8.3], [9.0, 14.0, 4.0]]
+    vel = [[0.02, 0.0, 0.0], [-0.02, 0.003, 0.0], [0.0, -0.01, 0.01]]
+    s = O.Oracle(20, 18, 16, radius=rad, pos=pos, vel=vel, kn=50.0, F0=0.05, debye=0.2,
+                 lub_cut=0.5, lub_delta=0.03)
+    m = np.array([4 / 3 * math.pi * a ** 3 for a in rad])
+
+    def total():
+        f = s.populations()
+        fluid = s.owner() < 0
+        jf = np.einsum("qa,qn->a", CF, f[:, fluid])
+        _, U, _ = s.particles()
+        Fp, _ = s.pending()
+        return jf + (m[:, None] * U).sum(0) + Fp.sum(0)
+
+    p0 = total()
+    nsteps = 0
+    for _ in range(6):
+        s.step(10)
+        nsteps += 10
+        np.testing.assert_allclose(total(), p0, rtol=0, atol=1e-12)
+    assert s.error() == 0
+
+
+# ---------------------------------------------------------------- contacts
+def test_normal_contact_closed_form():
+    """Linear spring + dashpot: F = (kn delta_n + eta_n v_n), repulsive,
+    equal and opposite, no torque for a central approach."""
+    kn, eta = 200.0, 7.0
+    d = np.array([7.9, 0.0, 0.0])
+    u = np.array([0.01, 0.0, 0.0])             # a approaching b
+    t, Fa, Ta, Tb, fn, Ft, ht = O.contact(4.0, 4.0, d, u, [0, 0, 0], [0, 0, 0], kn, 0.2 * kn,
+                                          eta, 1.0, 1.0, [0, 0, 0])
+    assert t
+    assert fn == pytest.approx(kn * 0.1 + eta * 0.01, rel=1e-13)
+    np.testing.assert_allclose(Fa, [-fn, 0, 0], atol=1e-14)
+    np.testing.assert_allclose(Ta, 0, atol=1e-15)
+    np.testing.assert_allclose(Ft, 0, atol=1e-15)
+    t, *_ = O.contact(4.0, 4.0, [8.01, 0, 0], u, [0, 0, 0], [0, 0, 0], kn, kn, eta, 1.0, 1.0,
+                      [0.3, 0.1, 0.0])
+    assert not t
+
+
+def test_tangential_spring_and_coulomb_slip():
+    """Stick: F_t = -kt * integral of v_t; slip once |F_t| reaches mu |F_n|,
+    then |F_t| = mu |F_n| exactly with the spring reset to the slip length;
+    torque a n x F_t on both spheres (Eq. 11t)."""
+    kn, kt, mu = 100.0, 20.0, 0.5
+    ra, rb = 4.0, 5.0
+    d = np.array([0.0, 8.95, 0.0])              # overlap 0.05, n = +y
+    vt = np.array([0.004, 0.0, 0.0])
+    ht = np.zeros(3)
+    fn_expected = kn * 0.05
+    slipped = False
+    for k in range(1, 200):
+        t, Fa, Ta, Tb, fn, Ft, ht = O.contact(ra, rb, d, vt, [0, 0, 0], [0, 0, 0], kn, kt, 0.0,
+                                              mu, 0.5, ht)
+        assert fn == pytest.approx(fn_expected, rel=1e-13)
+        trial = kt * 0.004 * 0.5 * k
+        if trial < mu * fn:
+            assert Ft[0] == pytest.approx(-trial, rel=1e-12)
+        else:
+            slipped = True
+            assert np.linalg.norm(Ft) == pytest.approx(mu * fn, rel=1e-13)
+            np.testing.assert_allclose(ht, -Ft / kt, rtol=1e-14)
+        assert np.linalg.norm(Ft) <= mu * abs(fn) * (1 + 1e-12)
+        n = d / np.linalg.norm(d)
+        np.testing.assert_allclose(Ta, ra * np.cross(n, Ft), atol=1e-14)
+        np.testing.assert_allclose(Tb, rb * np.cross(n, Ft), atol=1e-14)
+    assert slipped
+
+
+def test_contact_rolling_without_slip_has_no_tangential_force():
+    """Relative surface velocity includes the spins: equal and opposite rolling
+    (U_ab = 0, a Omega_a + b Omega_b = 0) loads no tangential spring."""
+    d = np.array([7.95, 0.0, 0.0])
+    wa = np.array([0.0, 0.0, 0.01])
+    wb = -wa * 4.0 / 4.0
+    t, Fa, Ta, Tb, fn, Ft, ht = O.contact(4.0, 4.0, d, [0, 0, 0], wa, wb, 100.0, 20.0, 0.0,
+                                          1.0, 1.0, [0, 0, 0])
+    assert t
+    np.testing.assert_allclose(Ft, 0, atol=1e-16)
+
+
+# ------------------------------------------------------------- lubrication
+ETA0 = 1.0 / 6.0
+
+
+def test_lubrication_reynolds_limit_equal_spheres():
+    """P7: for equal spheres the squeeze force is (3/2) pi eta a^2 U / h at
+    leading order; with delta = 0 and the cutoff term subtracted the oracle
+    gives (3/2) pi eta a^2 U (1/h - 1/h_c) exactly."""
+    a, h, hc, U = 4.0, 1e-3, 2.0, 0.01
+    d = np.array([0.0, 0.0, 2 * a + h])
+    Fa, Ta, Tb = O.lubrication(a, a, d, [0, 0, U], [0, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    expect = 1.5 * math.pi * ETA0 * a * a * U * (1 / h - 1 / hc)
+    assert -Fa[2] == pytest.approx(expect, rel=1e-12)
+    np.testing.assert_allclose(Fa[:2], 0, atol=1e-16)
+
+
+def test_lubrication_vanishes_at_cutoff_and_beyond():
+    a, b = 4.0, 5.6
+    for h in (0.5, 0.5000001, 0.7):
+        d = np.array([a + b + h, 0.0, 0.0])
+        Fa, Ta, Tb = O.lubrication(a, b, d, [0.01, 0.02, -0.01], [0.001, 0, 0.002],
+                                   [0, 0.003, 0], ETA0, 0.04, 0.5)
+        assert np.abs(Fa).max() < 1e-14 and np.abs(Ta).max() < 1e-13
+
+
+@pytest.mark.parametrize("ra,rb", [(4.0, 4.0), (4.0, 5.6), (5.6, 4.0)])
+def test_lubrication_frame_indifference(ra, rb):
+    """A touching pair rotating rigidly has no relative surface motion: the
+    leading-order tangential force and both torques vanish.  This holds only
+    with beta = a_b / a_a in the printed Y^A, Y^B, Y^C functions."""
+    d = np.array([ra + rb, 0.0, 0.0]) * 1.00001
+    Om = np.array([0.0, 0.002, 0.005])
+    uab = np.cross(Om, -d)                       # U_a - U_b = Om x (R_a - R_b)
+    Fa, Ta, Tb = O.lubrication(ra, rb, d, uab, Om, Om, ETA0, 0.0, 0.5)
+    scale = ETA0 * 6 * math.pi * ra * np.linalg.norm(uab)
+    assert np.abs(Fa).max() < 1e-3 * scale
+    assert np.abs(Ta).max() < 1e-3 * scale * ra
+    assert np.abs(Tb).max() < 1e-3 * scale * rb
+
+
+def _resistance_matrix(ra, rb, d):
+    """12 x 12 map (U_a, U_b, W_a, W_b) -> (F_a, F_b, T_a, T_b) probed column by column."""
+    M = np.zeros((12, 12))
+    for k in range(12):
+        e = np.zeros(12)
+        e[k] = 1.0
+        Ua, Ub, Wa, Wb = e[0:3], e[3:6], e[6:9], e[9:12]
+        Fa, Ta, Tb = O.lubrication(ra, rb, d, Ua - Ub, Wa, Wb, ETA0, 0.04, 0.5)
+        M[:, k] = np.concatenate([Fa, -Fa, Ta, Tb])
+    return M
+
+
+@pytest.mark.parametrize("ra,rb", [(4.0, 4.0), (4.0, 5.6)])
+def test_lubrication_reciprocity_and_dissipation(ra, rb):
+    """Lorentz reciprocity (A_ab = A_ba^T and its B, C analogues, Appendix A):
+    the resistance matrix is symmetric, and it is negative semidefinite."""
+    d = np.array([0.3, -0.2, 1.0])
+    d = d / np.linalg.norm(d) * (ra + rb + 0.1)
+    M = _resistance_matrix(ra, rb, d)
+    np.testing.assert_allclose(M, M.T, atol=1e-12 * np.abs(M).max())
+    ev = np.linalg.eigvalsh(0.5 * (M + M.T))
+    assert ev.max() < 1e-10 * np.abs(ev).max()
+
+
+# --------------------------------------------------------------- protocol
+def test_oscillatory_protocol_eq16():
+    """P9: gamma(2 pi k / omega) = 0, dgamma/dt = omega gamma0 sin(omega t + Theta),
+    and the summed per-step increments return the offset to zero after a cycle."""
+    period = 1000
+    om = 2 * math.pi / period
+    for theta in (0.0, math.pi / 2, 1.1):
+        sh = O.shear(1, gamma0=0.7, omega=om, theta=theta)
+        for k in range(3):
+            assert abs(O.gamma(sh, k * period)) < 1e-12
+        for t in (13.0, 250.5, 777.0):
+            eps = 1e-4
+            num = (O.gamma(sh, t + eps) - O.gamma(sh, t - eps)) / (2 * eps)
+            assert num == pytest.approx(om * 0.7 * math.sin(om * t + theta), rel=1e-6, abs=1e-12)
+        ly = 24.0
+        tot = sum(O.le_increment(sh, t, ly) for t in range(period))
+        assert abs(tot) < 1e-12
+    s = O.Oracle(8, 24, 4, tau=1.0)
+    s.step(period, O.shear(1, gamma0=0.7, omega=om, theta=math.pi / 2))
+    d = s.delta
+    assert min(d, 8 - d) < 1e-9
+
+
+# -------------------------------------------------------- angular stress
+def test_angular_stress_eq26_matches_virial_normal_part():
+    """P8: monodisperse disks, contacts at bin centres with |r| = 2a: Eq. 26's
+    normal part equals the pairwise virial of Eq. 12 per unit area (with the
+    opposite sign convention: Eq. 26 counts compression positive)."""
+    nb, a, N, area = 36, 3.0, 50, 4000.0
+    rng = np.random.default_rng(5)
+    dth = math.pi / nb
+    hist = np.zeros((nb, 3))
+    vir = np.zeros((2, 2))
+    ncont = 0
+    for b in range(nb):
+        for _ in range(int(rng.integers(0, 4))):
+            th = (b + 0.5) * dth
+            F = float(rng.uniform(0.1, 2.0))
+            n = np.array([math.cos(th), math.sin(th)])
+            hist[b] += [1, F, 0.0]
+            vir += np.outer(2 * a * n, F * n)      # r_alpha F_beta, r = 2a n, F = F n
+            ncont += 1
+    phi = N * math.pi * a * a / area
+    Z = 2 * ncont / N
+    sig = O.angular_stress(hist, phi, Z, a, True)
+    np.testing.assert_allclose(sig[:2, :2], vir / area, rtol=1e-12)
+    rho = hist[:, 0] / (ncont * dth)
+    assert (rho * dth).sum() == pytest.approx(1.0, rel=1e-14)       # Eq. 23
+
+
+def test_angular_stress_eq27_as_printed_is_twice_the_virial():
+    """Eq. 27 is implemented as printed.  With rho normalised over [0, pi)
+    (Eq. 23) its prefactor 3 phi_3 Z <F> / (2 pi a^2) gives twice the pairwise
+    virial of coplanar monodisperse contacts, while Eq. a18 / a19 (prefactor
+    3/4, rho normalised over [0, 2 pi) by Eq. a14) gives the virial itself."""
+    nb, a, N, V = 24, 4.5, 40, 30000.0
+    rng = np.random.default_rng(6)
+    dth = math.pi / nb
+    hist = np.zeros((nb, 3))
+    vir = np.zeros((2, 2))
+    nc = 0
+    for b in range(nb):
+        for _ in range(int(rng.integers(0, 4))):
+            th = (b + 0.5) * dth
+            F = float(rng.uniform(0.1, 2.0))
+            n = np.array([math.cos(th), math.sin(th)])
+            hist[b] += [1, F, 0.0]
+            vir += np.outer(2 * a * n, F * n)
+            nc += 1
+    phi3 = N * 4 / 3 * math.pi * a ** 3 / V
+    Z = 2 * nc / N
+    sig = O.angular_stress(hist, phi3, Z, a, False)
+    np.testing.assert_allclose(sig[:2, :2], 2 * vir / V, rtol=1e-12)
+
+
+def test_histogram_of_a_single_contact():
+    """A single overlapping pair, fluid held at rest: one histogram count in
+    the bin of the contact angle, the normal force of the spring law, and the
+    contact virial -r F / V of Eq. 12."""
+    th = 0.3
+    r = 8.9
+    pa = np.array([20.0, 20.0, 20.0])
+    pb = pa - r * np.array([math.cos(th), math.sin(th), 0.0])   # r_ab = R_a - R_b at angle th
+    kn = 300.0
+    s = O.Oracle(40, 40, 40, radius=[4.5, 4.5], pos=[pa, pb], kn=kn, eta_n=0.0, lub_cut=0.0,
+                 dem_substeps=1)
+    s.step(1)
+    _, hist = s.stress(O.CONTACT)
+    b = int(th / (math.pi / 36))
+    assert hist[b, 0] == 1 and hist[:, 0].sum() == 1
+    assert hist[b, 1] == pytest.approx(kn * 0.1, rel=1e-9)
+    sig, _ = s.stress(O.CONTACT)
+    n = np.array([math.cos(th), math.sin(th), 0.0])
+    expect = -np.outer(r * n, kn * 0.1 * n) / 40 ** 3
+    np.testing.assert_allclose(sig, expect, rtol=1e-8, atol=1e-18)
