@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark: the sheared-suspension step (lattice Boltzmann + particles) on
+the 96^3 dense bulk-shear workload (bidisperse radii 4 / 5.6, phi_3 = 0.50,
+N = 882, kn = 1e3, kt = 0.5 kn, mu = 1, shear rate 1e-4, FP32 storage).
+
+One "step" is one full pass of the hot path: collide-stream with bounce-back
+and Lees-Edwards planes, link momentum exchange, particle sub-steps (cell
+list, contacts, repulsion, lubrication, integration), node-map update and the
+stress / histogram accumulation.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS and particle-steps/s vs HBM roofline; batched reduced-precision vs plain "
+          "at ≤2% stress")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(seed_offset: int = 0, L: int = 96):
+    from paper_1904_02929_gb300 import inputs
+    return inputs.config_dst(seed=1002 + seed_offset, phi3=0.50, L=L, rate=1e-4, precision="fp32")
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm_copy_gbs", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+            for k, val in d.items():
+                if "hbm" in k.lower() and isinstance(val, (int, float)):
+                    return float(val), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def k1_traffic(workload_name: str):
+    """DRAM bytes per collide-stream launch from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_collide_stream_dst96_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_1904_02929_gb300", "csrc", "lbm.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    fields = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("lbm_cu_sha256_16") != h or fields.get("workload") != workload_name:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.p = None
+        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle as O
+    kw = dict(w.params)
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
+    sh = O.shear(**w.shear)
+    t0 = time.perf_counter()
+    o.step(1, sh)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    k = max(1, min(20, int(budget_s / max(per, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    o.step(k, sh)
+    dt = time.perf_counter() - t0
+    steps = k
+    return {
+        "value": w.ncell * steps / dt / 1e6,
+        "unit": "MLUPS",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{w.name}: {steps} FP64 oracle steps after 1 warm-up step on one host core "
+                  f"({dt:.1f} s)",
+        "particle_steps_per_s": w.n * steps / dt,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    w = workload()
+    kw = dict(w.params)
+    sh = O.shear(**w.shear)
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
+    t0 = time.perf_counter()
+    o.step(1, sh)
+    per = time.perf_counter() - t0
+    sample = w
+    if (args.steps + args.warmup) * per > 150.0:
+        sample = workload(L=48)
+        o = O.Oracle(sample.nx, sample.ny, sample.nz, sample.radius, sample.pos, **dict(sample.params))
+    for _ in range(args.warmup):
+        o.step(1, sh)
+    t0 = time.perf_counter()
+    o.step(args.steps, sh)
+    dt = time.perf_counter() - t0
+    val = sample.ncell * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "particles": w.n,
+                   "storage": "fp64", "sample": sample.name},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample.name}, {args.steps} timed oracle steps"},
+        "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "particle_steps_per_s": sample.n * args.steps / dt,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1904_02929_gb300 import susp as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # independent boxes per rank (weak scaling, no data-path collective)
+    w = workload(seed_offset=rank)
+    g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **w.params)
+    info = g.info()
+    sh = S.make_shear(**w.shear)
+    g.step(args.warmup, sh)
+    torch.cuda.synchronize()
+    nfluid = int((g.owner() < 0).sum())
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    S.susp_profile(g.h, True)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    for k in range(K):
+        flush.zero_()                       # L2 flushed between timed steps (untimed)
+        ev0[k].record()
+        g.step(1, sh)
+        ev1[k].record()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    k1_ms, k1_n = S.susp_profile_read(g.h)
+    S.susp_profile(g.h, False)
+    st = S.susp_stress(g.h, S.TOTAL, g.nbins)   # raises on any device error flag
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    mlups = world * w.ncell * K / (t_max / 1e3) / 1e6
+    psteps = world * w.n * K / (t_max / 1e3)
+
+    # --- end to end through the public API: create (host arrays up), K steps
+    # each followed by the read-back of positions and stress into host memory
+    del flush
+    pos_host = torch.empty(3 * w.n, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    e = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **w.params)
+    for k in range(K):
+        e.step(1, sh)
+        R, _, _ = e.particles()
+        pos_host.numpy()[:] = R.ravel()
+        s_tot, _ = e.stress(S.TOTAL)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (w.n * (8 + 24 + 24 + 24)) / K                # radii, positions, velocities, spins
+    # pos / vel / spin, stress sums, counters, histogram and the error word of each read-back
+    d2h = 3 * 24 * w.n + 72 * 8 + 2 * 8 + 3 * 8 * g.nbins + 2 * 4
+
+    if rank == 0:
+        peak, peak_kind = peak_hbm()
+        alg_bytes = 2 * 19 * 4 * nfluid                  # FP32 populations of fluid nodes
+        k1_avg_s = (k1_ms / max(k1_n, 1)) / 1e3
+        achieved = alg_bytes / k1_avg_s / 1e9
+        traffic = k1_traffic(w.name)
+        line = {
+            "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "particles": w.n,
+                       "phi3": 0.50, "storage": "fp32", "shear_rate": w.shear["rate"],
+                       "dem_substeps": info.dem_substeps, "fluid_nodes": nfluid,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas{world}"},
+            "particle_steps_per_s": psteps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_collide_stream<fp32>", "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": k1_ms / max(k1_n, 1)},
+            "e2e": {"value": world * w.ncell * K / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": info.launches_per_step * K,
+            "clocks": clk,
+            "stress_xy_total": float(st[0][0, 1]),
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * susp.h — C ABI of the GB300 (sm_103a) sheared-suspension step.
+ *
+ * Method: Pradipto & Hayakawa, "Simulation of dense non-Brownian suspensions
+ * with the lattice Boltzmann method: shear jammed and fragile states"
+ * (arXiv:1904.02929).  One step is
+ *   - the D3Q19 lattice-Boltzmann collide-stream update (Appendix A, Eq. 3-5;
+ *     BGK, which equals the paper's linear operator when every non-conserved
+ *     mode relaxes fully, i.e. tau = 1),
+ *   - moving-particle bounce-back and link momentum exchange (Eq. 6-10),
+ *   - a Lees-Edwards sheared boundary in y (x flow, z vorticity), driven by a
+ *     constant rate or the oscillatory strain of Eq. 16,
+ *   - per particle: frictional contacts with tangential-spring history and
+ *     Coulomb slip (Eq. 11, 11t), double-layer repulsion (Eq. 13), the pairwise
+ *     lubrication correction (Appendix A) and rigid-body integration (Eq. 1),
+ *   - stress sums (Eq. 12, 14, 15) and angular contact histograms (Eq. 19-23)
+ *     for the angular stress of Eq. 26 / 27.
+ *
+ * Memory: the caller owns one device workspace of susp_workspace_bytes()
+ * bytes (for example a torch uint8 tensor).  The library never allocates
+ * device memory.  All work is enqueued on the caller's CUDA stream.
+ *
+ * Threading: a handle is used from one host thread at a time.  Calls that
+ * return host data (susp_stress, susp_get_*, susp_save) synchronise the
+ * handle's stream; susp_step is asynchronous.
+ *
+ * Populations exchanged with the host are FP64, layout [19][nz][ny][nx]
+ * (x fastest), in this velocity order (c_x, c_y, c_z):
+ *   0 ( 0, 0, 0)   1 ( 1, 0, 0)   2 (-1, 0, 0)   3 ( 0, 1, 0)   4 ( 0,-1, 0)
+ *   5 ( 0, 0, 1)   6 ( 0, 0,-1)   7 ( 1, 1, 0)   8 (-1,-1, 0)   9 ( 1,-1, 0)
+ *  10 (-1, 1, 0)  11 ( 1, 0, 1)  12 (-1, 0,-1)  13 ( 1, 0,-1)  14 (-1, 0, 1)
+ *  15 ( 0, 1, 1)  16 ( 0,-1,-1)  17 ( 0, 1,-1)  18 ( 0,-1, 1)
+ * and hold post-collision values n*(r, c_q, t).  Values at solid nodes
+ * (inside a particle's mapped radius) are undefined.
+ */
+#ifndef SUSP_H
+#define SUSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SUSP_OK = 0,
+  SUSP_EINVAL = -1,     /* bad argument or parameter                             */
+  SUSP_ENOMEM = -2,     /* workspace too small, or a fixed-capacity table full   */
+  SUSP_ECUDA = -3,      /* a CUDA call failed (message in susp_last_error)       */
+  SUSP_EOVERLAP = -4,   /* two mapped spheres claimed one node (Appendix A (i))  */
+  SUSP_EUNSTABLE = -5,  /* non-positive density or a particle faster than 0.5/step */
+  SUSP_ETIMEOUT = -6,   /* reserved: a bounded device wait gave up               */
+  SUSP_ESTATE = -7      /* call not valid in the handle's state                  */
+} susp_status;
+
+typedef enum {
+  SUSP_FP64 = 0,        /* populations stored and computed in FP64               */
+  SUSP_FP32 = 1,        /* stored and computed in FP32                           */
+  SUSP_FP16_DEV = 2,    /* stored as FP16 deviations n - C^q rho0, FP32 compute  */
+  SUSP_BF16_DEV = 3     /* stored as BF16 deviations n - C^q rho0, FP32 compute  */
+} susp_precision;
+
+typedef struct {
+  int nx, ny, nz;           /* lattice; x flow, y gradient (Lees-Edwards), z vorticity; each >= 4 */
+  double tau;               /* BGK relaxation time (> 0.5); eta0 = rho0 (tau - 1/2) / 3            */
+  double rho0;              /* reference fluid density, used in Eq. 7                             */
+  int n;                    /* number of particles (>= 0)                                          */
+  const double *radius;     /* [n] contact radii (host; copied)                                     */
+  const double *pos;        /* [3n] centres, x y z per particle (host; copied)                      */
+  const double *vel;        /* [3n] initial velocities or NULL (host; copied)                       */
+  const double *omega;      /* [3n] initial angular velocities or NULL (host; copied)               */
+  double rho_p;             /* particle density; m = rho_p 4/3 pi a^3, I = 2/5 m a^2                */
+  double mu;                /* Coulomb friction coefficient (Sec. 2)                                */
+  double kn;                /* normal spring constant (Sec. 2)                                      */
+  double kt_ratio;          /* kt / kn (the paper uses 0.2)                                         */
+  double eta_n;             /* normal dashpot; < 0 selects sqrt(m0 kn) with m0 the mean mass         */
+  double F0, debye;         /* double-layer force F0 exp(-h / debye) (Eq. 13); F0 = 0 disables      */
+  double lub_delta;         /* roughness length delta of the lubrication functions                  */
+  double lub_cut;           /* lubrication correction for gaps below lub_cut; 0 disables            */
+  double a_map_ratio;       /* mapped radius / contact radius (0.95 in Appendix A)                  */
+  int dem_substeps;         /* particle sub-steps per lattice step; 0 = automatic                   */
+  int quasi2d;              /* monolayer: U_z = 0, Omega_x = Omega_y = 0 (Sec. 4.1)                 */
+  int move_particles;       /* 0 = particles held at their given velocities                         */
+  int nbins;                /* angular histogram bins over [0, pi) (Eq. 19-23); <= 0 selects 36    */
+  double body_force[3];     /* uniform force density on the fluid (0 for shear runs)                */
+  susp_precision prec;      /* population storage                                                   */
+} susp_params;
+
+typedef struct {
+  int kind;                 /* 0: constant rate; 1: oscillatory strain, Eq. 16                     */
+  double rate;              /* kind 0: shear rate (lattice units)                                   */
+  double gamma0;            /* kind 1: strain amplitude                                             */
+  double omega;             /* kind 1: angular frequency (per lattice step)                         */
+  double theta;             /* kind 1: initial phase Theta                                          */
+} susp_shear;
+
+typedef enum {
+  SUSP_STRESS_VISCOUS = 0,  /* fluid viscous stress + particle stresslet (sigma^h, Appendix A)      */
+  SUSP_STRESS_CONTACT = 1,  /* contact virial, Eq. 12                                               */
+  SUSP_STRESS_REPULSIVE = 2,/* double-layer virial, Eq. 14                                          */
+  SUSP_STRESS_TOTAL = 3,    /* Eq. 15                                                               */
+  SUSP_STRESS_ANGULAR = 4   /* Eq. 26 (quasi2d) or Eq. 27 from the contact histogram                */
+} susp_stress_kind;
+
+typedef struct susp susp;
+
+/* Bytes of device workspace needed for these parameters; 0 if they are invalid. */
+size_t susp_workspace_bytes(const susp_params *p);
+
+/* Create a box.  dev_workspace: device pointer to >= susp_workspace_bytes(p)
+ * bytes, 256-byte aligned, owned by the caller and kept alive until
+ * susp_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Initial fluid at rest (n = C^q rho0); nodes inside a_map_ratio * radius are
+ * solid.  Synchronises the stream.  Errors: SUSP_EINVAL, SUSP_ENOMEM,
+ * SUSP_EOVERLAP, SUSP_ECUDA; *out is NULL on error. */
+susp_status susp_create(const susp_params *p, void *dev_workspace, size_t bytes,
+                        void *cuda_stream, susp **out);
+
+/* Advance nsteps lattice steps under the shear protocol *sh.  The step
+ * counter t is absolute and continues across calls; the Lees-Edwards offset
+ * is the compensated sum of the per-step increments L_y (gamma(t+1) - gamma(t)),
+ * so a new protocol (e.g. the amplitude reduction of Sec. 4.1) continues it
+ * without a jump.  Asynchronous; device-side errors surface at the next
+ * synchronising call.  Errors: SUSP_EINVAL. */
+susp_status susp_step(susp *h, int nsteps, const susp_shear *sh);
+
+/* Time-averaged stress since the last reset, row-major out[9].  If hist is
+ * non-NULL and nbins equals the handle's bin count, hist[3*nbins] receives
+ * (count, sum F_nor, sum F_tan) per angular bin.  Synchronises; returns the
+ * device error status (SUSP_EOVERLAP, SUSP_EUNSTABLE, SUSP_ENOMEM) if set. */
+susp_status susp_stress(susp *h, susp_stress_kind kind, double out[9], double *hist, int nbins);
+
+/* Zero the stress and histogram accumulators (asynchronous). */
+susp_status susp_stress_reset(susp *h);
+
+/* Particle state to host arrays [3n] (any may be NULL).  Synchronises. */
+susp_status susp_get_particles(susp *h, double *pos, double *vel, double *omega);
+
+/* Hydrodynamic link force and torque [3n] that the next step applies. Synchronises. */
+susp_status susp_get_hydro(susp *h, double *force, double *torque);
+
+/* Populations to / from FP64 host arrays [19*nx*ny*nz] in the layout above.
+ * Set converts to the storage precision and recomputes the link forces.
+ * Both synchronise. */
+susp_status susp_get_populations(susp *h, double *f);
+susp_status susp_set_populations(susp *h, const double *f);
+
+/* Node owner map [nx*ny*nz] (-1 fluid, else particle index). Synchronises. */
+susp_status susp_get_owner(susp *h, int32_t *owner);
+
+/* Step counter and Lees-Edwards offset (in [0, nx)).  Synchronises. */
+susp_status susp_get_time(susp *h, int64_t *t, double *delta);
+
+/* Run facts: particle sub-steps per lattice step, kernels launched per step,
+ * whether the pair search is brute force (small boxes), lattice nodes. */
+typedef struct {
+  int dem_substeps;
+  int launches_per_step;
+  int brute_force_pairs;
+  long long ncell;
+  size_t workspace_bytes;
+} susp_info;
+susp_status susp_get_info(susp *h, susp_info *info);
+
+/* Instrumentation (no counterpart in the paper): when enabled, each step
+ * brackets its collide-stream launch with CUDA events on the handle's stream
+ * (at most 4096 steps per window).  susp_profile_read synchronises and
+ * returns the summed launch time in ms and the number of launches, then
+ * starts a new window. */
+susp_status susp_profile(susp *h, int enable);
+susp_status susp_profile_read(susp *h, double *ms_total, int *launches);
+
+/* Release the handle (not the caller's workspace). */
+void susp_destroy(susp *h);
+
+/* Message of the last failing call on this thread (never NULL). */
+const char *susp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

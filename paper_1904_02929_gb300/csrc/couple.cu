@@ -1,0 +1,353 @@
+// couple.cu — fluid-particle coupling on the node map (Appendix A).
+//
+// Nodes closer than the mapped radius a_map = 0.95 a to a particle centre
+// (any Lees-Edwards image) are solid and owned by that particle.  After the
+// particles move:
+//   k_uncover: solid nodes that left the mapped sphere become fluid with
+//              n = n^eq(rho0, rho0 u_b); the particle loses that momentum
+//              (and its moment about the centre);
+//   k_cover:   fluid nodes that entered become solid; their momentum
+//              sum_q n_q c_q goes to the particle;
+//   k_links:   for every solid node s of the particle and direction p, the
+//              fluid node r that pulls population p from s (r = s + c_p, or
+//              across a Lees-Edwards plane the node whose nearest source is
+//              s) forms a boundary link; the link sets bit p of r's mask (for
+//              non-crossing links) and contributes the momentum exchange
+//              f = [2 n*_q(r) - 6 C^q rho0 (u_b . c_q)] c_q,  q = -p (Eq. 6),
+//              to F^h (Eq. 9), (r_b - R) x f to T^h (Eq. 10) and
+//              (r_b - R)_a f_b to the particle stresslet (sigma^h).
+// One block per particle scans the cells of the particle's bounding boxes
+// (one per Lees-Edwards image that reaches into the box).  Per-particle sums
+// use a fixed-order block reduction, so they are deterministic.
+#include "susp_dev.cuh"
+
+namespace susp_dev {
+
+struct ImgBox {
+  int x0, y0, z0, ex, ey, ez, cnt;
+};
+
+template <typename TC>
+__device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delta, TC reach,
+                                     ImgBox (&b)[3]) {
+  int total = 0;
+#pragma unroll
+  for (int k = -1; k <= 1; ++k) {
+    ImgBox& B = b[k + 1];
+    const TC cx = Rx + (TC)k * delta, cy = Ry + (TC)k * (TC)v.ny, cz = Rz;
+    int y0 = (int)ceil(cy - reach), y1 = (int)floor(cy + reach);
+    if (y0 < 0) y0 = 0;
+    if (y1 > v.ny - 1) y1 = v.ny - 1;
+    const int x0 = (int)ceil(cx - reach), x1 = (int)floor(cx + reach);
+    const int z0 = (int)ceil(cz - reach), z1 = (int)floor(cz + reach);
+    B.x0 = x0; B.y0 = y0; B.z0 = z0;
+    B.ex = x1 - x0 + 1; B.ey = y1 - y0 + 1; B.ez = z1 - z0 + 1;
+    B.cnt = (y0 > y1) ? 0 : B.ex * B.ey * B.ez;
+    total += B.cnt;
+  }
+  return total;
+}
+
+__device__ inline void box_cell(const View& v, const ImgBox (&b)[3], int t, int& x, int& y, int& z) {
+  int k = 0;
+  while (t >= b[k].cnt) { t -= b[k].cnt; ++k; }
+  const int lx = t % b[k].ex;
+  t /= b[k].ex;
+  const int ly = t % b[k].ey, lz = t / b[k].ey;
+  x = wrapi(b[k].x0 + lx, v.nx);
+  y = b[k].y0 + ly;
+  z = wrapi(b[k].z0 + lz, v.nz);
+}
+
+template <typename TC>
+__device__ inline TC pdelta(const Proto* pr) { return sel<TC>(pr->delta, pr->delta_f); }
+template <typename TC>
+__device__ inline TC pule(const Proto* pr) { return sel<TC>(pr->ule, pr->ule_f); }
+
+// Initial claim of the solid nodes (creation).
+template <int P>
+__global__ void k_claim(View v) {
+  using TC = typename Store<P>::C;
+  const int i = blockIdx.x;
+  const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
+  const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
+  const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
+  const TC delta = pdelta<TC>(v.proto);
+  ImgBox b[3];
+  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int x, y, z;
+    box_cell(v, b, t, x, y, z);
+    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
+    le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+    if (dx * dx + dy * dy + dz * dz < am * am) {
+      const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
+      const int old = atomicCAS(v.owner + c, -1, i);
+      if (old == -1) atomicOr(v.mask + c, 1u);
+      else if (old != i) atomicOr(v.err, ERR_OVERLAP);
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_uncover(View v, typename Store<P>::T* __restrict__ f) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  __shared__ TC red[32 * 6];
+  const int i = blockIdx.x;
+  // clear the mask bits of last step's links of this particle
+  const int off = v.link_off[i], nl = v.link_cnt[i];
+  for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+    const uint32_t L = v.links[off + k];
+    atomicAnd(v.mask + (L >> 5), ~(1u << (L & 31u)));
+  }
+  const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
+  const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
+  const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
+  const TC delta = pdelta<TC>(v.proto), ule = pule<TC>(v.proto);
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  ImgBox b[3];
+  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  TC acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int x, y, z;
+    box_cell(v, b, t, x, y, z);
+    const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
+    if (v.owner[c] != i) continue;
+    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
+    const int k = le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+    if (dx * dx + dy * dy + dz * dz < am * am) continue;
+    // solid node leaves the mapped sphere: fluid at rho0 and the boundary velocity
+    const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+    const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+    const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+    const TC jx = rho0 * ubx, jy = rho0 * uby, jz = rho0 * ubz;
+    const TC inv = (TC)1 / rho0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      f[(long long)q * v.ncell + c] =
+          S::enc(feq<TC>(q, rho0, jx, jy, jz, inv), (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+    v.owner[c] = -1;
+    atomicAnd(v.mask + c, ~1u);
+    acc[0] -= jx; acc[1] -= jy; acc[2] -= jz;
+    acc[3] -= dy * jz - dz * jy; acc[4] -= dz * jx - dx * jz; acc[5] -= dx * jy - dy * jx;
+  }
+  block_sum<TC, 6>(acc, red);
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) {
+      v.Fcov[3 * i + a] = (double)acc[a];
+      v.Tcov[3 * i + a] = (double)acc[3 + a];
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::T* __restrict__ f) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  __shared__ TC red[32 * 6];
+  const int i = blockIdx.x;
+  const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
+  const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
+  const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
+  const TC delta = pdelta<TC>(v.proto);
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  ImgBox b[3];
+  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  TC acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int x, y, z;
+    box_cell(v, b, t, x, y, z);
+    const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
+    const int own = v.owner[c];
+    if (own == i) continue;
+    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
+    le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+    if (!(dx * dx + dy * dy + dz * dz < am * am)) continue;
+    const int old = own == -1 ? atomicCAS(v.owner + c, -1, i) : own;
+    if (old != -1) { atomicOr(v.err, ERR_OVERLAP); continue; }
+    atomicOr(v.mask + c, 1u);
+    TC jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const TC fq = S::load(f, (long long)q * v.ncell + c, (TC)D3Q19::w(q) * rho0, (TC)v.inv_scale);
+      jx += fq * (TC)D3Q19::cx(q); jy += fq * (TC)D3Q19::cy(q); jz += fq * (TC)D3Q19::cz(q);
+    }
+    acc[0] += jx; acc[1] += jy; acc[2] += jz;
+    acc[3] += dy * jz - dz * jy; acc[4] += dz * jx - dx * jz; acc[5] += dx * jy - dy * jx;
+  }
+  block_sum<TC, 6>(acc, red);
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) {
+      v.Fcov[3 * i + a] += (double)acc[a];
+      v.Tcov[3 * i + a] += (double)acc[3 + a];
+    }
+  }
+}
+
+// Fluid node that pulls population p from solid node (x, y, z); returns its
+// index or -1 if it is solid.  crossing = the pull passes a Lees-Edwards plane.
+__device__ inline long long link_target(const View& v, const Proto* pr, int x, int y, int z, int p,
+                                        int& rx, int& ry, int& rz, bool& crossing) {
+  const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+  ry = y + cpy;
+  rz = wrapi(z + cpz, v.nz);
+  crossing = (ry < 0) || (ry >= v.ny);
+  if (!crossing) {
+    rx = wrapi(x + cpx, v.nx);
+  } else if (ry >= v.ny) {
+    // receiver at y = 0 pulls from below: nearest source x_r - c_px + di + near_lo
+    ry = 0;
+    rx = wrapi(x + cpx - pr->di - pr->near_lo, v.nx);
+  } else {
+    // receiver at y = ny-1 pulls from above: nearest source x_r - c_px - di - 1 + near_hi
+    ry = v.ny - 1;
+    rx = wrapi(x + cpx + pr->di + 1 - pr->near_hi, v.nx);
+  }
+  const long long r = rx + (long long)v.nx * (ry + (long long)v.ny * rz);
+  return v.owner[r] == -1 ? r : -1;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_links(View v, const typename Store<P>::T* __restrict__ f) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  __shared__ TC red[32 * 15];
+  __shared__ int s_count;
+  const int i = blockIdx.x;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
+  const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
+  const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
+  const Proto* pr = v.proto;
+  const TC delta = pdelta<TC>(pr), ule = pule<TC>(pr);
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  const int off = v.link_off[i], cap = v.link_cap[i];
+  ImgBox b[3];
+  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  TC acc[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) acc[k] = 0;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int x, y, z;
+    box_cell(v, b, t, x, y, z);
+    const long long s = x + (long long)v.nx * (y + (long long)v.ny * z);
+    if (v.owner[s] != i) continue;
+    for (int p = 1; p < 19; ++p) {
+      int rx, ry, rz;
+      bool crossing;
+      const long long r = link_target(v, pr, x, y, z, p, rx, ry, rz, crossing);
+      if (r < 0) continue;
+      if (!crossing) {
+        atomicOr(v.mask + r, 1u << p);
+        const int slot = atomicAdd(&s_count, 1);
+        if (slot < cap) v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
+      }
+      const int q = D3Q19::opp(p);
+      const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+      TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
+      const int k = le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+      const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+      const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+      const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
+      const TC wq = (TC)D3Q19::w(q);
+      const TC nq = S::load(f, (long long)q * v.ncell + r, wq * rho0, (TC)v.inv_scale);
+      const TC mag = (TC)2 * nq - (TC)6 * wq * rho0 * cu;
+      const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
+      acc[0] += fx; acc[1] += fy; acc[2] += fz;
+      acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
+      acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
+      acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
+      acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+    }
+  }
+  block_sum<TC, 15>(acc, red);
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 3; ++a) {
+      v.Fh[3 * i + a] = (double)acc[a];
+      v.Th[3 * i + a] = (double)acc[3 + a];
+    }
+    for (int a = 0; a < 9; ++a) v.slet_part[9 * i + a] = (double)acc[6 + a];
+    if (s_count > cap) atomicOr(v.err, ERR_LINKS);
+    v.link_cnt[i] = s_count < cap ? s_count : cap;
+  }
+}
+
+template <int P>
+__global__ void k_init_pop(View v, typename Store<P>::T* __restrict__ f) {
+  using TC = typename Store<P>::C;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= v.ncell) return;
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+#pragma unroll
+  for (int q = 0; q < 19; ++q)
+    f[(long long)q * v.ncell + idx] = Store<P>::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+}
+
+}  // namespace susp_dev
+
+using namespace susp_dev;
+
+#define SUSP_DISPATCH(prec, KER, grid, block, stream, ...)                                        \
+  switch (prec) {                                                                                \
+    case 0: KER<0><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
+    case 1: KER<1><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
+    case 2: KER<2><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
+    default: KER<3><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                             \
+  }
+
+template <int P> using PT = typename Store<P>::T;
+
+void launch_claim(int prec, const View& v, cudaStream_t s) {
+  if (v.n == 0) return;
+  switch (prec) {
+    case 0: k_claim<0><<<v.n, 128, 0, s>>>(v); break;
+    case 1: k_claim<1><<<v.n, 128, 0, s>>>(v); break;
+    case 2: k_claim<2><<<v.n, 128, 0, s>>>(v); break;
+    default: k_claim<3><<<v.n, 128, 0, s>>>(v); break;
+  }
+}
+
+void launch_node_update(int prec, const View& v, void* f, cudaStream_t s) {
+  if (v.n == 0) return;
+  switch (prec) {
+    case 0:
+      k_uncover<0><<<v.n, 256, 0, s>>>(v, (PT<0>*)f);
+      k_cover<0><<<v.n, 256, 0, s>>>(v, (const PT<0>*)f);
+      break;
+    case 1:
+      k_uncover<1><<<v.n, 256, 0, s>>>(v, (PT<1>*)f);
+      k_cover<1><<<v.n, 256, 0, s>>>(v, (const PT<1>*)f);
+      break;
+    case 2:
+      k_uncover<2><<<v.n, 256, 0, s>>>(v, (PT<2>*)f);
+      k_cover<2><<<v.n, 256, 0, s>>>(v, (const PT<2>*)f);
+      break;
+    default:
+      k_uncover<3><<<v.n, 256, 0, s>>>(v, (PT<3>*)f);
+      k_cover<3><<<v.n, 256, 0, s>>>(v, (const PT<3>*)f);
+      break;
+  }
+}
+
+void launch_links(int prec, const View& v, const void* f, cudaStream_t s) {
+  if (v.n == 0) return;
+  switch (prec) {
+    case 0: k_links<0><<<v.n, 256, 0, s>>>(v, (const PT<0>*)f); break;
+    case 1: k_links<1><<<v.n, 256, 0, s>>>(v, (const PT<1>*)f); break;
+    case 2: k_links<2><<<v.n, 256, 0, s>>>(v, (const PT<2>*)f); break;
+    default: k_links<3><<<v.n, 256, 0, s>>>(v, (const PT<3>*)f); break;
+  }
+}
+
+void launch_init_pop(int prec, const View& v, void* f, cudaStream_t s) {
+  const int nb = (int)((v.ncell + 255) / 256);
+  switch (prec) {
+    case 0: k_init_pop<0><<<nb, 256, 0, s>>>(v, (PT<0>*)f); break;
+    case 1: k_init_pop<1><<<nb, 256, 0, s>>>(v, (PT<1>*)f); break;
+    case 2: k_init_pop<2><<<nb, 256, 0, s>>>(v, (PT<2>*)f); break;
+    default: k_init_pop<3><<<nb, 256, 0, s>>>(v, (PT<3>*)f); break;
+  }
+}

@@ -1,0 +1,185 @@
+// susp_dev.cuh — device-side definitions shared by the CUDA translation units
+// of the sheared-suspension step (lattice, storage traits, state views).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace susp_dev {
+
+// ---------------------------------------------------------------- D3Q19
+// Velocity set of Appendix A with weights C^q = 1/3, 1/18, 1/36; the order is
+// the one documented in include/susp.h.
+struct D3Q19 {
+  static constexpr int Q = 19;
+  // components packed as (c + 1) in two bits per direction:
+  //   cx = 0 1 -1 0 0 0 0 1 -1 1 -1 1 -1 1 -1 0 0 0 0
+  //   cy = 0 0 0 1 -1 0 0 1 -1 -1 1 0 0 0 0 1 -1 1 -1
+  //   cz = 0 0 0 0 0 1 -1 0 0 0 0 1 -1 -1 1 1 -1 -1 1
+  __host__ __device__ static constexpr int cx(int q) { return (int)((0x1548889549ULL >> (2 * q)) & 3) - 1; }
+  __host__ __device__ static constexpr int cy(int q) { return (int)((0x895609495ULL >> (2 * q)) & 3) - 1; }
+  __host__ __device__ static constexpr int cz(int q) { return (int)((0x20a0954955ULL >> (2 * q)) & 3) - 1; }
+  // opposite direction: pairs (1,2) (3,4) ... (17,18)
+  __host__ __device__ static constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+  __host__ __device__ static constexpr double w(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+// ------------------------------------------------------------ storage traits
+// P = 0 FP64, 1 FP32, 2 FP16 deviation, 3 BF16 deviation from C^q rho0.
+template <int P> struct Store;
+template <> struct Store<0> {
+  using T = double; using C = double;
+  __device__ static C load(const T* f, long long i, C, C) { return f[i]; }
+  __device__ static T enc(C v, C, C) { return v; }
+};
+template <> struct Store<1> {
+  using T = float; using C = float;
+  __device__ static C load(const T* f, long long i, C, C) { return __ldg(f + i); }
+  __device__ static T enc(C v, C, C) { return v; }
+};
+template <> struct Store<2> {
+  using T = __half; using C = float;
+  // value = base + stored / scale
+  __device__ static C load(const T* f, long long i, C base, C inv_scale) {
+    return base + __half2float(f[i]) * inv_scale;
+  }
+  __device__ static T enc(C v, C base, C scale) { return __float2half_rn((v - base) * scale); }
+};
+template <> struct Store<3> {
+  using T = __nv_bfloat16; using C = float;
+  __device__ static C load(const T* f, long long i, C base, C inv_scale) {
+    return base + __bfloat162float(f[i]) * inv_scale;
+  }
+  __device__ static T enc(C v, C base, C scale) { return __float2bfloat16_rn((v - base) * scale); }
+};
+
+// ------------------------------------------------------------ protocol state
+// Lees-Edwards state of the current step t (transition t -> t+1): offset
+// Delta_t (compensated sum), image velocity U_t = Ly (gamma(t+1) - gamma(t)),
+// and the same for t+1.  The streaming shift of Delta_t is split into an
+// integer part di and fraction w, with the nearest-source choices for the two
+// boundary planes precomputed so that every kernel makes the same decision.
+struct Proto {
+  long long t;
+  double delta, delta_c, ule;
+  double delta_n, delta_nc, ule_n;
+  int di, near_lo, near_hi, pad;
+  double w;
+  float wf_lo, wf_hi;          // interpolation weight on c1 for y = 0 / y = ny-1 receivers
+  float delta_f, ule_f;        // FP32 copies of delta and ule
+  int kind, ny;
+  double rate, gamma0, omega, theta;
+};
+
+__device__ inline double proto_increment(const Proto& s, long long t) {
+  if (s.kind == 0) return (double)s.ny * s.rate;
+  double a = s.omega * (double)t + s.theta;
+  double b = s.omega * (double)(t + 1) + s.theta;
+  return (double)s.ny * s.gamma0 * (cos(a) - cos(b));
+}
+
+// ------------------------------------------------------------ state view
+struct View {
+  // lattice
+  int nx, ny, nz;
+  long long ncell;
+  double tau, rho0, g[3];
+  float inv_scale, scale;       // deviation storage scale (P = 2, 3)
+  // per-node constants in both precisions (no FP64 arithmetic on the FP32 paths)
+  double omega_d, vf_d;         // 1/tau and -(1 - 1/(2 tau))
+  float omega_f, vf_f, rho0_f, g_f[3];
+  uint32_t* mask;               // bit 0 solid, bit p: pull source of p is solid (not LE-crossing)
+  int* owner;                   // -1 fluid, else particle
+  void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
+  double* visc_part;            // [nblk][6]
+  int nblk_lb;
+  // particles
+  int n;
+  double *R, *U, *W, *rad, *amap, *mass, *inert;
+  void* plb;                    // [n][12] compute-type copy: R, U, W (and pad)
+  double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
+  double *slet_part, *cvir_part, *rvir_part;   // [n][9]
+  int* ncont_part;              // [n]
+  uint32_t* links;              // per-particle segments of (cell << 5 | p)
+  int *link_off, *link_cap, *link_cnt;
+  // cell list
+  int ncx, ncy, ncz, brute;
+  double csx, csy, csz;
+  int *cell_start, *cell_cnt, *cell_ids, *pcell;
+  int ncells;
+  // tangential-spring table: per particle a, partners b > a
+  int K;
+  int *hcnt0, *hpart0, *hcnt1, *hpart1;
+  double *hval0, *hval1;
+  // physics
+  double mu, kn, kt, eta_n, F0, debye, lub_delta, lub_cut, eta0, hrange;
+  int nsub, quasi2d, move, nbins;
+  // accumulators
+  double* sums;                 // [4][9] Kahan sums (visc, slet, contact, repulsive) + [4][9] comps
+  double* hist;                 // [3 nbins]
+  unsigned long long* counters; // [0] samples, [1] contacts
+  Proto* proto;
+  int* err;
+};
+
+enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
+
+// Select the double or float copy of a constant for compute type T.
+template <typename T> __device__ __forceinline__ T sel(double d, float f);
+template <> __device__ __forceinline__ double sel<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float sel<float>(double, float f) { return f; }
+
+__host__ __device__ inline int wrapi(int v, int L) { int r = v % L; return r < 0 ? r + L : r; }
+
+// Lees-Edwards minimum image of d = p - R for a particle centre R: returns k,
+// the image R + k (delta, ny, 0) moving with U + k U_LE e_x.
+template <typename T>
+__device__ inline int le_image(T& dx, T& dy, T& dz, T delta, int nx, int ny, int nz) {
+  const T fny = (T)ny, fnx = (T)nx, fnz = (T)nz;
+  int k = (int)floor(dy / fny + (T)0.5);
+  dy -= (T)k * fny;
+  dx -= (T)k * delta;
+  dx -= fnx * floor(dx / fnx + (T)0.5);
+  dz -= fnz * floor(dz / fnz + (T)0.5);
+  return k;
+}
+
+template <typename T>
+__device__ inline T feq(int q, T rho, T jx, T jy, T jz, T inv_rho) {
+  T jc = jx * (T)D3Q19::cx(q) + jy * (T)D3Q19::cy(q) + jz * (T)D3Q19::cz(q);
+  T jj = jx * jx + jy * jy + jz * jz;
+  return (T)D3Q19::w(q) * (rho + (T)3 * jc + (T)4.5 * jc * jc * inv_rho - (T)1.5 * jj * inv_rho);
+}
+
+// Block-wide sum of NV values held by every thread (blockDim multiple of 32,
+// <= 1024); result valid in thread 0.  Fixed reduction order.
+template <typename T, int NV>
+__device__ inline void block_sum(T (&v)[NV], T* smem /* [32][NV] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[wid * NV + k] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = lane < nw ? smem[lane * NV + k] : (T)0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace susp_dev

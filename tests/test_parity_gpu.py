@@ -1,0 +1,216 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 storage <= 1e-12 relative on populations after 100 steps,
+FP32 <= 2e-5; particle centres <= 1e-9 (FP64) over 50 steps; stresses of FP64
+runs <= 1e-9 relative.  Population errors are max |gpu - oracle| over the
+nodes that are fluid on both sides, divided by max |oracle| there.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1904_02929_gb300 import inputs as I
+from paper_1904_02929_gb300 import susp as S
+
+pytestmark = pytest.mark.gpu
+
+C_LAT, W_LAT, _ = O.lattice()
+
+
+def _both(nx, ny, nz, radius=(), pos=(), precision="fp64", **kw):
+    g = S.Suspension(nx, ny, nz, radius, pos, precision=precision, **kw)
+    o = O.Oracle(nx, ny, nz, radius, pos, **kw)
+    return g, o
+
+
+def _step(g, o, n, **sh):
+    g.step(n, S.make_shear(**sh))
+    o.step(n, O.shear(**sh))
+
+
+def _pop_err(g, o):
+    fo, fg = o.populations(), g.populations()
+    fl = (o.owner() < 0) & (g.owner() < 0)
+    return np.abs(fg[:, fl] - fo[:, fl]).max() / np.abs(fo[:, fl]).max()
+
+
+def _params(w, **over):
+    kw = dict(w.params)
+    kw.update(over)
+    return kw
+
+
+# ------------------------------------------------------------------ fluid only
+@pytest.mark.parametrize("shape", [(37, 21, 13), (32, 16, 8), (4, 4, 4)])
+def test_fluid_lees_edwards_fp64(shape):
+    nx, ny, nz = shape
+    f0 = I.random_populations(nx, ny, nz, seed=11, amplitude=0.03, weights=W_LAT)
+    g, o = _both(nx, ny, nz, tau=0.8)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    _step(g, o, 100, kind=0, rate=3.7e-3)
+    assert _pop_err(g, o) < 1e-12
+    tg, dg = g.time()
+    assert tg == 100 and abs(dg - o.delta) < 1e-12
+
+
+def test_fluid_oscillatory_fp64():
+    nx, ny, nz = 24, 18, 10
+    f0 = I.random_populations(nx, ny, nz, seed=12, amplitude=0.03, weights=W_LAT)
+    g, o = _both(nx, ny, nz, tau=1.0)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    sh = dict(kind=1, gamma0=0.5, omega=2 * math.pi / 50, theta=math.pi / 2)
+    _step(g, o, 60, **sh)
+    # amplitude reduction: a second protocol continues the offset
+    sh2 = dict(kind=1, gamma0=0.05, omega=2 * math.pi / 50, theta=math.pi / 2)
+    _step(g, o, 40, **sh2)
+    assert _pop_err(g, o) < 1e-12
+    assert abs(g.time()[1] - o.delta) < 1e-11
+
+
+def test_fluid_fp32():
+    nx, ny, nz = 40, 24, 12
+    f0 = I.random_populations(nx, ny, nz, seed=13, amplitude=0.03, weights=W_LAT)
+    g, o = _both(nx, ny, nz, precision="fp32", tau=0.9)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    _step(g, o, 100, kind=0, rate=2.3e-3)
+    assert _pop_err(g, o) < 2e-5
+
+
+def test_viscous_stress_fp64():
+    nx, ny, nz = 16, 20, 8
+    f0 = I.random_populations(nx, ny, nz, seed=14, amplitude=0.02, weights=W_LAT)
+    g, o = _both(nx, ny, nz, tau=0.7)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    _step(g, o, 30, kind=0, rate=1e-3)
+    sg, _ = g.stress(S.VISCOUS)
+    so, _ = o.stress(O.VISCOUS)
+    assert np.abs(sg - so).max() <= 1e-10 * np.abs(so).max()
+
+
+# ------------------------------------------------------------ with particles
+def test_held_particles_fp64():
+    w = I.config_small()
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, **_params(w, move_particles=False))
+    assert (g.owner() == o.owner()).all()
+    _step(g, o, 100, kind=0, rate=1e-3)
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+    Fg, Tg = g.hydro()
+    Fo, To = o.hydro()
+    scale = np.abs(Fo).max()
+    # the oracle holds the link sums of the last step, the library those for the next
+    o.step(1, O.shear(kind=0, rate=1e-3))
+    Fo, To = o.hydro()
+    assert np.abs(Fg - Fo).max() <= 1e-10 * max(scale, np.abs(Fo).max())
+    assert np.abs(Tg - To).max() <= 1e-10 * np.abs(To).max()
+
+
+def test_moving_particles_fp64_trajectories():
+    w = I.config_small()
+    vel = np.random.default_rng(21).normal(0, 2e-3, (w.n, 3))
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, vel=vel, **_params(w))
+    _step(g, o, 50, kind=0, rate=2e-3)
+    Rg, Ug, Wg = g.particles()
+    Ro, Uo, Wo = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9
+    assert np.abs(Ug - Uo).max() < 1e-9
+    assert np.abs(Wg - Wo).max() < 1e-9
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+
+
+def test_dense_contacts_lubrication_repulsion_fp64():
+    """Bidisperse 40^3 at phi_3 ~ 0.35 with kn = 1e3, kt = 0.5 kn, F0 > 0:
+    contacts, tangential history, Coulomb slip, lubrication and double-layer
+    forces are all active; 50 steps of trajectories and every stress kind."""
+    a_min = 4.0
+    box = (40, 40, 40)
+    n = I.n_for_phi3(0.35, box, a_min, 1.4 * a_min)
+    r = I.bidisperse_radii(n, a_min)
+    pos = I.place_spheres(box, r, seed=31, min_gap=0.02)
+    vel = np.random.default_rng(32).normal(0, 5e-3, (n, 3))
+    kw = dict(tau=1.0, kn=1e3, kt_ratio=0.5, mu=1.0, F0=0.2, debye=0.08, lub_delta=0.04,
+              lub_cut=0.5, a_map_ratio=0.95, nbins=36)
+    g, o = _both(*box, r, pos, vel=vel, **kw)
+    _step(g, o, 50, kind=0, rate=1e-3)
+    Rg, Ug, _ = g.particles()
+    Ro, Uo, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+    for kind in (S.VISCOUS, S.CONTACT, S.REPULSIVE, S.TOTAL, S.ANGULAR):
+        sg, hg = g.stress(kind)
+        so, ho = o.stress(kind)
+        assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
+    assert (hg[:, 0] == ho[:, 0]).all()
+    assert hg[:, 0].sum() > 0, "the run should have contacts"
+
+
+def test_quasi2d_oscillatory_fp64():
+    box = (64, 64, 12)
+    a_max = 3.0
+    a_min = a_max / 1.4
+    n = I.n_for_phi2(0.45, box, a_min, a_max)
+    r = I.bidisperse_radii(n, a_min)
+    pos = I.place_spheres(box, r, seed=41, quasi2d=True, min_gap=0.05)
+    m0 = 0.5 * 4 / 3 * math.pi * (a_min ** 3 + a_max ** 3)
+    kw = dict(tau=1.0, kn=0.36 * m0, kt_ratio=0.2, mu=1.0, F0=2e-4 * 0.36 * m0,
+              debye=0.02 * a_min, lub_delta=0.01 * a_min, lub_cut=0.5, quasi2d=True)
+    g, o = _both(*box, r, pos, **kw)
+    sh = dict(kind=1, gamma0=0.3, omega=2 * math.pi / 400, theta=0.0)
+    _step(g, o, 60, **sh)
+    Rg, _, _ = g.particles()
+    Ro, _, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9
+    assert np.abs(Rg[:, 2] - box[2] / 2).max() == 0.0
+    assert _pop_err(g, o) < 1e-12
+    sg, _ = g.stress(S.ANGULAR)
+    so, _ = o.stress(O.ANGULAR)
+    assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300)
+
+
+def test_moving_particles_fp32():
+    w = I.config_small(precision="fp32")
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **_params(w))
+    _step(g, o, 100, kind=0, rate=1e-3)
+    assert _pop_err(g, o) < 2e-5
+    Rg, _, _ = g.particles()
+    Ro, _, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-4
+
+
+# ---------------------------------------------------------------- edge cases
+def test_no_particles_and_minimum_box():
+    g = S.Suspension(4, 4, 4, precision="fp32")
+    g.step(3, S.make_shear(kind=0, rate=1e-2))
+    f = g.populations()
+    assert np.isfinite(f).all()
+    s, h = g.stress(S.TOTAL)
+    assert np.isfinite(s).all() and h.sum() == 0
+
+
+def test_overlapping_mapped_spheres_are_rejected():
+    with pytest.raises(S.SuspError) as e:
+        S.Suspension(24, 24, 24, [4.0, 4.0], [[12, 12, 12], [12, 12, 17.0]], precision="fp32")
+    assert e.value.status == S.SUSP_EOVERLAP
+
+
+# -------------------------------------------------------- full-size workload
+def test_full_size_dense_shear_fp32_sampled():
+    """The benchmark workload (96^3, phi_3 = 0.50, FP32) in the benchmark's
+    launch configuration: a few steps against the oracle on the whole box."""
+    w = I.config_dst(phi3=0.50)
+    kw = _params(w)
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **kw)
+    _step(g, o, 3, **w.shear)
+    assert _pop_err(g, o) < 2e-5
+    Rg, _, _ = g.particles()
+    Ro, _, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-6
+    assert (g.owner() == o.owner()).mean() > 0.99999
