@@ -433,16 +433,24 @@ static void link_forces(orc_sim *s, double delta, double ule) {
     for (int y = 0; y < s->ny; ++y)
       for (int x = 0; x < s->nx; ++x) {
         long c = cidx(s, x, y, z);
-        if (s->owner[c] >= 0) continue;
+        int own = s->owner[c];
         for (int p = 1; p < Q; ++p) {
           double v;
           int i = pull_source(s, s->fA, x, y, z, p, L, ule, &v);
-          if (i < 0) continue;
-          int q = opposite(p); /* c_q points from the fluid node into the solid */
+          if (i < 0 || i == own) continue;
+          int q = opposite(p); /* c_q points from node r into particle i's solid */
           double arm[3], ub[3];
           link_geometry(s, i, x, y, z, q, delta, ule, arm, ub);
-          double cu = ub[0] * CV[q][0] + ub[1] * CV[q][1] + ub[2] * CV[q][2];
-          double mag = 2.0 * s->fA[q * s->ncell + c] - 6.0 * weight(q) * s->rho0 * cu;
+          double mag;
+          if (own < 0) {
+            /* fluid node: momentum exchange of the bounced population */
+            double cu = ub[0] * CV[q][0] + ub[1] * CV[q][1] + ub[2] * CV[q][2];
+            mag = 2.0 * s->fA[q * s->ncell + c] - 6.0 * weight(q) * s->rho0 * cu;
+          } else {
+            /* node of another particle touching i's solid: it counts as fluid
+             * at rest, so a particle in a fluid at rest feels no net force */
+            mag = 2.0 * weight(q) * s->rho0;
+          }
           double fv[3] = {mag * CV[q][0], mag * CV[q][1], mag * CV[q][2]};
           double tq[3];
           cross(arm, fv, tq);

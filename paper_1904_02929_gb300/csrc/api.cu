@@ -17,7 +17,8 @@ using namespace susp_dev;
 // launchers defined in the other translation units
 void launch_plane_moments(int prec, const View& v, const void* fin, cudaStream_t s);
 void launch_collide_stream(int prec, const View& v, const void* fin, void* fout, cudaStream_t s);
-int lb_blocks(long long ncell);
+int lb_blocks(int nx, int ny, int nz);
+int lb_grid_blocks(int prec, int nx, int ny, int nz);
 void launch_claim(int prec, const View& v, cudaStream_t s);
 void launch_node_update(int prec, const View& v, void* f, cudaStream_t s);
 void launch_links(int prec, const View& v, const void* f, cudaStream_t s);
@@ -35,6 +36,8 @@ susp_status fail(susp_status st, const std::string& msg) {
 }
 
 const int HSLOTS = 16;        // tangential springs per particle (partners with larger index)
+const int FIN_BLOCKS = 32;    // blocks of the per-step finalisation
+const int FIN_VALS = 40;      // 6 visc, 9 stresslet, 9 contact, 1 contacts, 9 repulsive
 const double KPI = 3.14159265358979323846;
 
 size_t esize(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
@@ -43,11 +46,11 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t fa, fb, mask, owner, pm, visc;
-  size_t R, U, W, rad, amap, mass, inert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
+  size_t R, U, W, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
   size_t slet, cvir, rvir, ncont, links, loff, lcap, lcnt;
   size_t cstart, ccnt, cids, pcell;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
-  size_t sums, hist, counters, proto, err;
+  size_t sums, hist, counters, proto, err, finp, finc;
   size_t total;
   long long nlinks;
   int ncx, ncy, ncz, brute, ncells;
@@ -97,9 +100,10 @@ void make_layout(const susp_params* p, Layout& L) {
   L.mask = take(4 * nc);
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
-  L.visc = take(6 * 8 * (size_t)lb_blocks(nc));
+  L.visc = take(6 * 8 * (size_t)lb_blocks(p->nx, p->ny, p->nz));
   L.R = take(24 * nn); L.U = take(24 * nn); L.W = take(24 * nn);
   L.rad = take(8 * nn); L.amap = take(8 * nn); L.mass = take(8 * nn); L.inert = take(8 * nn);
+  L.imass = take(8 * nn); L.iinert = take(8 * nn);
   L.plb = take(12 * csize(prec) * nn);
   L.Fh = take(24 * nn); L.Th = take(24 * nn); L.Fcov = take(24 * nn); L.Tcov = take(24 * nn);
   L.Fp = take(24 * nn); L.Tp = take(24 * nn);
@@ -133,6 +137,8 @@ void make_layout(const susp_params* p, Layout& L) {
   L.counters = take(8 * 4);
   L.proto = take(sizeof(Proto));
   L.err = take(4);
+  L.finp = take(8 * FIN_VALS * FIN_BLOCKS);
+  L.finc = take(4);
   L.total = o;
 }
 
@@ -172,57 +178,72 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
   *pp = s;
 }
 
-// End of step t: reduce the per-block / per-particle stress partials in a
-// fixed order, add them to the compensated time sums, then advance the
-// protocol to t+1.
-__global__ void __launch_bounds__(256) k_finalize(View v) {
-  __shared__ double red[32 * 28];
-  double acc[28];
-  for (int k = 0; k < 28; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < v.nblk_lb; b += blockDim.x)
+// End of step t: reduce the per-block / per-particle stress partials, add
+// them to the compensated time sums, then advance the protocol to t+1.
+// FIN_BLOCKS blocks each reduce a slice into fin_part; the last block to
+// finish sums the slices in block order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_finalize(View v, double* fin_part, unsigned* fin_count) {
+  __shared__ double red[32 * 37];
+  __shared__ bool last;
+  double acc[37];
+  for (int k = 0; k < 37; ++k) acc[k] = 0.0;
+  const int G = gridDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = G * blockDim.x;
+  for (int b = tid; b < v.nblk_lb; b += nthr)
     for (int k = 0; k < 6; ++k) acc[k] += v.visc_part[6LL * b + k];
-  for (int i = threadIdx.x; i < v.n; i += blockDim.x) {
+  for (int i = tid; i < v.n; i += nthr) {
     for (int k = 0; k < 9; ++k) {
       acc[6 + k] += v.slet_part[9 * i + k];
       acc[15 + k] += v.cvir_part[9 * i + k];
+      acc[25 + k] += v.rvir_part[9 * i + k];
     }
     acc[24] += v.ncont_part[i];
   }
-  block_sum<double, 28>(acc, red);
-  // the repulsive virial separately (keeps the shared buffer small)
-  double racc[9];
-  for (int k = 0; k < 9; ++k) racc[k] = 0.0;
-  for (int i = threadIdx.x; i < v.n; i += blockDim.x)
-    for (int k = 0; k < 9; ++k) racc[k] += v.rvir_part[9 * i + k];
-  block_sum<double, 9>(racc, red);
+  block_sum<double, 37>(acc, red);
   if (threadIdx.x == 0) {
-    // visc partials: xx yy zz xy xz yz -> full 3x3
-    const double vs[9] = {acc[0], acc[3], acc[4], acc[3], acc[1], acc[5], acc[4], acc[5], acc[2]};
-    double* S = v.sums;
-    double* Cc = v.sums + 36;
-    for (int k = 0; k < 36; ++k) {
-      double x;
-      if (k < 9) x = vs[k];
-      else if (k < 18) x = acc[6 + (k - 9)];
-      else if (k < 27) x = v.move ? acc[15 + (k - 18)] : 0.0;
-      else x = v.move ? racc[k - 27] : 0.0;
-      const double y = x - Cc[k];
-      const double t = S[k] + y;
-      Cc[k] = (t - S[k]) - y;
-      S[k] = t;
-    }
-    v.counters[0] += 1ULL;
-    if (v.move) v.counters[1] += (unsigned long long)(acc[24] + 0.5);
-    // protocol: t -> t+1
-    Proto s = *v.proto;
-    s.t += 1;
-    s.delta = s.delta_n; s.delta_c = s.delta_nc; s.ule = s.ule_n;
-    s.delta_n = s.delta; s.delta_nc = s.delta_c;
-    kahan_le(s.delta_n, s.delta_nc, s.ule, v.nx);
-    s.ule_n = proto_increment(s, s.t + 1);
-    proto_derive(s, v.nx);
-    *v.proto = s;
+    for (int k = 0; k < 37; ++k) fin_part[FIN_VALS * blockIdx.x + k] = acc[k];
+    __threadfence();
+    last = (atomicAdd(fin_count, 1u) == (unsigned)G - 1);
   }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // column k of the slices, summed in block order by thread k
+  __shared__ double tot[37];
+  if (threadIdx.x < 37) {
+    double t = 0.0;
+    for (int b = 0; b < G; ++b) t += ((volatile double*)fin_part)[FIN_VALS * b + threadIdx.x];
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  *fin_count = 0u;
+  // visc partials: xx yy zz xy xz yz -> full 3x3
+  const double vs[9] = {tot[0], tot[3], tot[4], tot[3], tot[1], tot[5], tot[4], tot[5], tot[2]};
+  double* S = v.sums;
+  double* Cc = v.sums + 36;
+  for (int k = 0; k < 36; ++k) {
+    double x;
+    if (k < 9) x = vs[k];
+    else if (k < 18) x = tot[6 + (k - 9)];
+    else if (k < 27) x = v.move ? tot[15 + (k - 18)] : 0.0;
+    else x = v.move ? tot[25 + (k - 27)] : 0.0;
+    const double y = x - Cc[k];
+    const double t = S[k] + y;
+    Cc[k] = (t - S[k]) - y;
+    S[k] = t;
+  }
+  v.counters[0] += 1ULL;
+  if (v.move) v.counters[1] += (unsigned long long)(tot[24] + 0.5);
+  // protocol: t -> t+1
+  Proto s = *v.proto;
+  s.t += 1;
+  s.delta = s.delta_n; s.delta_c = s.delta_nc; s.ule = s.ule_n;
+  s.delta_n = s.delta; s.delta_nc = s.delta_c;
+  kahan_le(s.delta_n, s.delta_nc, s.ule, v.nx);
+  s.ule_n = proto_increment(s, s.t + 1);
+  proto_derive(s, v.nx);
+  *v.proto = s;
 }
 
 }  // namespace
@@ -319,12 +340,15 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.scale = (float)h->scale; v.inv_scale = (float)(1.0 / h->scale);
   v.omega_d = 1.0 / p->tau; v.vf_d = -(1.0 - 0.5 / p->tau);
   v.omega_f = (float)v.omega_d; v.vf_f = (float)v.vf_d; v.rho0_f = (float)p->rho0;
+  v.inv_nx_d = 1.0 / p->nx; v.inv_ny_d = 1.0 / p->ny; v.inv_nz_d = 1.0 / p->nz;
+  v.inv_nx_f = (float)v.inv_nx_d; v.inv_ny_f = (float)v.inv_ny_d; v.inv_nz_f = (float)v.inv_nz_d;
   v.mask = (uint32_t*)(w + L.mask); v.owner = (int*)(w + L.owner);
-  v.plane_mom = w + L.pm; v.visc_part = (double*)(w + L.visc); v.nblk_lb = lb_blocks(v.ncell);
+  v.plane_mom = w + L.pm; v.visc_part = (double*)(w + L.visc); v.nblk_lb = lb_grid_blocks((int)p->prec, p->nx, p->ny, p->nz);
   v.n = n;
   v.R = (double*)(w + L.R); v.U = (double*)(w + L.U); v.W = (double*)(w + L.W);
   v.rad = (double*)(w + L.rad); v.amap = (double*)(w + L.amap);
   v.mass = (double*)(w + L.mass); v.inert = (double*)(w + L.inert);
+  v.inv_m = (double*)(w + L.imass); v.inv_I = (double*)(w + L.iinert);
   v.plb = w + L.plb;
   v.Fh = (double*)(w + L.Fh); v.Th = (double*)(w + L.Th);
   v.Fcov = (double*)(w + L.Fcov); v.Tcov = (double*)(w + L.Tcov);
@@ -335,6 +359,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.link_cap = (int*)(w + L.lcap); v.link_cnt = (int*)(w + L.lcnt);
   v.ncx = L.ncx; v.ncy = L.ncy; v.ncz = L.ncz; v.brute = L.brute; v.ncells = L.ncells;
   v.csx = L.csx; v.csy = L.csy; v.csz = L.csz;
+  v.inv_csx = 1.0 / L.csx; v.inv_csy = 1.0 / L.csy; v.inv_csz = 1.0 / L.csz;
   v.cell_start = (int*)(w + L.cstart); v.cell_cnt = (int*)(w + L.ccnt);
   v.cell_ids = (int*)(w + L.cids); v.pcell = (int*)(w + L.pcell);
   v.K = HSLOTS;
@@ -398,6 +423,10 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
     cudaMemcpyAsync(v.amap, amap.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.mass, mass.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inert, inert.data(), 8 * n, cudaMemcpyHostToDevice, s);
+    std::vector<double> im(n), iI(n);
+    for (int i = 0; i < n; ++i) { im[i] = 1.0 / mass[i]; iI[i] = 1.0 / inert[i]; }
+    cudaMemcpyAsync(v.inv_m, im.data(), 8 * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(v.inv_I, iI.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.link_off, off.data(), 4 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.link_cap, cap.data(), 4 * n, cudaMemcpyHostToDevice, s);
     // synchronous copies above read pageable host memory; wait before the vectors go away
@@ -445,7 +474,7 @@ susp_status susp_step(susp* h, int nsteps, const susp_shear* sh) {
         h->parity ^= 1;
       }
     }
-    k_finalize<<<1, 256, 0, s>>>(v);
+    k_finalize<<<FIN_BLOCKS, 256, 0, s>>>(v, (double*)(h->ws + h->L.finp), (unsigned*)(h->ws + h->L.finc));
     launch_node_update(h->prec, v, h->fout, s);
     launch_links(h->prec, v, h->fout, s);
     std::swap(h->fin, h->fout);

@@ -15,7 +15,11 @@
 //              non-crossing links) and contributes the momentum exchange
 //              f = [2 n*_q(r) - 6 C^q rho0 (u_b . c_q)] c_q,  q = -p (Eq. 6),
 //              to F^h (Eq. 9), (r_b - R) x f to T^h (Eq. 10) and
-//              (r_b - R)_a f_b to the particle stresslet (sigma^h).
+//              (r_b - R)_a f_b to the particle stresslet (sigma^h).  A node
+//              of another particle in place of r counts as fluid at rest
+//              (f = 2 C^q rho0 c_q): when two mapped spheres come closer than
+//              one lattice spacing their solid nodes touch, and without this
+//              the rest pressure on each particle would not balance.
 // One block per particle scans the cells of the particle's bounding boxes
 // (one per Lees-Edwards image that reaches into the box).  Per-particle sums
 // use a fixed-order block reduction, so they are deterministic.
@@ -48,15 +52,30 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
   return total;
 }
 
-__device__ inline void box_cell(const View& v, const ImgBox (&b)[3], int t, int& x, int& y, int& z) {
-  int k = 0;
-  while (t >= b[k].cnt) { t -= b[k].cnt; ++k; }
-  const int lx = t % b[k].ex;
-  t /= b[k].ex;
-  const int ly = t % b[k].ey, lz = t / b[k].ey;
-  x = wrapi(b[k].x0 + lx, v.nx);
-  y = b[k].y0 + ly;
-  z = wrapi(b[k].z0 + lz, v.nz);
+// Visit the cells of a particle's image boxes: half-warps take (y, z) rows and
+// their 16 lanes run along x (coalesced).  fn(x, y, z, c, dx, dy, dz, k) gets
+// the cell index and the minimum-image displacement from the particle centre.
+template <typename TC, typename F>
+__device__ __forceinline__ void for_box_cells(const View& v, const ImgBox (&b)[3], TC Rx, TC Ry, TC Rz,
+                                              TC delta, F&& fn) {
+  const int lane = threadIdx.x & 15, half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
+#pragma unroll
+  for (int kb = 0; kb < 3; ++kb) {
+    const ImgBox B = b[kb];
+    if (B.cnt == 0) continue;
+    const int rows = B.ey * B.ez;
+    for (int row = half; row < rows; row += nhalf) {
+      const int lz = row / B.ey, ly = row - lz * B.ey;
+      const int y = B.y0 + ly, z = wrapi(B.z0 + lz, v.nz);
+      for (int lx = lane; lx < B.ex; lx += 16) {
+        const int x = wrapi(B.x0 + lx, v.nx);
+        TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
+        const int k = le_image_v(v, dx, dy, dz, delta);
+        const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
+        fn(x, y, z, c, dx, dy, dz, k);
+      }
+    }
+  }
 }
 
 template <typename TC>
@@ -74,19 +93,14 @@ __global__ void k_claim(View v) {
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto);
   ImgBox b[3];
-  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int x, y, z;
-    box_cell(v, b, t, x, y, z);
-    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
-    le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
     if (dx * dx + dy * dy + dz * dz < am * am) {
-      const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
       const int old = atomicCAS(v.owner + c, -1, i);
       if (old == -1) atomicOr(v.mask + c, 1u);
       else if (old != i) atomicOr(v.err, ERR_OVERLAP);
     }
-  }
+  });
 }
 
 template <int P>
@@ -107,16 +121,12 @@ __global__ void __launch_bounds__(256) k_uncover(View v, typename Store<P>::T* _
   const TC delta = pdelta<TC>(v.proto), ule = pule<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   ImgBox b[3];
-  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int x, y, z;
-    box_cell(v, b, t, x, y, z);
-    const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
-    if (v.owner[c] != i) continue;
-    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
-    const int k = le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
-    if (dx * dx + dy * dy + dz * dz < am * am) continue;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k) {
+    // only nodes outside the mapped sphere can leave it
+    if (dx * dx + dy * dy + dz * dz < am * am) return;
+    if (v.owner[c] != i) return;
     // solid node leaves the mapped sphere: fluid at rho0 and the boundary velocity
     const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
     const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(256) k_uncover(View v, typename Store<P>::T* _
     atomicAnd(v.mask + c, ~1u);
     acc[0] -= jx; acc[1] -= jy; acc[2] -= jz;
     acc[3] -= dy * jz - dz * jy; acc[4] -= dz * jx - dx * jz; acc[5] -= dx * jy - dy * jx;
-  }
+  });
   block_sum<TC, 6>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -153,19 +163,17 @@ __global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::
   const TC delta = pdelta<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   ImgBox b[3];
-  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int x, y, z;
-    box_cell(v, b, t, x, y, z);
-    const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
+  const TC inner = am > (TC)1 ? am - (TC)1 : (TC)0;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
+    const TC d2 = dx * dx + dy * dy + dz * dz;
+    // nodes deeper than a_map - 1 were inside before the move (speed < 0.5)
+    if (!(d2 < am * am) || d2 < inner * inner) return;
     const int own = v.owner[c];
-    if (own == i) continue;
-    TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
-    le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
-    if (!(dx * dx + dy * dy + dz * dz < am * am)) continue;
+    if (own == i) return;
     const int old = own == -1 ? atomicCAS(v.owner + c, -1, i) : own;
-    if (old != -1) { atomicOr(v.err, ERR_OVERLAP); continue; }
+    if (old != -1) { atomicOr(v.err, ERR_OVERLAP); return; }
     atomicOr(v.mask + c, 1u);
     TC jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::
     }
     acc[0] += jx; acc[1] += jy; acc[2] += jz;
     acc[3] += dy * jz - dz * jy; acc[4] += dz * jx - dx * jz; acc[5] += dx * jy - dy * jx;
-  }
+  });
   block_sum<TC, 6>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -185,10 +193,10 @@ __global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::
   }
 }
 
-// Fluid node that pulls population p from solid node (x, y, z); returns its
-// index or -1 if it is solid.  crossing = the pull passes a Lees-Edwards plane.
+// Node that pulls population p from solid node (x, y, z); returns its index
+// and owner.  crossing = the pull passes a Lees-Edwards plane.
 __device__ inline long long link_target(const View& v, const Proto* pr, int x, int y, int z, int p,
-                                        int& rx, int& ry, int& rz, bool& crossing) {
+                                        int& rx, int& ry, int& rz, bool& crossing, int& own) {
   const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
   ry = y + cpy;
   rz = wrapi(z + cpz, v.nz);
@@ -205,7 +213,8 @@ __device__ inline long long link_target(const View& v, const Proto* pr, int x, i
     rx = wrapi(x + cpx + pr->di + 1 - pr->near_hi, v.nx);
   }
   const long long r = rx + (long long)v.nx * (ry + (long long)v.ny * rz);
-  return v.owner[r] == -1 ? r : -1;
+  own = v.owner[r];
+  return r;
 }
 
 template <int P>
@@ -225,36 +234,55 @@ __global__ void __launch_bounds__(256) k_links(View v, const typename Store<P>::
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   const int off = v.link_off[i], cap = v.link_cap[i];
   ImgBox b[3];
-  const int total = particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[15];
 #pragma unroll
   for (int k = 0; k < 15; ++k) acc[k] = 0;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int x, y, z;
-    box_cell(v, b, t, x, y, z);
-    const long long s = x + (long long)v.nx * (y + (long long)v.ny * z);
-    if (v.owner[s] != i) continue;
+  // A link's receiver lies within sqrt(2) of its solid node, or -- across a
+  // Lees-Edwards plane, where the receiver is the node whose nearest source is
+  // s -- within sqrt(1.5^2 + 1) = 1.80; deeper solid nodes cannot have links.
+  const TC inner = am > (TC)2 ? am - (TC)2 : (TC)0;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int x, int y, int z, long long s, TC sdx, TC sdy, TC sdz, int) {
+    const TC d2 = sdx * sdx + sdy * sdy + sdz * sdz;
+    if (!(d2 < am * am) || d2 < inner * inner) return;
+    if (v.owner[s] != i) return;
     for (int p = 1; p < 19; ++p) {
-      int rx, ry, rz;
+      int rx, ry, rz, own;
       bool crossing;
-      const long long r = link_target(v, pr, x, y, z, p, rx, ry, rz, crossing);
-      if (r < 0) continue;
-      if (!crossing) {
-        atomicOr(v.mask + r, 1u << p);
-        const int slot = atomicAdd(&s_count, 1);
-        if (slot < cap) v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
+      const long long r = link_target(v, pr, x, y, z, p, rx, ry, rz, crossing, own);
+      // warp-aggregated slot in the particle's link segment (non-crossing fluid links)
+      const bool want = own < 0 && !crossing;
+      const unsigned act = __activemask();
+      const unsigned bal = __ballot_sync(act, want);
+      if (bal) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(bal) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&s_count, __popc(bal));
+        base = __shfl_sync(act, base, leader);
+        if (want) {
+          const int slot = base + __popc(bal & ((1u << lane) - 1u));
+          atomicOr(v.mask + r, 1u << p);
+          if (slot < cap) v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
+        }
       }
+      if (own == i) continue;
       const int q = D3Q19::opp(p);
       const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
       TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
-      const int k = le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
+      const int k = le_image_v(v, dx, dy, dz, delta);
       const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
       const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
       const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
       const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
-      const TC wq = (TC)D3Q19::w(q);
-      const TC nq = S::load(f, (long long)q * v.ncell + r, wq * rho0, (TC)v.inv_scale);
-      const TC mag = (TC)2 * nq - (TC)6 * wq * rho0 * cu;
+      const TC wqq = wq<TC>(q);
+      TC mag;
+      if (own < 0) {
+        const TC nq = S::load(f, (long long)q * v.ncell + r, wqq * rho0, (TC)v.inv_scale);
+        mag = (TC)2 * nq - (TC)6 * wqq * rho0 * cu;
+      } else {
+        mag = (TC)2 * wqq * rho0;   // another particle's node: fluid at rest
+      }
       const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
       acc[0] += fx; acc[1] += fy; acc[2] += fz;
       acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
@@ -262,7 +290,7 @@ __global__ void __launch_bounds__(256) k_links(View v, const typename Store<P>::
       acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
       acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
     }
-  }
+  });
   block_sum<TC, 15>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {

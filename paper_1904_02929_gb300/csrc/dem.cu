@@ -25,9 +25,9 @@ __global__ void k_cell_count(View v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   double x = v.R[3 * i], y = v.R[3 * i + 1], z = v.R[3 * i + 2];
-  x -= v.nx * floor(x / v.nx);
-  z -= v.nz * floor(z / v.nz);
-  int cx = (int)floor(x / v.csx), cy = (int)floor(y / v.csy), cz = (int)floor(z / v.csz);
+  x -= v.nx * floor(x * v.inv_nx_d);
+  z -= v.nz * floor(z * v.inv_nz_d);
+  int cx = (int)floor(x * v.inv_csx), cy = (int)floor(y * v.inv_csy), cz = (int)floor(z * v.inv_csz);
   cx = min(max(cx, 0), v.ncx - 1);
   cy = min(max(cy, 0), v.ncy - 1);
   cz = min(max(cz, 0), v.ncz - 1);
@@ -83,78 +83,99 @@ __global__ void k_cell_sort(View v) {
   }
 }
 
-__device__ inline void cross3(const double a[3], const double b[3], double o[3]) {
+template <typename T>
+__device__ inline void cross3(const T a[3], const T b[3], T o[3]) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
-__device__ inline double dot3(const double a[3], const double b[3]) {
+template <typename T>
+__device__ inline T dot3(const T a[3], const T b[3]) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+template <typename T>
 struct PairOut {
-  double Fa[3], Ta[3], Tb[3];   // total pair force on a (b gets -Fa), torques
-  double Fc[3];                 // contact part of Fa (for the virial)
-  double Fr[3];                 // double-layer part of Fa
-  double ht[3];                 // updated tangential spring
-  double fn;                    // normal-force magnitude (repulsive positive)
-  double d[3];                  // R_b - R_a (minimum image)
+  T Fa[3], Ta[3], Tb[3];   // total pair force on a (b gets -Fa), torques on a and b
+  T Fc[3];                 // contact part of Fa (for the virial)
+  T Fr[3];                 // double-layer part of Fa
+  T ht[3];                 // updated tangential spring
+  T fn;                    // normal-force magnitude (repulsive positive)
+  T d[3];                  // R_b - R_a (minimum image)
   int touching;
 };
 
-// Full interaction of the canonical pair (a, b); returns false if out of range.
-__device__ bool pair_interact(const View& v, int a, int b, const int* hcnt, const int* hpart,
-                              const double* hval, double delta, double ule, double dt, PairOut& o) {
-  double d[3] = {v.R[3 * b] - v.R[3 * a], v.R[3 * b + 1] - v.R[3 * a + 1], v.R[3 * b + 2] - v.R[3 * a + 2]};
-  const int k = (int)floor(d[1] / v.ny + 0.5);
+// Minimum-image displacement R_b - R_a in FP64 (positions are FP64 on every
+// path); returns false when the pair is out of range.
+__device__ inline bool pair_geometry(const View& v, int a, int b, double delta, double d[3], int& k,
+                                     double& h) {
+  d[0] = v.R[3 * b] - v.R[3 * a];
+  d[1] = v.R[3 * b + 1] - v.R[3 * a + 1];
+  d[2] = v.R[3 * b + 2] - v.R[3 * a + 2];
+  k = (int)floor(d[1] * v.inv_ny_d + 0.5);
   d[1] -= k * (double)v.ny;
   d[0] -= k * delta;
-  d[0] -= v.nx * floor(d[0] / v.nx + 0.5);
-  d[2] -= v.nz * floor(d[2] / v.nz + 0.5);
-  const double ra = v.rad[a], rb = v.rad[b];
-  const double dist = sqrt(dot3(d, d));
-  const double h = dist - ra - rb;
-  if (!(h < v.hrange) && !(h < 0.0)) return false;
-  const double uab[3] = {v.U[3 * a] - v.U[3 * b] - k * ule, v.U[3 * a + 1] - v.U[3 * b + 1],
-                         v.U[3 * a + 2] - v.U[3 * b + 2]};
-  const double* wa = v.W + 3 * a;
-  const double* wb = v.W + 3 * b;
-  const double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+  d[0] -= v.nx * floor(d[0] * v.inv_nx_d + 0.5);
+  d[2] -= v.nz * floor(d[2] * v.inv_nz_d + 0.5);
+  const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double rsum = v.rad[a] + v.rad[b];
+  const double lim = rsum + v.hrange + 1e-9;
+  if (!(d2 < lim * lim)) return false;   // cheap rejection before the square root
+  h = sqrt(d2) - rsum;
+  return (h < v.hrange) || (h < 0.0);
+}
+
+// Full interaction of the canonical pair (a, b) in precision T, given the
+// minimum-image displacement.
+template <typename T>
+__device__ void pair_interact(const View& v, int a, int b, const double dd[3], int k, double hd,
+                              const int* hcnt, const int* hpart, const double* hval, T ule, T dt,
+                              PairOut<T>& o) {
+  const T d[3] = {(T)dd[0], (T)dd[1], (T)dd[2]};
+  const T ra = (T)v.rad[a], rb = (T)v.rad[b];
+  const T dist = sqrt(dot3(d, d));
+  const T h = (T)hd;
+  const T uab[3] = {(T)(v.U[3 * a] - v.U[3 * b]) - (T)k * ule, (T)(v.U[3 * a + 1] - v.U[3 * b + 1]),
+                    (T)(v.U[3 * a + 2] - v.U[3 * b + 2])};
+  const T wa[3] = {(T)v.W[3 * a], (T)v.W[3 * a + 1], (T)v.W[3 * a + 2]};
+  const T wb[3] = {(T)v.W[3 * b], (T)v.W[3 * b + 1], (T)v.W[3 * b + 2]};
+  const T n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
   for (int c = 0; c < 3; ++c) {
-    o.Fa[c] = o.Ta[c] = o.Tb[c] = o.Fc[c] = o.Fr[c] = o.ht[c] = 0.0;
+    o.Fa[c] = o.Ta[c] = o.Tb[c] = o.Fc[c] = o.Fr[c] = o.ht[c] = (T)0;
     o.d[c] = d[c];
   }
-  o.fn = 0.0;
+  o.fn = (T)0;
   o.touching = 0;
   // ---- contact
-  const double overlap = ra + rb - dist;
-  if (overlap > 0.0) {
-    double ht[3] = {0.0, 0.0, 0.0};
+  const T overlap = ra + rb - dist;
+  if (hd < 0.0) {
+    T ht[3] = {0, 0, 0};
     const int m = hcnt[a];
     for (int s = 0; s < m; ++s)
       if (hpart[a * v.K + s] == b) {
-        for (int c = 0; c < 3; ++c) ht[c] = hval[3 * (a * v.K + s) + c];
+        for (int c = 0; c < 3; ++c) ht[c] = (T)hval[3 * (a * v.K + s) + c];
         break;
       }
-    const double ws[3] = {ra * wa[0] + rb * wb[0], ra * wa[1] + rb * wb[1], ra * wa[2] + rb * wb[2]};
-    double rot[3];
+    const T ws[3] = {ra * wa[0] + rb * wb[0], ra * wa[1] + rb * wb[1], ra * wa[2] + rb * wb[2]};
+    T rot[3];
     cross3(ws, n, rot);
-    const double vv[3] = {uab[0] + rot[0], uab[1] + rot[1], uab[2] + rot[2]};
-    const double vn = dot3(vv, n);
-    const double vt[3] = {vv[0] - vn * n[0], vv[1] - vn * n[1], vv[2] - vn * n[2]};
-    const double fn = v.kn * overlap + v.eta_n * vn;
-    const double hn = dot3(ht, n);
+    const T vv[3] = {uab[0] + rot[0], uab[1] + rot[1], uab[2] + rot[2]};
+    const T vn = dot3(vv, n);
+    const T vt[3] = {vv[0] - vn * n[0], vv[1] - vn * n[1], vv[2] - vn * n[2]};
+    const T kn = (T)v.kn, kt = (T)v.kt;
+    const T fn = kn * overlap + (T)v.eta_n * vn;
+    const T hn = dot3(ht, n);
     for (int c = 0; c < 3; ++c) ht[c] = ht[c] - hn * n[c] + vt[c] * dt;
-    double ft[3] = {-v.kt * ht[0], -v.kt * ht[1], -v.kt * ht[2]};
-    const double ftm = sqrt(dot3(ft, ft));
-    const double cap = v.mu * fabs(fn);
-    if (ftm >= cap && ftm > 0.0) {
+    T ft[3] = {-kt * ht[0], -kt * ht[1], -kt * ht[2]};
+    const T ftm = sqrt(dot3(ft, ft));
+    const T cap = (T)v.mu * fabs(fn);
+    if (ftm >= cap && ftm > (T)0) {
       for (int c = 0; c < 3; ++c) {
         ft[c] = cap * ft[c] / ftm;
-        ht[c] = -ft[c] / v.kt;
+        ht[c] = -ft[c] / kt;
       }
     }
-    double tq[3];
+    T tq[3];
     cross3(n, ft, tq);
     for (int c = 0; c < 3; ++c) {
       o.Fc[c] = -fn * n[c] + ft[c];
@@ -167,85 +188,104 @@ __device__ bool pair_interact(const View& v, int a, int b, const int* hcnt, cons
     o.touching = 1;
   }
   // ---- double-layer repulsion
-  if (v.F0 > 0.0 && h < 10.0 * v.debye) {
-    const double fr = v.F0 * exp(-(h > 0.0 ? h : 0.0) / v.debye);
+  if (v.F0 > 0.0 && hd < 10.0 * v.debye) {
+    const T fr = (T)v.F0 * exp(-(h > (T)0 ? h : (T)0) / (T)v.debye);
     for (int c = 0; c < 3; ++c) {
       o.Fr[c] = -fr * n[c];
       o.Fa[c] += o.Fr[c];
     }
   }
   // ---- lubrication correction
-  if (v.lub_cut > 0.0 && h < v.lub_cut) {
-    const double hh = h < 0.0 ? 0.0 : h;
-    const double sc = 2.0 / (ra + rb);
-    const double xi = sc * hh, xc = sc * v.lub_cut, dl = sc * v.lub_delta;
-    const double inv = 1.0 / (xi + dl) - 1.0 / (xc + dl);
-    const double lg = log((xc + dl) / (xi + dl));
-    const double be = rb / ra, bj = ra / rb;
-    const double pi = 3.14159265358979323846;
-    const double e0 = v.eta0;
-    const double op = 1.0 + be, oq = 1.0 + bj;
-    const double XA = e0 * 6.0 * pi * ra * (2.0 * be * be / (op * op * op)) * inv;
-    const double YA = e0 * 6.0 * pi * ra * (4.0 * be * (2.0 + be + 2.0 * be * be) / (15.0 * op * op * op)) * lg;
-    const double YBa = e0 * 4.0 * pi * ra * ra * (be * (4.0 + be) / (5.0 * op * op)) * lg;
-    const double YBb = e0 * 4.0 * pi * rb * rb * (bj * (4.0 + bj) / (5.0 * oq * oq)) * lg;
-    const double YCaa = e0 * 8.0 * pi * ra * ra * ra * (2.0 * be / (5.0 * op)) * lg;
-    const double YCbb = e0 * 8.0 * pi * rb * rb * rb * (2.0 * bj / (5.0 * oq)) * lg;
-    const double YCab = e0 * 8.0 * pi * ra * ra * ra * (be * be / (10.0 * op)) * lg;
-    const double un = dot3(uab, n);
-    double wan[3], wbn[3], nxu[3];
+  if (v.lub_cut > 0.0 && hd < v.lub_cut) {
+    const T hh = h < (T)0 ? (T)0 : h;
+    const T sc = (T)2 / (ra + rb);
+    const T xi = sc * hh, xc = sc * (T)v.lub_cut, dl = sc * (T)v.lub_delta;
+    const T inv = (T)1 / (xi + dl) - (T)1 / (xc + dl);
+    const T lg = log((xc + dl) / (xi + dl));
+    const T be = rb / ra, bj = ra / rb;
+    const T pi = (T)3.14159265358979323846;
+    const T e0 = (T)v.eta0;
+    const T op = (T)1 + be, oq = (T)1 + bj;
+    const T XA = e0 * (T)6 * pi * ra * ((T)2 * be * be / (op * op * op)) * inv;
+    const T YA = e0 * (T)6 * pi * ra * ((T)4 * be * ((T)2 + be + (T)2 * be * be) / ((T)15 * op * op * op)) * lg;
+    const T YBa = e0 * (T)4 * pi * ra * ra * (be * ((T)4 + be) / ((T)5 * op * op)) * lg;
+    const T YBb = e0 * (T)4 * pi * rb * rb * (bj * ((T)4 + bj) / ((T)5 * oq * oq)) * lg;
+    const T YCaa = e0 * (T)8 * pi * ra * ra * ra * ((T)2 * be / ((T)5 * op)) * lg;
+    const T YCbb = e0 * (T)8 * pi * rb * rb * rb * ((T)2 * bj / ((T)5 * oq)) * lg;
+    const T YCab = e0 * (T)8 * pi * ra * ra * ra * (be * be / ((T)10 * op)) * lg;
+    const T un = dot3(uab, n);
+    T wan[3], wbn[3], nxu[3];
     cross3(wa, n, wan);
     cross3(wb, n, wbn);
     cross3(n, uab, nxu);
-    const double wap = dot3(wa, n), wbp = dot3(wb, n);
+    const T wap = dot3(wa, n), wbp = dot3(wb, n);
     for (int c = 0; c < 3; ++c) {
-      const double ut = uab[c] - un * n[c];
+      const T ut = uab[c] - un * n[c];
       o.Fa[c] += -XA * un * n[c] - YA * ut - YBa * wan[c] - YBb * wbn[c];
-      const double wat = wa[c] - wap * n[c], wbt = wb[c] - wbp * n[c];
+      const T wat = wa[c] - wap * n[c], wbt = wb[c] - wbp * n[c];
       o.Ta[c] += -YBa * nxu[c] - YCaa * wat - YCab * wbt;
       o.Tb[c] += -YBb * nxu[c] - YCbb * wbt - YCab * wat;
     }
   }
-  return true;
 }
 
+template <typename T>
+__device__ inline T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// One warp per particle i; the lanes split the candidate partners (one
+// neighbour cell per lane, or a strided slice of all particles in brute-force
+// mode).  Forces are summed per lane and reduced across the warp.
+template <typename T>
 __global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ hcnt_old,
                                                const int* __restrict__ hpart_old,
                                                const double* __restrict__ hval_old, int* hcnt_new,
-                                               int* hpart_new, double* hval_new, double dt, int sample) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+                                               int* hpart_new, double* hval_new, double dt_d, int sample) {
+  __shared__ int s_slot[4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * 4 + wib;
+  if (lane == 0) s_slot[wib] = 0;
+  __syncwarp();
   if (i >= v.n) return;
   const Proto* pr = v.proto;
-  const double delta = pr->delta, ule = pr->ule;
-  double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-  double cv[9], rv[9];
-  for (int c = 0; c < 9; ++c) { cv[c] = 0.0; rv[c] = 0.0; }
-  int nnew = 0, ncont = 0;
+  const double delta = pr->delta;
+  const T ule = (T)pr->ule;
+  const T dt = (T)dt_d;
+  T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
+  T cv[9], rv[9];
+  for (int c = 0; c < 9; ++c) { cv[c] = (T)0; rv[c] = (T)0; }
+  int ncont = 0;
   const double pi = 3.14159265358979323846;
   const double dth = pi / v.nbins;
 
   auto visit = [&](int j) {
     if (j == i) return;
     const int a = i < j ? i : j, b = i < j ? j : i;
-    PairOut o;
-    if (!pair_interact(v, a, b, hcnt_old, hpart_old, hval_old, delta, ule, dt, o)) return;
+    double dd[3], hd;
+    int k;
+    if (!pair_geometry(v, a, b, delta, dd, k, hd)) return;
+    PairOut<T> o;
+    pair_interact<T>(v, a, b, dd, k, hd, hcnt_old, hpart_old, hval_old, ule, dt, o);
     if (i == a) {
-      for (int c = 0; c < 3; ++c) { F[c] += o.Fa[c]; T[c] += o.Ta[c]; }
+      for (int c = 0; c < 3; ++c) { F[c] += o.Fa[c]; Tq[c] += o.Ta[c]; }
       if (o.touching) {
-        if (nnew < v.K) {
-          hpart_new[a * v.K + nnew] = b;
-          for (int c = 0; c < 3; ++c) hval_new[3 * (a * v.K + nnew) + c] = o.ht[c];
-          ++nnew;
+        const int slot = atomicAdd(&s_slot[wib], 1);
+        if (slot < v.K) {
+          hpart_new[a * v.K + slot] = b;
+          for (int c = 0; c < 3; ++c) hval_new[3 * (a * v.K + slot) + c] = (double)o.ht[c];
         } else {
           atomicOr(v.err, ERR_PAIRS);
         }
       }
       if (sample) {
-        const double r[3] = {-o.d[0], -o.d[1], -o.d[2]};
+        const T r[3] = {-o.d[0], -o.d[1], -o.d[2]};
         if (o.touching) {
           for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) cv[3 * x + y] += 0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
-          double th = atan2(r[1], r[0]);
+            for (int y = 0; y < 3; ++y) cv[3 * x + y] += (T)0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
+          double th = atan2((double)r[1], (double)r[0]);
           const double tx = -sin(th), ty = cos(th);
           if (th < 0.0) th += pi;
           if (th >= pi) th -= pi;
@@ -253,51 +293,57 @@ __global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ h
           if (bin >= v.nbins) bin = v.nbins - 1;
           if (bin < 0) bin = 0;
           atomicAdd(v.hist + 3 * bin, 1.0);
-          atomicAdd(v.hist + 3 * bin + 1, o.fn);
-          atomicAdd(v.hist + 3 * bin + 2, o.Fc[0] * tx + o.Fc[1] * ty);
+          atomicAdd(v.hist + 3 * bin + 1, (double)o.fn);
+          atomicAdd(v.hist + 3 * bin + 2, (double)o.Fc[0] * tx + (double)o.Fc[1] * ty);
           ++ncont;
         }
         if (v.F0 > 0.0)
           for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) rv[3 * x + y] += 0.5 * (r[x] * o.Fr[y] + r[y] * o.Fr[x]);
+            for (int y = 0; y < 3; ++y) rv[3 * x + y] += (T)0.5 * (r[x] * o.Fr[y] + r[y] * o.Fr[x]);
       }
     } else {
-      for (int c = 0; c < 3; ++c) { F[c] -= o.Fa[c]; T[c] += o.Tb[c]; }
+      for (int c = 0; c < 3; ++c) { F[c] -= o.Fa[c]; Tq[c] += o.Tb[c]; }
     }
   };
 
   if (v.brute) {
-    for (int j = 0; j < v.n; ++j) visit(j);
-  } else {
-    double x = v.R[3 * i], y = v.R[3 * i + 1], z = v.R[3 * i + 2];
-    x -= v.nx * floor(x / v.nx);
-    z -= v.nz * floor(z / v.nz);
-    const int cy = min(max((int)floor(y / v.csy), 0), v.ncy - 1);
-    const int cz = min(max((int)floor(z / v.csz), 0), v.ncz - 1);
+    for (int j = lane; j < v.n; j += 32) visit(j);
+  } else if (lane < 27) {
+    const int dyc = lane / 9 - 1, dxc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
     const int zlo = v.ncz >= 3 ? -1 : 0, zhi = v.ncz >= 2 ? 1 : 0;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int yc = cy + dy;
+    if (dzc >= zlo && dzc <= zhi) {
+      double x = v.R[3 * i], y = v.R[3 * i + 1], z = v.R[3 * i + 2];
+      x -= v.nx * floor(x * v.inv_nx_d);
+      z -= v.nz * floor(z * v.inv_nz_d);
+      const int cy = min(max((int)floor(y * v.inv_csy), 0), v.ncy - 1);
+      const int cz = min(max((int)floor(z * v.inv_csz), 0), v.ncz - 1);
+      int yc = cy + dyc;
       double xs = x;
       if (yc < 0) { yc += v.ncy; xs = x + delta; }
       else if (yc >= v.ncy) { yc -= v.ncy; xs = x - delta; }
-      xs -= v.nx * floor(xs / v.nx);
-      const int cxs = min(max((int)floor(xs / v.csx), 0), v.ncx - 1);
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xc = wrapi(cxs + dx, v.ncx);
-        for (int dz = zlo; dz <= zhi; ++dz) {
-          const int zc = wrapi(cz + dz, v.ncz);
-          const int c = xc + v.ncx * (yc + v.ncy * zc);
-          const int s = v.cell_start[c], e = v.cell_start[c + 1];
-          for (int t = s; t < e; ++t) visit(v.cell_ids[t]);
-        }
-      }
+      xs -= v.nx * floor(xs * v.inv_nx_d);
+      const int cxs = min(max((int)floor(xs * v.inv_csx), 0), v.ncx - 1);
+      const int xc = wrapi(cxs + dxc, v.ncx);
+      const int zc = wrapi(cz + dzc, v.ncz);
+      const int c = xc + v.ncx * (yc + v.ncy * zc);
+      const int s0 = v.cell_start[c], e0 = v.cell_start[c + 1];
+      for (int t = s0; t < e0; ++t) visit(v.cell_ids[t]);
     }
   }
-  for (int c = 0; c < 3; ++c) { v.Fp[3 * i + c] = F[c]; v.Tp[3 * i + c] = T[c]; }
-  hcnt_new[i] = nnew;
+  for (int c = 0; c < 3; ++c) { F[c] = warp_sum(F[c]); Tq[c] = warp_sum(Tq[c]); }
   if (sample) {
-    for (int c = 0; c < 9; ++c) { v.cvir_part[9 * i + c] = cv[c]; v.rvir_part[9 * i + c] = rv[c]; }
-    v.ncont_part[i] = ncont;
+    for (int c = 0; c < 9; ++c) { cv[c] = warp_sum(cv[c]); rv[c] = warp_sum(rv[c]); }
+    for (int o = 16; o > 0; o >>= 1) ncont += __shfl_xor_sync(0xffffffffu, ncont, o);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int c = 0; c < 3; ++c) { v.Fp[3 * i + c] = (double)F[c]; v.Tp[3 * i + c] = (double)Tq[c]; }
+    const int m = s_slot[wib];
+    hcnt_new[i] = m < v.K ? m : v.K;
+    if (sample) {
+      for (int c = 0; c < 9; ++c) { v.cvir_part[9 * i + c] = (double)cv[c]; v.rvir_part[9 * i + c] = (double)rv[c]; }
+      v.ncont_part[i] = ncont;
+    }
   }
 }
 
@@ -317,12 +363,12 @@ __global__ void k_integrate(View v, double dt, int last, int plb_double) {
   double* R = v.R + 3 * i;
   double* U = v.U + 3 * i;
   double* W = v.W + 3 * i;
-  const double m = v.mass[i], I = v.inert[i];
+  const double im = v.inv_m[i], iI = v.inv_I[i];
   for (int c = 0; c < 3; ++c) {
     const double F = v.Fh[3 * i + c] + v.Fcov[3 * i + c] + v.Fp[3 * i + c];
     const double T = v.Th[3 * i + c] + v.Tcov[3 * i + c] + v.Tp[3 * i + c];
-    U[c] += dt * F / m;
-    W[c] += dt * T / I;
+    U[c] += dt * F * im;
+    W[c] += dt * T * iI;
   }
   if (v.quasi2d) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
   for (int c = 0; c < 3; ++c) R[c] += dt * U[c];
@@ -354,11 +400,14 @@ void launch_write_plb(const View& v, int plb_double, cudaStream_t s) {
   k_write_plb<<<(v.n + 127) / 128, 128, 0, s>>>(v, plb_double);
 }
 
-// One particle sub-step: cell list, pair interactions, integration.
+// One particle sub-step: (at sub-step 0) the cell list, then the pair
+// interactions and the integration.  The cell list stays valid over the
+// sub-steps of a lattice step: the cells are at least one lattice unit larger
+// than the interaction range and a particle moves less than 0.5 per step.
 void launch_dem_substep(const View& v, int parity, int sub, int plb_double, cudaStream_t s) {
   if (v.n == 0) return;
   const int nb = (v.n + 127) / 128;
-  if (!v.brute) {
+  if (!v.brute && sub == 0) {
     cudaMemsetAsync(v.cell_cnt, 0, sizeof(int) * v.ncells, s);
     k_cell_count<<<nb, 128, 0, s>>>(v);
     k_cell_scan<<<1, 1024, 0, s>>>(v);
@@ -372,6 +421,10 @@ void launch_dem_substep(const View& v, int parity, int sub, int plb_double, cuda
   int* hp_new = parity ? v.hpart0 : v.hpart1;
   double* hv_new = parity ? v.hval0 : v.hval1;
   const double dt = 1.0 / v.nsub;
-  k_pairs<<<nb, 128, 0, s>>>(v, hc_old, hp_old, hv_old, hc_new, hp_new, hv_new, dt, sub == 0);
+  const int pb = (v.n + 3) / 4;
+  if (plb_double)
+    k_pairs<double><<<pb, 128, 0, s>>>(v, hc_old, hp_old, hv_old, hc_new, hp_new, hv_new, dt, sub == 0);
+  else
+    k_pairs<float><<<pb, 128, 0, s>>>(v, hc_old, hp_old, hv_old, hc_new, hp_new, hv_new, dt, sub == 0);
   k_integrate<<<nb, 128, 0, s>>>(v, dt, sub == v.nsub - 1, plb_double);
 }

@@ -24,31 +24,32 @@
 
 namespace susp_dev {
 
-template <int P>
-__device__ __forceinline__ typename Store<P>::C bounce_value(
-    const View& v, const typename Store<P>::C* __restrict__ plb, int i, int x, int y, int z, int q,
-    typename Store<P>::C nq_self, typename Store<P>::C delta, typename Store<P>::C ule,
-    typename Store<P>::C rho0) {
-  using TC = typename Store<P>::C;
+// Moving-wall term of Eq. 7 for the population p pulled at node (x, y, z)
+// from the solid node r - c_p of particle i:  -6 C^q rho0 (u_b . c_q) with
+// q = -p, u_b = U + Omega x (r_b - R) at r_b = r + c_q / 2 (Eq. 8).
+template <typename TC>
+__device__ __forceinline__ TC wall_term(const View& v, const TC* __restrict__ plb, int i, int x, int y,
+                                        int z, int q, TC delta, TC ule, TC rho0) {
   const TC* pp = plb + 12 * i;
-  TC dx = (TC)x + (TC)0.5 * (TC)D3Q19::cx(q) - pp[0];
-  TC dy = (TC)y + (TC)0.5 * (TC)D3Q19::cy(q) - pp[1];
-  TC dz = (TC)z + (TC)0.5 * (TC)D3Q19::cz(q) - pp[2];
-  int k = le_image(dx, dy, dz, delta, v.nx, v.ny, v.nz);
-  TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
-  TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
-  TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
-  TC cu = ubx * (TC)D3Q19::cx(q) + uby * (TC)D3Q19::cy(q) + ubz * (TC)D3Q19::cz(q);
-  return nq_self - (TC)6 * (TC)D3Q19::w(q) * rho0 * cu;
+  const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+  TC dx = (TC)x + (TC)0.5 * cqx - pp[0];
+  TC dy = (TC)y + (TC)0.5 * cqy - pp[1];
+  TC dz = (TC)z + (TC)0.5 * cqz - pp[2];
+  const int k = le_image_v(v, dx, dy, dz, delta);
+  const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+  const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+  const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+  const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
+  return -(TC)6 * wq<TC>(q) * rho0 * cu;
 }
 
 // Pull across a Lees-Edwards plane (direction p with c_py = +1 at y = 0, or
 // c_py = -1 at y = ny-1).
 template <int P, int p>
-__device__ __noinline__ typename Store<P>::C le_pull(const View v, const typename Store<P>::T* __restrict__ fin,
-                                                     const typename Store<P>::C* __restrict__ plb,
-                                                     const Proto* __restrict__ pr, int x, int y, int z,
-                                                     long long idx) {
+__device__ __forceinline__ typename Store<P>::C le_pull(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                                        const typename Store<P>::C* __restrict__ plb,
+                                                        const Proto* __restrict__ pr, int x, int y, int z,
+                                                        long long idx) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   const int nx = v.nx, ny = v.ny;
@@ -74,8 +75,8 @@ __device__ __noinline__ typename Store<P>::C le_pull(const View v, const typenam
   const TC base_q = (TC)D3Q19::w(q) * rho0;
   const int on = v.owner[in_];
   if (on >= 0) {
-    TC self = S::load(fin, (long long)q * nc + idx, base_q, (TC)v.inv_scale);
-    return bounce_value<P>(v, plb, on, x, y, z, q, self, delta, ule, rho0);
+    const TC self = S::load(fin, (long long)q * nc + idx, base_q, (TC)v.inv_scale);
+    return self + wall_term<TC>(v, plb, on, x, y, z, q, delta, ule, rho0);
   }
   const TC* pm = reinterpret_cast<const TC*>(v.plane_mom) + (below ? 4LL * v.nz * nx : 0);
   const long long k0 = 4LL * (c0x + (long long)nx * sz), k1 = 4LL * (c1x + (long long)nx * sz);
@@ -99,112 +100,173 @@ __device__ __noinline__ typename Store<P>::C le_pull(const View v, const typenam
   return val;
 }
 
-template <int P, int p>
+// Plain pull of population p, or (mask bit p set) the node's own population q
+// = -p, which becomes the bounce-back value once the wall term is added.
+template <int P, int p, bool BND>
 __device__ __forceinline__ void pull_one(const View& v, const typename Store<P>::T* __restrict__ fin,
                                          const typename Store<P>::C* __restrict__ plb,
                                          const Proto* __restrict__ pr, uint32_t m, int x, int y,
                                          int z, int xm, int xp, int zm, int zp, long long idx,
-                                         typename Store<P>::C delta, typename Store<P>::C ule,
-                                         typename Store<P>::C (&n)[19]) {
+                                         typename Store<P>::C rho0, typename Store<P>::C (&n)[19]) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
   constexpr int q = D3Q19::opp(p);
   const int sy = y - cpy;
-  if (cpy != 0 && (sy < 0 || sy >= v.ny)) {
+  if (BND && cpy != 0 && (sy < 0 || sy >= v.ny)) {
     n[p] = le_pull<P, p>(v, fin, plb, pr, x, y, z, idx);
     return;
   }
-  const int sx = cpx == 1 ? xm : (cpx == -1 ? xp : x);
-  const int sz = cpz == 1 ? zm : (cpz == -1 ? zp : z);
-  const long long sidx = sx + (long long)v.nx * (sy + (long long)v.ny * sz);
   const long long nc = v.ncell;
-  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   if ((m >> p) & 1u) {
-    const int i = v.owner[sidx];
-    const TC self = S::load(fin, (long long)q * nc + idx, (TC)D3Q19::w(q) * rho0, (TC)v.inv_scale);
-    n[p] = bounce_value<P>(v, plb, i, x, y, z, q, self, delta, ule, rho0);
+    n[p] = S::load(fin, (long long)q * nc + idx, (TC)D3Q19::w(q) * rho0, (TC)v.inv_scale);
   } else {
+    const int sx = cpx == 1 ? xm : (cpx == -1 ? xp : x);
+    const int sz = cpz == 1 ? zm : (cpz == -1 ? zp : z);
+    const long long sidx = sx + (long long)v.nx * (sy + (long long)v.ny * sz);
     n[p] = S::load(fin, (long long)p * nc + sidx, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
   }
 }
 
-template <int P, int p>
+template <int P, int p, bool BND>
 struct PullAll {
   __device__ __forceinline__ static void run(const View& v, const typename Store<P>::T* __restrict__ fin,
                                              const typename Store<P>::C* __restrict__ plb,
                                              const Proto* __restrict__ pr, uint32_t m, int x, int y,
                                              int z, int xm, int xp, int zm, int zp, long long idx,
-                                             typename Store<P>::C delta, typename Store<P>::C ule,
-                                             typename Store<P>::C (&n)[19]) {
-    pull_one<P, p>(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, delta, ule, n);
-    PullAll<P, p + 1>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, delta, ule, n);
+                                             typename Store<P>::C rho0, typename Store<P>::C (&n)[19]) {
+    pull_one<P, p, BND>(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
+    PullAll<P, p + 1, BND>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
   }
 };
-template <int P>
-struct PullAll<P, 19> {
+template <int P, bool BND>
+struct PullAll<P, 19, BND> {
   __device__ __forceinline__ static void run(const View&, const typename Store<P>::T* __restrict__,
                                              const typename Store<P>::C* __restrict__,
                                              const Proto* __restrict__, uint32_t, int, int, int, int,
                                              int, int, int, long long, typename Store<P>::C,
-                                             typename Store<P>::C, typename Store<P>::C (&)[19]) {}
+                                             typename Store<P>::C (&)[19]) {}
 };
 
+template <typename TC>
+__device__ __forceinline__ void add_at(TC (&n)[19], int p, TC val) {
+  switch (p) {
+#define SUSP_ADD_CASE(k) case k: n[k] += val; break;
+    SUSP_ADD_CASE(1) SUSP_ADD_CASE(2) SUSP_ADD_CASE(3) SUSP_ADD_CASE(4) SUSP_ADD_CASE(5)
+    SUSP_ADD_CASE(6) SUSP_ADD_CASE(7) SUSP_ADD_CASE(8) SUSP_ADD_CASE(9) SUSP_ADD_CASE(10)
+    SUSP_ADD_CASE(11) SUSP_ADD_CASE(12) SUSP_ADD_CASE(13) SUSP_ADD_CASE(14) SUSP_ADD_CASE(15)
+    SUSP_ADD_CASE(16) SUSP_ADD_CASE(17) SUSP_ADD_CASE(18)
+#undef SUSP_ADD_CASE
+    default: break;
+  }
+}
+
+// Directions whose pull crosses a Lees-Edwards plane at y = 0 (c_py = +1) and
+// at y = ny-1 (c_py = -1); their mask bits are never set.
+__host__ __device__ constexpr uint32_t crossing_bits(int sign) {
+  uint32_t b = 0;
+  for (int p = 1; p < 19; ++p)
+    if (D3Q19::cy(p) == sign) b |= 1u << p;
+  return b;
+}
+
+// One lattice node: pull (Eq. 3) with bounce-back (Eq. 7) and Lees-Edwards
+// planes, BGK collision (Eq. 4, 5), store, viscous-stress accumulation.
+// BND: the node lies on a Lees-Edwards plane (y = 0 or ny-1); interior rows
+// compile without the plane code.
+template <int P, bool BND>
+__device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                        typename Store<P>::T* __restrict__ fout, int x, int y, int z,
+                                        typename Store<P>::C (&acc)[6]) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  const int nx = v.nx;
+  const long long idx = x + (long long)nx * (y + (long long)v.ny * z);
+  const long long nc = v.ncell;
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  const uint32_t m = v.mask[idx];
+  if (m & 1u) {
+    // solid node: its populations are undefined; writing the rest state keeps
+    // every stored sector complete (no read-for-ownership of partial sectors)
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      fout[(long long)q * nc + idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+    return;
+  }
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int zm = z == 0 ? v.nz - 1 : z - 1, zp = z == v.nz - 1 ? 0 : z + 1;
+  const Proto* pr = v.proto;
+  const TC* plb = reinterpret_cast<const TC*>(v.plb);
+  TC n[19];
+  n[0] = S::load(fin, idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
+  PullAll<P, 1, BND>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
+  // moving-wall terms of the bounce-back links (few per node, one code copy)
+  uint32_t links = m & ~1u;
+  if (BND) {
+    if (y == 0) links &= ~crossing_bits(1);
+    if (y == v.ny - 1) links &= ~crossing_bits(-1);
+  }
+  if (links) {
+    const TC delta = sel<TC>(pr->delta, pr->delta_f), ule = sel<TC>(pr->ule, pr->ule_f);
+    while (links) {
+      const int p = __ffs(links) - 1;
+      links &= links - 1;
+      const int sx = wrapi(x - D3Q19::cx(p), nx), sy = y - D3Q19::cy(p), sz = wrapi(z - D3Q19::cz(p), v.nz);
+      const int i = v.owner[sx + (long long)nx * (sy + (long long)v.ny * sz)];
+      add_at(n, p, wall_term<TC>(v, plb, i, x, y, z, D3Q19::opp(p), delta, ule, rho0));
+    }
+  }
+  TC rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    const TC cxq = (TC)D3Q19::cx(q), cyq = (TC)D3Q19::cy(q), czq = (TC)D3Q19::cz(q);
+    rho += n[q];
+    jx += n[q] * cxq; jy += n[q] * cyq; jz += n[q] * czq;
+    pxx += n[q] * cxq * cxq; pyy += n[q] * cyq * cyq; pzz += n[q] * czq * czq;
+    pxy += n[q] * cxq * cyq; pxz += n[q] * cxq * czq; pyz += n[q] * cyq * czq;
+  }
+  if (!(rho > (TC)0)) atomicOr(v.err, ERR_UNSTABLE);
+  const TC inv = (TC)1 / rho;
+  const TC omega = sel<TC>(v.omega_d, v.omega_f);
+  const TC gx = sel<TC>(v.g[0], v.g_f[0]), gy = sel<TC>(v.g[1], v.g_f[1]), gz = sel<TC>(v.g[2], v.g_f[2]);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    const TC fe = feq<TC>(q, rho, jx, jy, jz, inv);
+    const TC gc = gx * (TC)D3Q19::cx(q) + gy * (TC)D3Q19::cy(q) + gz * (TC)D3Q19::cz(q);
+    const TC o = n[q] - omega * (n[q] - fe) + (TC)3 * (TC)D3Q19::w(q) * gc;
+    fout[(long long)q * nc + idx] = S::enc(o, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+  }
+  const TC vf = sel<TC>(v.vf_d, v.vf_f);
+  const TC third = rho / (TC)3;
+  acc[0] += vf * (pxx - jx * jx * inv - third);
+  acc[1] += vf * (pyy - jy * jy * inv - third);
+  acc[2] += vf * (pzz - jz * jz * inv - third);
+  acc[3] += vf * (pxy - jx * jy * inv);
+  acc[4] += vf * (pxz - jx * jz * inv);
+  acc[5] += vf * (pyz - jy * jz * inv);
+}
+
+// Persistent grid over 32 (x) by 8 (y) tiles of the lattice, z slowest; each
+// block sums its nodes' viscous stress once, at the end.
 template <int P>
 __global__ void __launch_bounds__(256) k_collide_stream(View v, const typename Store<P>::T* __restrict__ fin,
                                                         typename Store<P>::T* __restrict__ fout) {
   using TC = typename Store<P>::C;
-  using S = Store<P>;
   __shared__ TC red[32 * 6];
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  if (idx < v.ncell) {
-    const uint32_t m = v.mask[idx];
-    if (!(m & 1u)) {
-      const int nx = v.nx;
-      const int x = (int)(idx % nx);
-      const long long t1 = idx / nx;
-      const int y = (int)(t1 % v.ny);
-      const int z = (int)(t1 / v.ny);
-      const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-      const int zm = z == 0 ? v.nz - 1 : z - 1, zp = z == v.nz - 1 ? 0 : z + 1;
-      const Proto* pr = v.proto;
-      const TC delta = sel<TC>(pr->delta, pr->delta_f), ule = sel<TC>(pr->ule, pr->ule_f);
-      const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-      const TC* plb = reinterpret_cast<const TC*>(v.plb);
-      TC n[19];
-      n[0] = S::load(fin, idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
-      PullAll<P, 1>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, delta, ule, n);
-      TC rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-#pragma unroll
-      for (int q = 0; q < 19; ++q) {
-        const TC cxq = (TC)D3Q19::cx(q), cyq = (TC)D3Q19::cy(q), czq = (TC)D3Q19::cz(q);
-        rho += n[q];
-        jx += n[q] * cxq; jy += n[q] * cyq; jz += n[q] * czq;
-        pxx += n[q] * cxq * cxq; pyy += n[q] * cyq * cyq; pzz += n[q] * czq * czq;
-        pxy += n[q] * cxq * cyq; pxz += n[q] * cxq * czq; pyz += n[q] * cyq * czq;
-      }
-      if (!(rho > (TC)0)) atomicOr(v.err, ERR_UNSTABLE);
-      const TC inv = (TC)1 / rho;
-      const TC omega = sel<TC>(v.omega_d, v.omega_f);
-      const TC gx = sel<TC>(v.g[0], v.g_f[0]), gy = sel<TC>(v.g[1], v.g_f[1]),
-               gz = sel<TC>(v.g[2], v.g_f[2]);
-      const long long nc = v.ncell;
-#pragma unroll
-      for (int q = 0; q < 19; ++q) {
-        const TC fe = feq<TC>(q, rho, jx, jy, jz, inv);
-        const TC gc = gx * (TC)D3Q19::cx(q) + gy * (TC)D3Q19::cy(q) + gz * (TC)D3Q19::cz(q);
-        const TC o = n[q] - omega * (n[q] - fe) + (TC)3 * (TC)D3Q19::w(q) * gc;
-        fout[(long long)q * nc + idx] = S::enc(o, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
-      }
-      const TC vf = sel<TC>(v.vf_d, v.vf_f);
-      const TC third = rho / (TC)3;
-      acc[0] = vf * (pxx - jx * jx * inv - third);
-      acc[1] = vf * (pyy - jy * jy * inv - third);
-      acc[2] = vf * (pzz - jz * jz * inv - third);
-      acc[3] = vf * (pxy - jx * jy * inv);
-      acc[4] = vf * (pxz - jx * jz * inv);
-      acc[5] = vf * (pyz - jy * jz * inv);
+  const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
+  const int tiles_per_plane = ntx * nty;
+  const long long ntiles = (long long)tiles_per_plane * v.nz;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int z = (int)(t / tiles_per_plane);
+    const int r = (int)(t - (long long)z * tiles_per_plane);
+    const int ty = r / ntx, tx = r - ty * ntx;
+    const int x = tx * 32 + lx, y = ty * 8 + ly;
+    if (x < v.nx && y < v.ny) {
+      // a warp covers one x row, so this branch is warp-uniform
+      if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, acc);
+      else lb_node<P, false>(v, fin, fout, x, y, z, acc);
     }
   }
   block_sum<TC, 6>(acc, red);
@@ -245,7 +307,28 @@ __global__ void k_plane_moments(View v, const typename Store<P>::T* __restrict__
 
 using namespace susp_dev;
 
-int lb_blocks(long long ncell) { return (int)((ncell + 255) / 256); }
+// Tiles of the collide-stream grid (upper bound of its block count).
+int lb_blocks(int nx, int ny, int nz) { return ((nx + 31) / 32) * ((ny + 7) / 8) * nz; }
+
+// Persistent grid size: resident blocks of k_collide_stream<P> times SMs,
+// capped by the tile count.
+int lb_grid_blocks(int prec, int nx, int ny, int nz) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  switch (prec) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<0>, 256, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<1>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<2>, 256, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<3>, 256, 0); break;
+  }
+  if (e != cudaSuccess || per < 1) per = 1;
+  if (sms < 1) sms = 1;
+  const int tiles = lb_blocks(nx, ny, nz);
+  const int g = sms * per;
+  return g < tiles ? g : tiles;
+}
 
 void launch_plane_moments(int prec, const View& v, const void* fin, cudaStream_t s) {
   const long long per = 2LL * v.nx * v.nz;
@@ -259,7 +342,7 @@ void launch_plane_moments(int prec, const View& v, const void* fin, cudaStream_t
 }
 
 void launch_collide_stream(int prec, const View& v, const void* fin, void* fout, cudaStream_t s) {
-  const int nb = lb_blocks(v.ncell);
+  const int nb = v.nblk_lb;
   switch (prec) {
     case 0: k_collide_stream<0><<<nb, 256, 0, s>>>(v, (const double*)fin, (double*)fout); break;
     case 1: k_collide_stream<1><<<nb, 256, 0, s>>>(v, (const float*)fin, (float*)fout); break;

@@ -92,14 +92,16 @@ struct View {
   // per-node constants in both precisions (no FP64 arithmetic on the FP32 paths)
   double omega_d, vf_d;         // 1/tau and -(1 - 1/(2 tau))
   float omega_f, vf_f, rho0_f, g_f[3];
+  double inv_nx_d, inv_ny_d, inv_nz_d;   // reciprocal box lengths
+  float inv_nx_f, inv_ny_f, inv_nz_f;
   uint32_t* mask;               // bit 0 solid, bit p: pull source of p is solid (not LE-crossing)
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
   double* visc_part;            // [nblk][6]
-  int nblk_lb;
+  int nblk_lb;                  // blocks of the (persistent) collide-stream grid
   // particles
   int n;
-  double *R, *U, *W, *rad, *amap, *mass, *inert;
+  double *R, *U, *W, *rad, *amap, *mass, *inert, *inv_m, *inv_I;
   void* plb;                    // [n][12] compute-type copy: R, U, W (and pad)
   double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
   double *slet_part, *cvir_part, *rvir_part;   // [n][9]
@@ -108,7 +110,7 @@ struct View {
   int *link_off, *link_cap, *link_cnt;
   // cell list
   int ncx, ncy, ncz, brute;
-  double csx, csy, csz;
+  double csx, csy, csz, inv_csx, inv_csy, inv_csz;
   int *cell_start, *cell_cnt, *cell_ids, *pcell;
   int ncells;
   // tangential-spring table: per particle a, partners b > a
@@ -136,17 +138,32 @@ template <> __device__ __forceinline__ float sel<float>(double, float f) { retur
 __host__ __device__ inline int wrapi(int v, int L) { int r = v % L; return r < 0 ? r + L : r; }
 
 // Lees-Edwards minimum image of d = p - R for a particle centre R: returns k,
-// the image R + k (delta, ny, 0) moving with U + k U_LE e_x.
+// the image R + k (delta, ny, 0) moving with U + k U_LE e_x.  Multiplies by the
+// reciprocal box lengths (no division on the hot paths).
 template <typename T>
-__device__ inline int le_image(T& dx, T& dy, T& dz, T delta, int nx, int ny, int nz) {
+__device__ inline int le_image(T& dx, T& dy, T& dz, T delta, int nx, int ny, int nz, T ix, T iy,
+                               T iz) {
   const T fny = (T)ny, fnx = (T)nx, fnz = (T)nz;
-  int k = (int)floor(dy / fny + (T)0.5);
+  int k = (int)floor(dy * iy + (T)0.5);
   dy -= (T)k * fny;
   dx -= (T)k * delta;
-  dx -= fnx * floor(dx / fnx + (T)0.5);
-  dz -= fnz * floor(dz / fnz + (T)0.5);
+  dx -= fnx * floor(dx * ix + (T)0.5);
+  dz -= fnz * floor(dz * iz + (T)0.5);
   return k;
 }
+
+template <typename T>
+__device__ inline int le_image_v(const View& v, T& dx, T& dy, T& dz, T delta) {
+  return le_image<T>(dx, dy, dz, delta, v.nx, v.ny, v.nz, sel<T>(v.inv_nx_d, v.inv_nx_f),
+                     sel<T>(v.inv_ny_d, v.inv_ny_f), sel<T>(v.inv_nz_d, v.inv_nz_f));
+}
+
+// Lattice weight C^q for a runtime direction.
+__host__ __device__ inline float wq_f(int q) { return q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f); }
+__host__ __device__ inline double wq_d(int q) { return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+template <typename T> __device__ inline T wq(int q);
+template <> __device__ inline float wq<float>(int q) { return wq_f(q); }
+template <> __device__ inline double wq<double>(int q) { return wq_d(q); }
 
 template <typename T>
 __device__ inline T feq(int q, T rho, T jx, T jy, T jz, T inv_rho) {

@@ -153,26 +153,28 @@ def test_dense_contacts_lubrication_repulsion_fp64():
 
 
 def test_quasi2d_oscillatory_fp64():
-    box = (64, 64, 12)
-    a_max = 3.0
-    a_min = a_max / 1.4
-    n = I.n_for_phi2(0.45, box, a_min, a_max)
+    """Monolayer at the paper's resolution (radii 5 / 7, L_z = 4 a_max, Sec. 4.1)."""
+    box = (64, 64, 28)
+    a_min, a_max = 5.0, 7.0
+    n = I.n_for_phi2(0.5, box, a_min, a_max)
     r = I.bidisperse_radii(n, a_min)
     pos = I.place_spheres(box, r, seed=41, quasi2d=True, min_gap=0.05)
     m0 = 0.5 * 4 / 3 * math.pi * (a_min ** 3 + a_max ** 3)
     kw = dict(tau=1.0, kn=0.36 * m0, kt_ratio=0.2, mu=1.0, F0=2e-4 * 0.36 * m0,
               debye=0.02 * a_min, lub_delta=0.01 * a_min, lub_cut=0.5, quasi2d=True)
     g, o = _both(*box, r, pos, **kw)
-    sh = dict(kind=1, gamma0=0.3, omega=2 * math.pi / 400, theta=0.0)
+    sh = dict(kind=1, gamma0=0.1, omega=2 * math.pi / 400, theta=0.0)
     _step(g, o, 60, **sh)
+    assert o.error() == 0
     Rg, _, _ = g.particles()
     Ro, _, _ = o.particles()
     assert np.abs(Rg - Ro).max() < 1e-9
     assert np.abs(Rg[:, 2] - box[2] / 2).max() == 0.0
     assert _pop_err(g, o) < 1e-12
-    sg, _ = g.stress(S.ANGULAR)
-    so, _ = o.stress(O.ANGULAR)
-    assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300)
+    for kind in (S.VISCOUS, S.ANGULAR, S.TOTAL):
+        sg, _ = g.stress(kind)
+        so, _ = o.stress(kind)
+        assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
 
 
 def test_moving_particles_fp32():
@@ -202,15 +204,46 @@ def test_overlapping_mapped_spheres_are_rejected():
 
 
 # -------------------------------------------------------- full-size workload
-def test_full_size_dense_shear_fp32_sampled():
+def _dilate(m):
+    out = m.copy()
+    for ax in range(3):
+        for sft in (-1, 1):
+            out |= np.roll(m, sft, axis=ax)
+    return out
+
+
+def test_full_size_dense_shear_fp32():
     """The benchmark workload (96^3, phi_3 = 0.50, FP32) in the benchmark's
-    launch configuration: a few steps against the oracle on the whole box."""
+    launch configuration, against the oracle on the whole box for a few steps.
+    FP32 forces move the centres by ~1e-7 from the FP64 oracle, which can flip
+    the solid / fluid decision of nodes lying within that distance of a mapped
+    sphere's surface; such nodes must be rare, must lie on a surface, and the
+    comparison excludes them and their neighbours."""
     w = I.config_dst(phi3=0.50)
     kw = _params(w)
     g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **kw)
-    _step(g, o, 3, **w.shear)
-    assert _pop_err(g, o) < 2e-5
+    steps = 3
+    ever = np.zeros((w.nz, w.ny, w.nx), bool)
+    for _ in range(steps):
+        _step(g, o, 1, **w.shear)
+        og, oo = g.owner(), o.owner()
+        diff = og != oo
+        # a disagreement can be transient (covered, then uncovered): keep them all
+        ever |= diff
+        assert diff.mean() < 1e-5
+        Ro, _, _ = o.particles()
+        box = np.array([w.nx, w.ny, w.nz])
+        for z, y, x in np.argwhere(diff):
+            i = max(og[z, y, x], oo[z, y, x])
+            d = np.array([x, y, z]) - Ro[i]
+            d -= box * np.round(d / box)
+            assert abs(np.linalg.norm(d) - 0.95 * w.radius[i]) < 1e-3
+    assert o.error() == 0
+    near = ever
+    for _ in range(steps):
+        near = _dilate(near)
+    keep = ~near & (og < 0) & (oo < 0)
+    fo, fg = o.populations(), g.populations()
+    assert np.abs(fg[:, keep] - fo[:, keep]).max() / np.abs(fo[:, keep]).max() < 2e-5
     Rg, _, _ = g.particles()
-    Ro, _, _ = o.particles()
     assert np.abs(Rg - Ro).max() < 1e-6
-    assert (g.owner() == o.owner()).mean() > 0.99999
