@@ -171,6 +171,27 @@ susp_status susp_get_info(susp *h, susp_info *info);
 susp_status susp_profile(susp *h, int enable);
 susp_status susp_profile_read(susp *h, double *ms_total, int *launches);
 
+/* Allocation-free fluid step.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory or hand the library a
+ * workspace at all, e.g. code running inside a host framework that owns every
+ * device allocation, or a loop that must not touch the allocator.  It advances
+ * a particle-free FP32 box by one step -- the same collide-stream and
+ * Lees-Edwards planes as susp_step -- from f_in to f_out (device pointers,
+ * [19][nz][ny][nx] post-collision populations, caller-owned, not aliased),
+ * with Lees-Edwards offset delta and image velocity u_le for this step, and
+ * writes the step's viscous stress (3 x 3, row-major, per unit volume) to the
+ * device pointer visc_out.  Its scratch (plane moments and block partials)
+ * is a fixed static device array of about 2.2 MiB inside the library, held by
+ * every GPU that loads the library until the process exits; boxes with
+ * nx * nz > 65536 are rejected with SUSP_EINVAL.  The first call on a device
+ * looks up that array's address (cudaGetSymbolAddress), so make the first
+ * call on each device before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race.  Nothing is allocated; asynchronous on
+ * cuda_stream.  Errors: SUSP_EINVAL, SUSP_ECUDA. */
+susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double tau, double delta, double u_le,
+                                    const float *f_in, float *f_out, double *visc_out,
+                                    void *cuda_stream);
+
 /* Release the handle (not the caller's workspace). */
 void susp_destroy(susp *h);
 

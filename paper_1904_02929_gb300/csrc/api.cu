@@ -294,6 +294,8 @@ static void refresh_links(susp* h) {
   launch_links(h->prec, h->v, h->fin, h->stream);
 }
 
+void susp_set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* susp_last_error(void) { return g_err.c_str(); }

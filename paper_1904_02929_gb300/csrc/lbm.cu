@@ -352,3 +352,226 @@ void launch_collide_stream(int prec, const View& v, const void* fin, void* fout,
       break;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the collide-stream step (particle-free box, FP32).
+//
+// For callers that cannot allocate device memory or hand the library a
+// workspace at all: the two kernels below keep their scratch (the moments of
+// the two Lees-Edwards planes and the per-block viscous-stress partials) in
+// the file-scope device array susp_noalloc_scratch.  The array is part of the
+// library image, so every GPU that loads the library holds it until the
+// process exits; all calls share it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "../../include/susp.h"
+
+namespace susp_dev {
+
+constexpr int NOALLOC_MAX_PLANE_NODES = 65536;   // nx * nz
+constexpr int NOALLOC_MAX_BLOCKS = 4096;
+constexpr size_t NOALLOC_PLANE_BYTES = 2ull * NOALLOC_MAX_PLANE_NODES * 4 * sizeof(float);
+constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_PLANE_BYTES + 6ull * NOALLOC_MAX_BLOCKS * sizeof(double);
+
+static __device__ __align__(256) unsigned char susp_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+struct NoAllocLE {
+  int di;
+  float w_lo, w_hi, ule;   // interpolation weights on c1 (y = 0 / y = ny-1 receivers), U_LE
+};
+
+// Fluid-only pull across a Lees-Edwards plane: linear interpolation between
+// the two straddling nodes plus the Galilean correction with their moments.
+template <int p>
+__device__ __forceinline__ float noalloc_le_pull(const View& v, const float* __restrict__ fin,
+                                                 const float* __restrict__ pm_all, NoAllocLE le,
+                                                 int x, int z) {
+  const int nx = v.nx, ny = v.ny;
+  const long long nc = v.ncell;
+  constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+  const bool below = (cpy == 1);
+  const int sx = x - cpx, sz = wrapi(z - cpz, v.nz);
+  const int ys = below ? ny - 1 : 0;
+  const int c0x = below ? wrapi(sx + le.di, nx) : wrapi(sx - le.di - 1, nx);
+  const int c1x = c0x + 1 == nx ? 0 : c0x + 1;
+  const float w1 = below ? le.w_lo : le.w_hi;
+  const long long i0 = c0x + (long long)nx * (ys + (long long)ny * sz);
+  const long long i1 = c1x + (long long)nx * (ys + (long long)ny * sz);
+  const float* pm = pm_all + (below ? 4LL * v.nz * nx : 0);
+  const long long k0 = 4LL * (c0x + (long long)nx * sz), k1 = 4LL * (c1x + (long long)nx * sz);
+  const float a = 1.0f - w1;
+  float val = a * __ldg(fin + (long long)p * nc + i0) + w1 * __ldg(fin + (long long)p * nc + i1);
+  const float rho = a * pm[k0] + w1 * pm[k1];
+  const float jx = a * pm[k0 + 1] + w1 * pm[k1 + 1];
+  const float jy = a * pm[k0 + 2] + w1 * pm[k1 + 2];
+  const float jz = a * pm[k0 + 3] + w1 * pm[k1 + 3];
+  const float sgn = below ? -1.0f : 1.0f;
+  const float inv = 1.0f / rho;
+  val += feq<float>(p, rho, jx + sgn * rho * le.ule, jy, jz, inv) - feq<float>(p, rho, jx, jy, jz, inv);
+  return val;
+}
+
+template <int p>
+struct NoAllocPull {
+  __device__ __forceinline__ static void run(const View& v, const float* __restrict__ fin,
+                                             const float* __restrict__ pm, NoAllocLE le, int x, int y,
+                                             int z, int xm, int xp, int zm, int zp, float (&n)[19]) {
+    constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+    const int sy = y - cpy;
+    if (cpy != 0 && (sy < 0 || sy >= v.ny)) {
+      n[p] = noalloc_le_pull<p>(v, fin, pm, le, x, z);
+    } else {
+      const int sx = cpx == 1 ? xm : (cpx == -1 ? xp : x);
+      const int sz = cpz == 1 ? zm : (cpz == -1 ? zp : z);
+      n[p] = __ldg(fin + (long long)p * v.ncell + sx + (long long)v.nx * (sy + (long long)v.ny * sz));
+    }
+    NoAllocPull<p + 1>::run(v, fin, pm, le, x, y, z, xm, xp, zm, zp, n);
+  }
+};
+template <>
+struct NoAllocPull<19> {
+  __device__ __forceinline__ static void run(const View&, const float* __restrict__, const float* __restrict__,
+                                             NoAllocLE, int, int, int, int, int, int, int, float (&)[19]) {}
+};
+
+__global__ void __launch_bounds__(256) k_fluid_step_noalloc(View v, const float* __restrict__ fin,
+                                                            float* __restrict__ fout, NoAllocLE le,
+                                                            double* __restrict__ partials) {
+  __shared__ float red[32 * 6];
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+  const float* pm = reinterpret_cast<const float*>(v.plane_mom);
+  const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
+  const int tiles_per_plane = ntx * nty;
+  const long long ntiles = (long long)tiles_per_plane * v.nz;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const float omega = v.omega_f, vf = v.vf_f;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int z = (int)(t / tiles_per_plane);
+    const int r = (int)(t - (long long)z * tiles_per_plane);
+    const int ty = r / ntx, tx = r - ty * ntx;
+    const int x = tx * 32 + lx, y = ty * 8 + ly;
+    if (x >= v.nx || y >= v.ny) continue;
+    const long long idx = x + (long long)v.nx * (y + (long long)v.ny * z);
+    const int xm = x == 0 ? v.nx - 1 : x - 1, xp = x == v.nx - 1 ? 0 : x + 1;
+    const int zm = z == 0 ? v.nz - 1 : z - 1, zp = z == v.nz - 1 ? 0 : z + 1;
+    float n[19];
+    n[0] = __ldg(fin + idx);
+    NoAllocPull<1>::run(v, fin, pm, le, x, y, z, xm, xp, zm, zp, n);
+    float rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const float cxq = (float)D3Q19::cx(q), cyq = (float)D3Q19::cy(q), czq = (float)D3Q19::cz(q);
+      rho += n[q];
+      jx += n[q] * cxq; jy += n[q] * cyq; jz += n[q] * czq;
+      pxx += n[q] * cxq * cxq; pyy += n[q] * cyq * cyq; pzz += n[q] * czq * czq;
+      pxy += n[q] * cxq * cyq; pxz += n[q] * cxq * czq; pyz += n[q] * cyq * czq;
+    }
+    const float inv = 1.0f / rho;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const float fe = feq<float>(q, rho, jx, jy, jz, inv);
+      fout[(long long)q * v.ncell + idx] = n[q] - omega * (n[q] - fe);
+    }
+    const float third = rho / 3.0f;
+    acc[0] += vf * (pxx - jx * jx * inv - third);
+    acc[1] += vf * (pyy - jy * jy * inv - third);
+    acc[2] += vf * (pzz - jz * jz * inv - third);
+    acc[3] += vf * (pxy - jx * jy * inv);
+    acc[4] += vf * (pxz - jx * jz * inv);
+    acc[5] += vf * (pyz - jy * jz * inv);
+  }
+  block_sum<float, 6>(acc, red);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) partials[6LL * blockIdx.x + k] = (double)acc[k];
+}
+
+// Sums the per-block partials in block order and writes the 3 x 3 viscous
+// stress of the step (divided by the box volume); overwrites out.
+__global__ void k_fluid_visc_noalloc(const double* __restrict__ partials, int nblk, double inv_volume,
+                                     double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nblk; ++b)
+    for (int k = 0; k < 6; ++k) s[k] += partials[6LL * b + k];
+  const double full[9] = {s[0], s[3], s[4], s[3], s[1], s[5], s[4], s[5], s[2]};
+  for (int k = 0; k < 9; ++k) out[k] = full[k] * inv_volume;
+}
+
+}  // namespace susp_dev
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256];
+}  // namespace
+
+void susp_set_last_error(const char* msg);
+
+extern "C" susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double tau, double delta, double u_le,
+                                               const float* f_in, float* f_out, double* visc_out,
+                                               void* cuda_stream) {
+  using namespace susp_dev;
+  if (nx < 4 || ny < 4 || nz < 4 || !(tau > 0.5) || !f_in || !f_out || !visc_out) {
+    susp_set_last_error("susp_fluid_step_noalloc: bad argument");
+    return SUSP_EINVAL;
+  }
+  if ((long long)nx * nz > NOALLOC_MAX_PLANE_NODES || (long long)nx * ny * nz >= (1LL << 31)) {
+    susp_set_last_error("susp_fluid_step_noalloc: nx * nz exceeds 65536 (the size of its static scratch)");
+    return SUSP_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    susp_set_last_error("susp_fluid_step_noalloc: no current CUDA device");
+    return SUSP_ECUDA;
+  }
+  void* scratch = nullptr;
+  {
+    // first call on this device: look up the device address of the static array
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], susp_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        susp_set_last_error("susp_fluid_step_noalloc: cudaGetSymbolAddress failed");
+        return SUSP_ECUDA;
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  View v;
+  memset(&v, 0, sizeof v);
+  v.nx = nx; v.ny = ny; v.nz = nz;
+  v.ncell = (long long)nx * ny * nz;
+  v.tau = tau; v.rho0 = 1.0; v.rho0_f = 1.0f;
+  v.omega_d = 1.0 / tau; v.vf_d = -(1.0 - 0.5 / tau);
+  v.omega_f = (float)v.omega_d; v.vf_f = (float)v.vf_d;
+  v.scale = 1.0f; v.inv_scale = 1.0f;
+  v.plane_mom = scratch;
+  double* partials = reinterpret_cast<double*>(static_cast<char*>(scratch) + NOALLOC_PLANE_BYTES);
+  // offset split exactly as the library's protocol state does it
+  const double dm = delta - nx * floor(delta / nx);
+  NoAllocLE le;
+  le.di = (int)floor(dm);
+  const double w = dm - le.di;
+  le.w_lo = (float)w;
+  le.w_hi = (float)(1.0 - w);
+  le.ule = (float)u_le;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = ((nx + 31) / 32) * ((ny + 7) / 8) * nz;
+  int nblk = (sms > 0 ? sms : 1) * 4;
+  if (nblk > tiles) nblk = tiles;
+  if (nblk > NOALLOC_MAX_BLOCKS) nblk = NOALLOC_MAX_BLOCKS;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const long long per = 2LL * nx * nz;
+  k_plane_moments<1><<<(int)((per + 255) / 256), 256, 0, s>>>(v, f_in);
+  k_fluid_step_noalloc<<<nblk, 256, 0, s>>>(v, f_in, f_out, le, partials);
+  k_fluid_visc_noalloc<<<1, 32, 0, s>>>(partials, nblk, 1.0 / ((double)nx * ny * nz), visc_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    susp_set_last_error(cudaGetErrorString(e));
+    return SUSP_ECUDA;
+  }
+  return SUSP_OK;
+}

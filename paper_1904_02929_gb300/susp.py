@@ -94,6 +94,10 @@ def library() -> C.CDLL:
         L.susp_profile.argtypes = [C.c_void_p, C.c_int]
         L.susp_profile_read.restype = C.c_int
         L.susp_profile_read.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+        L.susp_fluid_step_noalloc.restype = C.c_int
+        L.susp_fluid_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p]
         L.susp_destroy.restype = None
         L.susp_destroy.argtypes = [C.c_void_p]
         L.susp_last_error.restype = C.c_char_p
@@ -196,6 +200,15 @@ def susp_profile_read(h):
     n = C.c_int(0)
     _check(library().susp_profile_read(h, C.byref(ms), C.byref(n)), "susp_profile_read")
     return float(ms.value), int(n.value)
+
+
+def susp_fluid_step_noalloc(nx, ny, nz, tau, delta, u_le, f_in_ptr, f_out_ptr, visc_out_ptr,
+                            stream) -> None:
+    """Allocation-free particle-free FP32 step; all pointers are device addresses."""
+    _check(library().susp_fluid_step_noalloc(int(nx), int(ny), int(nz), float(tau), float(delta),
+                                             float(u_le), C.c_void_p(f_in_ptr), C.c_void_p(f_out_ptr),
+                                             C.c_void_p(visc_out_ptr), C.c_void_p(stream)),
+           "susp_fluid_step_noalloc")
 
 
 def susp_destroy(h) -> None:
