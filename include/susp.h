@@ -67,7 +67,7 @@ typedef struct {
   double rho0;              /* reference fluid density, used in Eq. 7                             */
   int n;                    /* number of particles (>= 0)                                          */
   const double *radius;     /* [n] contact radii (host; copied)                                     */
-  const double *pos;        /* [3n] centres, x y z per particle (host; copied)                      */
+  const double *pos;        /* [3n] centres, x y z per particle (host; copied; finite; wrapped into the box) */
   const double *vel;        /* [3n] initial velocities or NULL (host; copied)                       */
   const double *omega;      /* [3n] initial angular velocities or NULL (host; copied)               */
   double rho_p;             /* particle density; m = rho_p 4/3 pi a^3, I = 2/5 m a^2                */
@@ -192,8 +192,60 @@ susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double tau, double d
                                     const float *f_in, float *f_out, double *visc_out,
                                     void *cuda_stream);
 
+/* Replay a captured CUDA graph of the step (default on; no counterpart in the
+ * paper).  susp_step captures the step once, on the handle's stream (which
+ * must not be the legacy default stream), and replays it every step: the
+ * population buffer and spring-table parities follow from the step counter on
+ * the device, so one graph serves every step.  If capture fails the step runs
+ * as plain launches.  Disabling drops the captured graph.  Synchronises. */
+susp_status susp_set_graphs(susp *h, int enable);
+
 /* Release the handle (not the caller's workspace). */
 void susp_destroy(susp *h);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent boxes stepped in lockstep by one launch sequence (no
+ * counterpart in the paper, which runs one box at a time; this serves
+ * parameter sweeps such as the volume-fraction and amplitude scans of
+ * Sec. 4).  Every kernel of the step covers all attached boxes: the
+ * collide-stream is one persistent grid over the tiles of every box, the
+ * particle sub-steps one cooperative grid over every particle.  Each box keeps
+ * its own parameters, protocol, step counter and workspace, and the results
+ * of a box are the same whether it is stepped alone or in a batch.
+ *
+ * Storage: the caller owns a device workspace of
+ * susp_batch_workspace_bytes(max_boxes) bytes (256-byte aligned) for the
+ * box descriptors, and a stream that is not the legacy default stream.
+ * Attach: the box must share the batch's storage precision and have a shear
+ * protocol set (susp_step with nsteps = 0); its stream is synchronised and
+ * from then on its work runs on the batch's stream.  While attached, susp_step
+ * with nsteps > 0 returns SUSP_ESTATE; the read-back calls work as usual.
+ * Attach and detach synchronise the batch's stream and drop its captured
+ * graph, so continuous batching (boxes joining and leaving between steps)
+ * costs one capture per membership change.  susp_destroy of an attached box
+ * detaches it first.  Errors: SUSP_EINVAL, SUSP_ENOMEM (batch full),
+ * SUSP_ESTATE, SUSP_ECUDA. */
+typedef struct susp_batch susp_batch;
+size_t susp_batch_workspace_bytes(int max_boxes);
+susp_status susp_batch_create(int max_boxes, void *dev_workspace, size_t bytes, void *cuda_stream,
+                              susp_batch **out);
+susp_status susp_batch_attach(susp_batch *b, susp *h);
+susp_status susp_batch_detach(susp_batch *b, susp *h);
+int susp_batch_size(const susp_batch *b);
+/* Advance every attached box by nsteps steps under its own protocol (asynchronous). */
+susp_status susp_batch_step(susp_batch *b, int nsteps);
+/* As susp_profile / susp_profile_read, for the batch's collide-stream launch. */
+susp_status susp_batch_profile(susp_batch *b, int enable);
+susp_status susp_batch_profile_read(susp_batch *b, double *ms_total, int *launches);
+/* Device error status of every attached box, in attach order (the order
+ * detaching keeps), into status[0 .. susp_batch_size(b)); n is the array's
+ * length.  One gather launch and one copy for the whole batch; synchronises
+ * the batch's stream.  A box whose status is not SUSP_OK keeps stepping
+ * safely (its kernels stay inside its own buffers) but its results are
+ * invalid; a server retires it.  Errors: SUSP_EINVAL, SUSP_ECUDA. */
+susp_status susp_batch_errors(susp_batch *b, int *status, int n);
+/* Release the batch (detaching its boxes), not the caller's workspace. */
+void susp_batch_destroy(susp_batch *b);
 
 /* Message of the last failing call on this thread (never NULL). */
 const char *susp_last_error(void);

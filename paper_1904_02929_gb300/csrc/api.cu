@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -15,16 +16,17 @@
 using namespace susp_dev;
 
 // launchers defined in the other translation units
-void launch_plane_moments(int prec, const View& v, const void* fin, cudaStream_t s);
-void launch_collide_stream(int prec, const View& v, const void* fin, void* fout, cudaStream_t s);
+void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s);
+void launch_collide_stream(int prec, const Batch& B, int grid, cudaStream_t s);
 int lb_blocks(int nx, int ny, int nz);
 int lb_grid_blocks(int prec, int nx, int ny, int nz);
-void launch_claim(int prec, const View& v, cudaStream_t s);
-void launch_node_update(int prec, const View& v, void* f, cudaStream_t s);
-void launch_links(int prec, const View& v, const void* f, cudaStream_t s);
+void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s);
+void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s);
+void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s);
 void launch_init_pop(int prec, const View& v, void* f, cudaStream_t s);
 void launch_write_plb(const View& v, int plb_double, cudaStream_t s);
-void launch_dem_substep(const View& v, int parity, int sub, int plb_double, cudaStream_t s);
+cudaError_t launch_dem_step(const Batch& B, int nparts, int ncells, int plb_double, int grid, cudaStream_t s);
+int dem_grid_blocks(int plb_double, int n);
 
 namespace {
 
@@ -36,8 +38,6 @@ susp_status fail(susp_status st, const std::string& msg) {
 }
 
 const int HSLOTS = 16;        // tangential springs per particle (partners with larger index)
-const int FIN_BLOCKS = 32;    // blocks of the per-step finalisation
-const int FIN_VALS = 40;      // 6 visc, 9 stresslet, 9 contact, 1 contacts, 9 repulsive
 const double KPI = 3.14159265358979323846;
 
 size_t esize(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
@@ -45,12 +45,12 @@ size_t csize(int prec) { return prec == 0 ? 8 : 4; }
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t fa, fb, mask, owner, pm, visc;
-  size_t R, U, W, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
+  size_t fa, fb, mask, owner, pm, vacc, views, tabs;
+  size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
   size_t slet, cvir, rvir, ncont, links, loff, lcap, lcnt;
   size_t cstart, ccnt, cids, pcell;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
-  size_t sums, hist, counters, proto, err, finp, finc;
+  size_t sums, hist, counters, proto, err;
   size_t total;
   long long nlinks;
   int ncx, ncy, ncz, brute, ncells;
@@ -61,6 +61,7 @@ bool valid(const susp_params* p, std::string& why) {
   if (!p) { why = "params is NULL"; return false; }
   if (p->nx < 4 || p->ny < 4 || p->nz < 4) { why = "lattice dims must be >= 4"; return false; }
   if ((long long)p->nx * p->ny * p->nz >= (1LL << 27)) { why = "lattice larger than 2^27 nodes"; return false; }
+  if (p->nx > 2047 || p->ny > 2047 || p->nz > 1023) { why = "lattice dims must be <= 2047 x 2047 x 1023"; return false; }
   if (!(p->tau > 0.5)) { why = "tau must exceed 1/2"; return false; }
   if (!(p->rho0 > 0.0)) { why = "rho0 must be positive"; return false; }
   if (p->n < 0) { why = "n < 0"; return false; }
@@ -73,6 +74,8 @@ bool valid(const susp_params* p, std::string& why) {
     if (!(p->a_map_ratio > 0.0 && p->a_map_ratio <= 1.0)) { why = "a_map_ratio in (0, 1]"; return false; }
     for (int i = 0; i < p->n; ++i) {
       if (!(p->radius[i] > 0.0)) { why = "radius must be positive"; return false; }
+      for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(p->pos[3 * i + c])) { why = "particle centres must be finite"; return false; }
       double am = p->a_map_ratio * p->radius[i] + 1.0;
       if (2 * am + 1 >= p->nx || 2 * am + 1 >= p->ny || 2 * am + 1 >= p->nz) {
         why = "particle too large for the box"; return false;
@@ -100,8 +103,11 @@ void make_layout(const susp_params* p, Layout& L) {
   L.mask = take(4 * nc);
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
-  L.visc = take(6 * 8 * (size_t)lb_blocks(p->nx, p->ny, p->nz));
+  L.vacc = take(6 * 8);
+  L.views = take(sizeof(View));
+  L.tabs = take(4 * 2 * sizeof(int));   // the one-box batch tables
   L.R = take(24 * nn); L.U = take(24 * nn); L.W = take(24 * nn);
+  L.R2 = take(24 * nn); L.U2 = take(24 * nn); L.W2 = take(24 * nn); L.pcx = take(4 * 8 * (size_t)nn);
   L.rad = take(8 * nn); L.amap = take(8 * nn); L.mass = take(8 * nn); L.inert = take(8 * nn);
   L.imass = take(8 * nn); L.iinert = take(8 * nn);
   L.plb = take(12 * csize(prec) * nn);
@@ -137,8 +143,6 @@ void make_layout(const susp_params* p, Layout& L) {
   L.counters = take(8 * 4);
   L.proto = take(sizeof(Proto));
   L.err = take(4);
-  L.finp = take(8 * FIN_VALS * FIN_BLOCKS);
-  L.finc = take(4);
   L.total = o;
 }
 
@@ -178,46 +182,35 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
   *pp = s;
 }
 
-// End of step t: reduce the per-block / per-particle stress partials, add
-// them to the compensated time sums, then advance the protocol to t+1.
-// FIN_BLOCKS blocks each reduce a slice into fin_part; the last block to
-// finish sums the slices in block order, so the result is deterministic.
-__global__ void __launch_bounds__(256) k_finalize(View v, double* fin_part, unsigned* fin_count) {
-  __shared__ double red[32 * 37];
-  __shared__ bool last;
-  double acc[37];
-  for (int k = 0; k < 37; ++k) acc[k] = 0.0;
-  const int G = gridDim.x;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = G * blockDim.x;
-  for (int b = tid; b < v.nblk_lb; b += nthr)
-    for (int k = 0; k < 6; ++k) acc[k] += v.visc_part[6LL * b + k];
-  for (int i = tid; i < v.n; i += nthr) {
-    for (int k = 0; k < 9; ++k) {
-      acc[6 + k] += v.slet_part[9 * i + k];
-      acc[15 + k] += v.cvir_part[9 * i + k];
-      acc[25 + k] += v.rvir_part[9 * i + k];
-    }
-    acc[24] += v.ncont_part[i];
-  }
-  block_sum<double, 37>(acc, red);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 37; ++k) fin_part[FIN_VALS * blockIdx.x + k] = acc[k];
-    __threadfence();
-    last = (atomicAdd(fin_count, 1u) == (unsigned)G - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // column k of the slices, summed in block order by thread k
+// End of step t, one block per box: sum the per-particle stress partials
+// (one warp per quantity, fixed order) and the step's viscous stress, add them
+// to the compensated time sums, then advance the protocol to t+1.
+__global__ void __launch_bounds__(256) k_finalize(Batch B) {
+  const View& v = B.views[blockIdx.x];
   __shared__ double tot[37];
-  if (threadIdx.x < 37) {
+  // quantity k: 0-5 viscous, 6-14 stresslet, 15-23 contact virial,
+  // 24 contact count, 25-33 repulsive virial (34-36 unused)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < 37; k += nw) {
     double t = 0.0;
-    for (int b = 0; b < G; ++b) t += ((volatile double*)fin_part)[FIN_VALS * b + threadIdx.x];
-    tot[threadIdx.x] = t;
+    if (k < 6) {
+      if (lane == 0) t = v.visc_acc[k];
+    } else if (k < 15) {
+      for (int i = lane; i < v.n; i += 32) t += v.slet_part[9 * i + (k - 6)];
+    } else if (k < 24) {
+      for (int i = lane; i < v.n; i += 32) t += v.cvir_part[9 * i + (k - 15)];
+    } else if (k == 24) {
+      for (int i = lane; i < v.n; i += 32) t += (double)v.ncont_part[i];
+    } else if (k < 34) {
+      for (int i = lane; i < v.n; i += 32) t += v.rvir_part[9 * i + (k - 25)];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[k] = t;
   }
   __syncthreads();
+  if (threadIdx.x < 6) v.visc_acc[threadIdx.x] = 0.0;
   if (threadIdx.x != 0) return;
-  *fin_count = 0u;
   // visc partials: xx yy zz xy xz yz -> full 3x3
   const double vs[9] = {tot[0], tot[3], tot[4], tot[3], tot[1], tot[5], tot[4], tot[5], tot[2]};
   double* S = v.sums;
@@ -246,9 +239,219 @@ __global__ void __launch_bounds__(256) k_finalize(View v, double* fin_part, unsi
   *v.proto = s;
 }
 
+// Error words of the boxes of a batch, in batch order.
+__global__ void k_gather_err(Batch B, int* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B.nbox) out[b] = *B.views[b].err;
+}
+
 }  // namespace
 
-// ------------------------------------------------------------ handle
+// ------------------------------------------------------------ step engine
+
+struct GraphSlot {
+  bool valid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t n0 = nullptr, n1 = nullptr;   // event-record nodes around the collide-stream
+};
+
+static const int PROF_MAX = 4096;
+
+// The launch sequence of one lattice step over a set of boxes (a single box,
+// or the boxes attached to a batch).  Every kernel takes the whole set; the
+// population buffers and spring tables of each box follow from its own step
+// counter on the device, so one captured graph serves every step.
+struct Engine {
+  int prec = 0;
+  Batch B{};                 // device views and prefix tables
+  int nbox = 0, nparts = 0, ncells = 0, nplane = 0, ntiles = 0;
+  bool any_move = false;     // some box has moving particles
+  int lb_grid = 1, dem_grid = 1;
+  cudaStream_t stream = nullptr;
+  bool use_graphs = true;
+  GraphSlot graphs[2];       // [timed]
+  bool prof = false;
+  int prof_n = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+static susp_status cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return SUSP_OK;
+}
+
+// Host copy of the prefix tables for the views of a set of boxes; fills the
+// engine's totals.  tabs receives tile, particle, plane, cell tables of
+// nbox + 1 entries each.
+static void eng_tables(Engine& e, const std::vector<const View*>& vs, std::vector<int>& tabs) {
+  const int nb = (int)vs.size();
+  tabs.assign(4 * (nb + 1), 0);
+  int* tile = tabs.data();
+  int* part = tile + (nb + 1);
+  int* plane = part + (nb + 1);
+  int* cell = plane + (nb + 1);
+  e.any_move = false;
+  int msub = 1;
+  for (int b = 0; b < nb; ++b) {
+    const View& v = *vs[b];
+    tile[b + 1] = tile[b] + lb_blocks(v.nx, v.ny, v.nz);
+    part[b + 1] = part[b] + v.n;
+    plane[b + 1] = plane[b] + 2 * v.nx * v.nz;
+    cell[b + 1] = cell[b] + (v.brute ? 0 : v.ncells);
+    if (v.move && v.n > 0) { e.any_move = true; msub = std::max(msub, v.nsub); }
+  }
+  e.nbox = nb;
+  e.ntiles = tile[nb]; e.nparts = part[nb]; e.nplane = plane[nb]; e.ncells = cell[nb];
+  e.B.nbox = nb;
+  e.B.max_nsub = msub;
+  e.lb_grid = std::max(1, std::min(lb_grid_blocks(e.prec, 0, 0, 0), e.ntiles));
+  e.dem_grid = dem_grid_blocks(e.prec == 0, e.nparts);
+}
+
+// Point the engine's batch at device storage for nbox views and the tables.
+static void eng_bind(Engine& e, char* views, char* tabs, int nbox) {
+  e.B.views = (const View*)views;
+  const int* t = (const int*)tabs;
+  e.B.tile_off = t;
+  e.B.part_off = t + (nbox + 1);
+  e.B.plane_off = t + 2 * (nbox + 1);
+  e.B.cell_off = t + 3 * (nbox + 1);
+}
+
+static void eng_drop_graphs(Engine& e) {
+  for (auto& g : e.graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = GraphSlot();
+  }
+}
+
+// The launches of one lattice step; ev0 / ev1 (optional) bracket the
+// collide-stream launch.
+static cudaError_t eng_enqueue(Engine& e, cudaEvent_t ev0, cudaEvent_t ev1) {
+  cudaStream_t s = e.stream;
+  cudaError_t err = cudaSuccess;
+  launch_plane_moments(e.prec, e.B, e.nplane, s);
+  if (ev0) cudaEventRecord(ev0, s);
+  launch_collide_stream(e.prec, e.B, e.lb_grid, s);
+  if (ev1) cudaEventRecord(ev1, s);
+  if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
+  k_finalize<<<e.nbox, 256, 0, s>>>(e.B);
+  launch_node_update(e.prec, e.B, e.nparts, s);
+  launch_links(e.prec, e.B, e.nparts, s);
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+// Capture one step as a CUDA graph (timed: with event-record nodes that each
+// replay retargets); false if capture is not possible on this stream.
+static bool eng_capture(Engine& e, int timed) {
+  GraphSlot& g = e.graphs[timed];
+  cudaStream_t s = e.stream;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaError_t le = eng_enqueue(e, timed ? e.ev[0] : nullptr, timed ? e.ev[1] : nullptr);
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (le != cudaSuccess || ce != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return false;
+  }
+  g.n0 = g.n1 = nullptr;
+  if (timed) {
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev = nullptr;
+      cudaGraphEventRecordNodeGetEvent(nd, &ev);
+      if (ev == e.ev[0]) g.n0 = nd;
+      if (ev == e.ev[1]) g.n1 = nd;
+    }
+    if (!g.n0 || !g.n1) {
+      cudaGraphDestroy(graph);
+      return false;
+    }
+  }
+  if (cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  g.graph = graph;
+  g.valid = true;
+  return true;
+}
+
+static susp_status eng_step(Engine& e, int nsteps) {
+  for (int it = 0; it < nsteps; ++it) {
+    const int timed = (e.prof && e.prof_n < PROF_MAX) ? 1 : 0;
+    cudaEvent_t ev0 = timed ? e.ev[2 * e.prof_n] : nullptr, ev1 = timed ? e.ev[2 * e.prof_n + 1] : nullptr;
+    bool done = false;
+    if (e.use_graphs && e.stream != nullptr) {
+      if (!e.graphs[timed].valid && !eng_capture(e, timed)) e.use_graphs = false;
+      if (e.use_graphs) {
+        GraphSlot& g = e.graphs[timed];
+        if (timed) {
+          cudaGraphExecEventRecordNodeSetEvent(g.exec, g.n0, ev0);
+          cudaGraphExecEventRecordNodeSetEvent(g.exec, g.n1, ev1);
+        }
+        done = cudaGraphLaunch(g.exec, e.stream) == cudaSuccess;
+        if (!done) { cudaGetLastError(); e.use_graphs = false; }
+      }
+    }
+    if (!done) {
+      susp_status st = cuda_check(eng_enqueue(e, ev0, ev1), "step launch");
+      if (st) return st;
+    }
+    if (timed) ++e.prof_n;
+  }
+  return cuda_check(cudaGetLastError(), "launch");
+}
+
+static susp_status eng_profile(Engine& e, int enable) {
+  if (enable && e.ev.empty()) {
+    e.ev.resize(2 * PROF_MAX);
+    for (auto& x : e.ev) {
+      susp_status st = cuda_check(cudaEventCreate(&x), "cudaEventCreate");
+      if (st) return st;
+    }
+  }
+  e.prof = enable != 0;
+  e.prof_n = 0;
+  return SUSP_OK;
+}
+
+static susp_status eng_profile_read(Engine& e, double* ms_total, int* launches) {
+  susp_status st = cuda_check(cudaStreamSynchronize(e.stream), "sync");
+  if (st) return st;
+  double tot = 0.0;
+  for (int k = 0; k < e.prof_n; ++k) {
+    float ms = 0.0f;
+    st = cuda_check(cudaEventElapsedTime(&ms, e.ev[2 * k], e.ev[2 * k + 1]), "cudaEventElapsedTime");
+    if (st) return st;
+    tot += ms;
+  }
+  if (ms_total) *ms_total = tot;
+  if (launches) *launches = e.prof_n;
+  e.prof_n = 0;
+  return SUSP_OK;
+}
+
+static void eng_release(Engine& e) {
+  if (e.stream) cudaStreamSynchronize(e.stream);
+  eng_drop_graphs(e);
+  for (auto& x : e.ev) cudaEventDestroy(x);
+  e.ev.clear();
+}
+
+// ------------------------------------------------------------ handles
 
 struct susp {
   susp_params p;
@@ -256,33 +459,26 @@ struct susp {
   Layout L;
   View v;
   char* ws;
-  void* fin;
-  void* fout;
-  cudaStream_t stream;
-  int parity;
   bool have_shear;
   susp_shear shear;
   std::vector<double> radius;
   double scale;
-  // instrumentation
-  bool prof;
-  int prof_n;
-  std::vector<cudaEvent_t> ev;
+  Engine eng;                 // the box stepped alone (a batch of one)
+  susp_batch* batch;          // batch the box is attached to, or NULL
 };
 
-static const int PROF_MAX = 4096;
+struct susp_batch {
+  int max_boxes;
+  int prec;
+  char* ws;
+  Engine eng;
+  std::vector<susp*> boxes;
+};
 
-static susp_status cuda_check(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-  return SUSP_OK;
-}
+static cudaStream_t stream_of(const susp* h) { return h->batch ? h->batch->eng.stream : h->eng.stream; }
 
-static susp_status device_status(susp* h) {
-  cudaError_t e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
-  int err = 0;
-  e = cudaMemcpy(&err, h->v.err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string("read error flag: ") + cudaGetErrorString(e));
+// Status for a box's device error word.
+static susp_status err_status(int err) {
   if (err & ERR_OVERLAP) return fail(SUSP_EOVERLAP, "two mapped spheres claimed one node");
   if (err & ERR_UNSTABLE) return fail(SUSP_EUNSTABLE, "non-positive density or particle speed >= 0.5");
   if (err & ERR_LINKS) return fail(SUSP_ENOMEM, "boundary-link table full");
@@ -290,8 +486,24 @@ static susp_status device_status(susp* h) {
   return SUSP_OK;
 }
 
+static susp_status device_status(susp* h) {
+  cudaError_t e = cudaStreamSynchronize(stream_of(h));
+  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+  int err = 0;
+  e = cudaMemcpy(&err, h->v.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(SUSP_ECUDA, std::string("read error flag: ") + cudaGetErrorString(e));
+  return err_status(err);
+}
+
+// Rebuild the boundary links of this box from its current populations.
 static void refresh_links(susp* h) {
-  launch_links(h->prec, h->v, h->fin, h->stream);
+  launch_links(h->prec, h->eng.B, h->v.n, stream_of(h));
+}
+
+static Proto read_proto(susp* h) {
+  Proto pr;
+  cudaMemcpy(&pr, h->v.proto, sizeof pr, cudaMemcpyDeviceToHost);
+  return pr;
 }
 
 void susp_set_last_error(const char* msg) { g_err = msg; }
@@ -324,12 +536,9 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   h->prec = (int)p->prec;
   h->L = L;
   h->ws = (char*)dev_workspace;
-  h->stream = (cudaStream_t)cuda_stream;
-  h->parity = 0;
   h->have_shear = false;
+  h->batch = nullptr;
   h->radius.assign(p->radius, p->radius + p->n);
-  h->prof = false;
-  h->prof_n = 0;
   h->scale = p->prec == SUSP_FP16_DEV ? 4096.0 : 1.0;
   char* w = h->ws;
   View& v = h->v;
@@ -339,15 +548,20 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.ncell = (long long)p->nx * p->ny * p->nz;
   v.tau = p->tau; v.rho0 = p->rho0;
   for (int a = 0; a < 3; ++a) { v.g[a] = p->body_force[a]; v.g_f[a] = (float)p->body_force[a]; }
+  v.has_g = (p->body_force[0] != 0.0 || p->body_force[1] != 0.0 || p->body_force[2] != 0.0);
   v.scale = (float)h->scale; v.inv_scale = (float)(1.0 / h->scale);
   v.omega_d = 1.0 / p->tau; v.vf_d = -(1.0 - 0.5 / p->tau);
   v.omega_f = (float)v.omega_d; v.vf_f = (float)v.vf_d; v.rho0_f = (float)p->rho0;
   v.inv_nx_d = 1.0 / p->nx; v.inv_ny_d = 1.0 / p->ny; v.inv_nz_d = 1.0 / p->nz;
   v.inv_nx_f = (float)v.inv_nx_d; v.inv_ny_f = (float)v.inv_ny_d; v.inv_nz_f = (float)v.inv_nz_d;
+  v.fa = w + L.fa; v.fb = w + L.fb;
+  v.visc_acc = (double*)(w + L.vacc);
   v.mask = (uint32_t*)(w + L.mask); v.owner = (int*)(w + L.owner);
-  v.plane_mom = w + L.pm; v.visc_part = (double*)(w + L.visc); v.nblk_lb = lb_grid_blocks((int)p->prec, p->nx, p->ny, p->nz);
+  v.plane_mom = w + L.pm;
   v.n = n;
   v.R = (double*)(w + L.R); v.U = (double*)(w + L.U); v.W = (double*)(w + L.W);
+  v.R2 = (double*)(w + L.R2); v.U2 = (double*)(w + L.U2); v.W2 = (double*)(w + L.W2);
+  v.pcx = (int*)(w + L.pcx);
   v.rad = (double*)(w + L.rad); v.amap = (double*)(w + L.amap);
   v.mass = (double*)(w + L.mass); v.inert = (double*)(w + L.inert);
   v.inv_m = (double*)(w + L.imass); v.inv_I = (double*)(w + L.iinert);
@@ -398,26 +612,43 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.sums = (double*)(w + L.sums); v.hist = (double*)(w + L.hist);
   v.counters = (unsigned long long*)(w + L.counters);
   v.proto = (Proto*)(w + L.proto); v.err = (int*)(w + L.err);
-  h->fin = w + L.fa;
-  h->fout = w + L.fb;
 
-  cudaStream_t s = h->stream;
+  Engine& e = h->eng;
+  e.prec = h->prec;
+  e.stream = (cudaStream_t)cuda_stream;
+  std::vector<int> tabs;
+  eng_tables(e, std::vector<const View*>{&v}, tabs);
+  eng_bind(e, w + L.views, w + L.tabs, 1);
+
+  cudaStream_t s = e.stream;
   susp_status st = SUSP_OK;
   // zero everything past the populations, then fill
   st = cuda_check(cudaMemsetAsync(w + L.mask, 0, L.total - L.mask, s), "memset workspace");
   if (st) { delete h; return st; }
   cudaMemsetAsync(v.owner, 0xff, 4 * v.ncell, s);
+  cudaMemcpyAsync(w + L.views, &v, sizeof(View), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + L.tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
+  std::vector<double> zeros(3 * n, 0.0), im(n), iI(n);
+  // centres into the box (the offset is zero at creation: plain periodic wrap)
+  std::vector<double> R(p->pos, p->pos + 3 * n);
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) {
+      const double L = c == 0 ? p->nx : (c == 1 ? p->ny : p->nz);
+      double& x = R[3 * i + c];
+      x -= L * floor(x / L);
+      if (!(x >= 0.0 && x < L)) x = 0.0;
+    }
+  std::vector<int> off(n), cap(n);
   if (n > 0) {
-    std::vector<double> zeros(3 * n, 0.0);
-    std::vector<int> off(n), cap(n);
     long long acc = 0;
     for (int i = 0; i < n; ++i) {
       double am = amap[i] + 1.0;
       cap[i] = (int)ceil(6.0 * 4.0 * KPI * am * am) + 64;
       off[i] = (int)acc;
       acc += cap[i];
+      im[i] = 1.0 / mass[i];
+      iI[i] = 1.0 / inert[i];
     }
-    std::vector<double> R(p->pos, p->pos + 3 * n);
     cudaMemcpyAsync(v.R, R.data(), 24 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.U, p->vel ? p->vel : zeros.data(), 24 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.W, p->omega ? p->omega : zeros.data(), 24 * n, cudaMemcpyHostToDevice, s);
@@ -425,25 +656,23 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
     cudaMemcpyAsync(v.amap, amap.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.mass, mass.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inert, inert.data(), 8 * n, cudaMemcpyHostToDevice, s);
-    std::vector<double> im(n), iI(n);
-    for (int i = 0; i < n; ++i) { im[i] = 1.0 / mass[i]; iI[i] = 1.0 / inert[i]; }
     cudaMemcpyAsync(v.inv_m, im.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inv_I, iI.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.link_off, off.data(), 4 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.link_cap, cap.data(), 4 * n, cudaMemcpyHostToDevice, s);
-    // synchronous copies above read pageable host memory; wait before the vectors go away
-    st = cuda_check(cudaStreamSynchronize(s), "upload particles");
-    if (st) { delete h; return st; }
   }
   Proto pr;
   memset(&pr, 0, sizeof pr);
   pr.ny = p->ny;
   cudaMemcpyAsync(v.proto, &pr, sizeof pr, cudaMemcpyHostToDevice, s);
+  // the copies above read pageable host memory: wait before it goes away
+  st = cuda_check(cudaStreamSynchronize(s), "upload");
+  if (st) { delete h; return st; }
   k_proto_set<<<1, 1, 0, s>>>(v.proto, v.nx, 0, 0.0, 0.0, 0.0, 0.0);
-  launch_init_pop(h->prec, v, h->fin, s);
-  launch_init_pop(h->prec, v, h->fout, s);
+  launch_init_pop(h->prec, v, v.fa, s);
+  launch_init_pop(h->prec, v, v.fb, s);
   launch_write_plb(v, h->prec == 0, s);
-  launch_claim(h->prec, v, s);
+  launch_claim(h->prec, e.B, n, s);
   refresh_links(h);
   st = cuda_check(cudaGetLastError(), "launch");
   if (st) { delete h; return st; }
@@ -453,40 +682,27 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   return SUSP_OK;
 }
 
+// Set the box's shear protocol at its current step (no-op when unchanged).
+static void set_shear(susp* h, const susp_shear* sh) {
+  if (h->have_shear && memcmp(&h->shear, sh, sizeof(susp_shear)) == 0) return;
+  k_proto_set<<<1, 1, 0, stream_of(h)>>>(h->v.proto, h->v.nx, sh->kind, sh->rate, sh->gamma0, sh->omega,
+                                         sh->theta);
+  refresh_links(h);   // the image velocity of the boundary links changed
+  h->shear = *sh;
+  h->have_shear = true;
+}
+
 susp_status susp_step(susp* h, int nsteps, const susp_shear* sh) {
   if (!h || !sh || nsteps < 0) return fail(SUSP_EINVAL, "bad argument to susp_step");
   if (sh->kind != 0 && sh->kind != 1) return fail(SUSP_EINVAL, "shear kind must be 0 or 1");
-  cudaStream_t s = h->stream;
-  View& v = h->v;
-  if (!h->have_shear || memcmp(&h->shear, sh, sizeof(susp_shear)) != 0) {
-    k_proto_set<<<1, 1, 0, s>>>(v.proto, v.nx, sh->kind, sh->rate, sh->gamma0, sh->omega, sh->theta);
-    refresh_links(h);   // the image velocity of the boundary links changed
-    h->shear = *sh;
-    h->have_shear = true;
-  }
-  for (int it = 0; it < nsteps; ++it) {
-    launch_plane_moments(h->prec, v, h->fin, s);
-    const bool timed = h->prof && h->prof_n < PROF_MAX;
-    if (timed) cudaEventRecord(h->ev[2 * h->prof_n], s);
-    launch_collide_stream(h->prec, v, h->fin, h->fout, s);
-    if (timed) { cudaEventRecord(h->ev[2 * h->prof_n + 1], s); ++h->prof_n; }
-    if (v.move && v.n > 0) {
-      for (int sub = 0; sub < v.nsub; ++sub) {
-        launch_dem_substep(v, h->parity, sub, h->prec == 0, s);
-        h->parity ^= 1;
-      }
-    }
-    k_finalize<<<FIN_BLOCKS, 256, 0, s>>>(v, (double*)(h->ws + h->L.finp), (unsigned*)(h->ws + h->L.finc));
-    launch_node_update(h->prec, v, h->fout, s);
-    launch_links(h->prec, v, h->fout, s);
-    std::swap(h->fin, h->fout);
-  }
-  return cuda_check(cudaGetLastError(), "launch");
+  if (h->batch && nsteps > 0) return fail(SUSP_ESTATE, "box is attached to a batch: step the batch");
+  set_shear(h, sh);
+  return eng_step(h->eng, nsteps);
 }
 
 susp_status susp_stress_reset(susp* h) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
-  cudaStream_t s = h->stream;
+  cudaStream_t s = stream_of(h);
   cudaMemsetAsync(h->v.sums, 0, 8 * 72, s);
   cudaMemsetAsync(h->v.hist, 0, 8 * 3 * h->v.nbins, s);
   cudaMemsetAsync(h->v.counters, 0, 8 * 2, s);
@@ -647,7 +863,8 @@ susp_status susp_get_populations(susp* h, double* f) {
   const long long nc = h->v.ncell, tot = 19 * nc;
   const size_t es = esize(h->prec);
   std::vector<char> raw(tot * es);
-  st = cuda_check(cudaMemcpy(raw.data(), h->fin, raw.size(), cudaMemcpyDeviceToHost), "read populations");
+  const void* fin = (read_proto(h).t & 1) ? h->v.fb : h->v.fa;
+  st = cuda_check(cudaMemcpy(raw.data(), fin, raw.size(), cudaMemcpyDeviceToHost), "read populations");
   if (st) return st;
   const double inv = 1.0 / h->scale;
   for (long long k = 0; k < tot; ++k) {
@@ -678,9 +895,10 @@ susp_status susp_set_populations(susp* h, const double* f) {
       default: ((uint16_t*)raw.data())[k] = float_to_bf16((float)((f[k] - base) * h->scale)); break;
     }
   }
-  susp_status st = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  susp_status st = cuda_check(cudaStreamSynchronize(stream_of(h)), "sync");
   if (st) return st;
-  st = cuda_check(cudaMemcpy(h->fin, raw.data(), raw.size(), cudaMemcpyHostToDevice), "write populations");
+  void* fin = (read_proto(h).t & 1) ? h->v.fb : h->v.fa;
+  st = cuda_check(cudaMemcpy(fin, raw.data(), raw.size(), cudaMemcpyHostToDevice), "write populations");
   if (st) return st;
   refresh_links(h);
   return device_status(h);
@@ -697,8 +915,8 @@ susp_status susp_get_time(susp* h, int64_t* t, double* delta) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
   susp_status st = device_status(h);
   if (st) return st;
-  Proto pr;
-  st = cuda_check(cudaMemcpy(&pr, h->v.proto, sizeof pr, cudaMemcpyDeviceToHost), "read protocol");
+  const Proto pr = read_proto(h);
+  st = cuda_check(cudaGetLastError(), "read protocol");
   if (st) return st;
   if (t) *t = pr.t;
   if (delta) *delta = pr.delta;
@@ -709,7 +927,7 @@ susp_status susp_get_info(susp* h, susp_info* info) {
   if (!h || !info) return fail(SUSP_EINVAL, "NULL argument");
   const View& v = h->v;
   int dem = 0;
-  if (v.move && v.n > 0) dem = v.nsub * ((v.brute ? 0 : 4) + 2);
+  if (v.move && v.n > 0) dem = (v.brute ? 0 : 4) + 1;
   info->dem_substeps = v.nsub;
   info->launches_per_step = 2 + dem + 1 + (v.n > 0 ? 3 : 0);
   info->brute_force_pairs = v.brute;
@@ -720,39 +938,150 @@ susp_status susp_get_info(susp* h, susp_info* info) {
 
 susp_status susp_profile(susp* h, int enable) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
-  if (enable && h->ev.empty()) {
-    h->ev.resize(2 * PROF_MAX);
-    for (auto& e : h->ev) {
-      susp_status st = cuda_check(cudaEventCreate(&e), "cudaEventCreate");
-      if (st) return st;
-    }
-  }
-  h->prof = enable != 0;
-  h->prof_n = 0;
-  return SUSP_OK;
+  return eng_profile(h->eng, enable);
 }
 
 susp_status susp_profile_read(susp* h, double* ms_total, int* launches) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
-  susp_status st = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  return eng_profile_read(h->eng, ms_total, launches);
+}
+
+susp_status susp_set_graphs(susp* h, int enable) {
+  if (!h) return fail(SUSP_EINVAL, "NULL handle");
+  susp_status st = cuda_check(cudaStreamSynchronize(h->eng.stream), "sync");
   if (st) return st;
-  double tot = 0.0;
-  for (int k = 0; k < h->prof_n; ++k) {
-    float ms = 0.0f;
-    st = cuda_check(cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]), "cudaEventElapsedTime");
-    if (st) return st;
-    tot += ms;
-  }
-  if (ms_total) *ms_total = tot;
-  if (launches) *launches = h->prof_n;
-  h->prof_n = 0;
+  eng_drop_graphs(h->eng);
+  h->eng.use_graphs = enable != 0;
   return SUSP_OK;
 }
 
 void susp_destroy(susp* h) {
   if (!h) return;
-  for (auto& e : h->ev) cudaEventDestroy(e);
+  if (h->batch) susp_batch_detach(h->batch, h);
+  eng_release(h->eng);
   delete h;
+}
+
+// ------------------------------------------------------------ batches
+
+size_t susp_batch_workspace_bytes(int max_boxes) {
+  if (max_boxes < 1) { g_err = "max_boxes must be >= 1"; return 0; }
+  return al(sizeof(View) * (size_t)max_boxes) + al(4 * sizeof(int) * (size_t)(max_boxes + 1)) +
+         al(sizeof(int) * (size_t)max_boxes);
+}
+
+susp_status susp_batch_create(int max_boxes, void* dev_workspace, size_t bytes, void* cuda_stream,
+                              susp_batch** out) {
+  if (out) *out = nullptr;
+  if (!out) return fail(SUSP_EINVAL, "out is NULL");
+  if (max_boxes < 1) return fail(SUSP_EINVAL, "max_boxes must be >= 1");
+  if (!dev_workspace || ((uintptr_t)dev_workspace & 255)) return fail(SUSP_EINVAL, "workspace NULL or not 256-byte aligned");
+  if (bytes < susp_batch_workspace_bytes(max_boxes)) return fail(SUSP_ENOMEM, "workspace smaller than susp_batch_workspace_bytes()");
+  if (!cuda_stream) return fail(SUSP_EINVAL, "a batch needs its own (non-default) stream");
+  susp_batch* b = new susp_batch();
+  b->max_boxes = max_boxes;
+  b->prec = -1;
+  b->ws = (char*)dev_workspace;
+  b->eng.stream = (cudaStream_t)cuda_stream;
+  return (*out = b, SUSP_OK);
+}
+
+// Upload the views and prefix tables of the attached boxes and reset the
+// captured graphs (the launch shapes change with the membership).
+static susp_status batch_rebuild(susp_batch* b) {
+  Engine& e = b->eng;
+  susp_status st = cuda_check(cudaStreamSynchronize(e.stream), "sync");
+  if (st) return st;
+  eng_drop_graphs(e);
+  const int nb = (int)b->boxes.size();
+  if (nb == 0) { e.nbox = 0; b->prec = -1; return SUSP_OK; }
+  e.prec = b->prec;
+  std::vector<const View*> vs;
+  std::vector<View> hv;
+  for (susp* h : b->boxes) { vs.push_back(&h->v); hv.push_back(h->v); }
+  std::vector<int> tabs;
+  eng_tables(e, vs, tabs);
+  char* views = b->ws;
+  char* tp = b->ws + al(sizeof(View) * (size_t)b->max_boxes);
+  eng_bind(e, views, tp, nb);
+  cudaMemcpyAsync(views, hv.data(), sizeof(View) * nb, cudaMemcpyHostToDevice, e.stream);
+  cudaMemcpyAsync(tp, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, e.stream);
+  return cuda_check(cudaStreamSynchronize(e.stream), "upload batch tables");
+}
+
+susp_status susp_batch_attach(susp_batch* b, susp* h) {
+  if (!b || !h) return fail(SUSP_EINVAL, "NULL argument");
+  if (h->batch) return fail(SUSP_ESTATE, "box is already attached to a batch");
+  if ((int)b->boxes.size() >= b->max_boxes) return fail(SUSP_ENOMEM, "batch is full");
+  if (b->prec >= 0 && b->prec != h->prec) return fail(SUSP_EINVAL, "boxes of one batch share the storage precision");
+  if (!h->have_shear) return fail(SUSP_ESTATE, "set the box's shear protocol (susp_step with nsteps = 0) first");
+  susp_status st = cuda_check(cudaStreamSynchronize(h->eng.stream), "sync box");
+  if (st) return st;
+  b->prec = h->prec;
+  b->boxes.push_back(h);
+  h->batch = b;
+  st = batch_rebuild(b);
+  if (st) { b->boxes.pop_back(); h->batch = nullptr; batch_rebuild(b); }
+  return st;
+}
+
+susp_status susp_batch_detach(susp_batch* b, susp* h) {
+  if (!b || !h) return fail(SUSP_EINVAL, "NULL argument");
+  auto it = std::find(b->boxes.begin(), b->boxes.end(), h);
+  if (it == b->boxes.end()) return fail(SUSP_ESTATE, "box is not attached to this batch");
+  susp_status st = cuda_check(cudaStreamSynchronize(b->eng.stream), "sync batch");
+  b->boxes.erase(it);
+  h->batch = nullptr;
+  susp_status st2 = batch_rebuild(b);
+  return st ? st : st2;
+}
+
+int susp_batch_size(const susp_batch* b) { return b ? (int)b->boxes.size() : 0; }
+
+susp_status susp_batch_step(susp_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return fail(SUSP_EINVAL, "bad argument to susp_batch_step");
+  if (b->boxes.empty()) return SUSP_OK;
+  return eng_step(b->eng, nsteps);
+}
+
+susp_status susp_batch_profile(susp_batch* b, int enable) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  return eng_profile(b->eng, enable);
+}
+
+susp_status susp_batch_profile_read(susp_batch* b, double* ms_total, int* launches) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  return eng_profile_read(b->eng, ms_total, launches);
+}
+
+susp_status susp_batch_errors(susp_batch* b, int* status, int n) {
+  if (!b || (!status && n > 0)) return fail(SUSP_EINVAL, "NULL argument");
+  const int nb = (int)b->boxes.size();
+  if (n < nb) return fail(SUSP_EINVAL, "status array shorter than the batch");
+  if (nb == 0) return SUSP_OK;
+  Engine& e = b->eng;
+  int* dev = (int*)(b->ws + al(sizeof(View) * (size_t)b->max_boxes) +
+                    al(4 * sizeof(int) * (size_t)(b->max_boxes + 1)));
+  k_gather_err<<<(nb + 127) / 128, 128, 0, e.stream>>>(e.B, dev);
+  std::vector<int> err(nb);
+  susp_status st = cuda_check(cudaMemcpyAsync(err.data(), dev, sizeof(int) * nb, cudaMemcpyDeviceToHost,
+                                              e.stream), "read error words");
+  if (st) return st;
+  st = cuda_check(cudaStreamSynchronize(e.stream), "sync batch");
+  if (st) return st;
+  const std::string keep = g_err;
+  for (int k = 0; k < nb; ++k) status[k] = (int)err_status(err[k]);
+  g_err = keep;
+  return SUSP_OK;
+}
+
+void susp_batch_destroy(susp_batch* b) {
+  if (!b) return;
+  if (b->eng.stream) cudaStreamSynchronize(b->eng.stream);
+  for (susp* h : b->boxes) h->batch = nullptr;
+  b->boxes.clear();
+  eng_release(b->eng);
+  delete b;
 }
 
 }  // extern "C"

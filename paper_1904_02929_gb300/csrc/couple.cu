@@ -38,7 +38,11 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
 #pragma unroll
   for (int k = -1; k <= 1; ++k) {
     ImgBox& B = b[k + 1];
-    const TC cx = Rx + (TC)k * delta, cy = Ry + (TC)k * (TC)v.ny, cz = Rz;
+    // image centre, x brought back into [0, nx): Rx + k delta can lie up to one
+    // period outside (0 <= delta < nx), and the cell visit wraps x only once
+    TC cx = Rx + (TC)k * delta;
+    cx -= (TC)v.nx * floor(cx * sel<TC>(v.inv_nx_d, v.inv_nx_f));
+    const TC cy = Ry + (TC)k * (TC)v.ny, cz = Rz;
     int y0 = (int)ceil(cy - reach), y1 = (int)floor(cy + reach);
     if (y0 < 0) y0 = 0;
     if (y1 > v.ny - 1) y1 = v.ny - 1;
@@ -53,7 +57,8 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
 }
 
 // Visit the cells of a particle's image boxes: half-warps take (y, z) rows and
-// their 16 lanes run along x (coalesced).  fn(x, y, z, c, dx, dy, dz, k) gets
+// their 16 lanes run along x (coalesced).  Box corners lie less than one period
+// outside the lattice (reach < L / 2, centres in [0, L)), so one wrap suffices.  fn(x, y, z, c, dx, dy, dz, k) gets
 // the cell index and the minimum-image displacement from the particle centre.
 template <typename TC, typename F>
 __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox (&b)[3], TC Rx, TC Ry, TC Rz,
@@ -66,9 +71,9 @@ __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox (&b)[3
     const int rows = B.ey * B.ez;
     for (int row = half; row < rows; row += nhalf) {
       const int lz = row / B.ey, ly = row - lz * B.ey;
-      const int y = B.y0 + ly, z = wrapi(B.z0 + lz, v.nz);
+      const int y = B.y0 + ly, z = wrap1(B.z0 + lz, v.nz);
       for (int lx = lane; lx < B.ex; lx += 16) {
-        const int x = wrapi(B.x0 + lx, v.nx);
+        const int x = wrap1(B.x0 + lx, v.nx);
         TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
         const int k = le_image_v(v, dx, dy, dz, delta);
         const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
@@ -85,9 +90,12 @@ __device__ inline TC pule(const Proto* pr) { return sel<TC>(pr->ule, pr->ule_f);
 
 // Initial claim of the solid nodes (creation).
 template <int P>
-__global__ void k_claim(View v) {
+__global__ void k_claim(Batch B) {
   using TC = typename Store<P>::C;
-  const int i = blockIdx.x;
+  const int g = blockIdx.x;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  const int i = g - B.part_off[bx];
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
@@ -104,11 +112,15 @@ __global__ void k_claim(View v) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) k_uncover(View v, typename Store<P>::T* __restrict__ f) {
+__global__ void __launch_bounds__(256) k_uncover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
-  const int i = blockIdx.x;
+  const int g = blockIdx.x;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  const int i = g - B.part_off[bx];
+  typename Store<P>::T* __restrict__ f = static_cast<typename Store<P>::T*>(fin_of(v));
   // clear the mask bits of last step's links of this particle
   const int off = v.link_off[i], nl = v.link_cnt[i];
   for (int k = threadIdx.x; k < nl; k += blockDim.x) {
@@ -152,11 +164,15 @@ __global__ void __launch_bounds__(256) k_uncover(View v, typename Store<P>::T* _
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::T* __restrict__ f) {
+__global__ void __launch_bounds__(256) k_cover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
-  const int i = blockIdx.x;
+  const int g = blockIdx.x;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  const int i = g - B.part_off[bx];
+  const typename Store<P>::T* __restrict__ f = static_cast<const typename Store<P>::T*>(fin_of(v));
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
@@ -193,38 +209,50 @@ __global__ void __launch_bounds__(256) k_cover(View v, const typename Store<P>::
   }
 }
 
-// Node that pulls population p from solid node (x, y, z); returns its index
-// and owner.  crossing = the pull passes a Lees-Edwards plane.
-__device__ inline long long link_target(const View& v, const Proto* pr, int x, int y, int z, int p,
-                                        int& rx, int& ry, int& rz, bool& crossing, int& own) {
+// Node that pulls population p from solid node (x, y, z); returns its index.
+// crossing = the pull passes a Lees-Edwards plane.
+__device__ __forceinline__ long long link_target_nr(const View& v, const Proto* pr, int x, int y, int z,
+                                                    int p, int& rx, int& ry, int& rz, bool& crossing) {
   const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
   ry = y + cpy;
-  rz = wrapi(z + cpz, v.nz);
+  rz = z + cpz;
+  if (rz < 0) rz += v.nz;
+  else if (rz >= v.nz) rz -= v.nz;
   crossing = (ry < 0) || (ry >= v.ny);
+  int xx;
   if (!crossing) {
-    rx = wrapi(x + cpx, v.nx);
+    xx = x + cpx;
   } else if (ry >= v.ny) {
     // receiver at y = 0 pulls from below: nearest source x_r - c_px + di + near_lo
     ry = 0;
-    rx = wrapi(x + cpx - pr->di - pr->near_lo, v.nx);
+    xx = x + cpx - pr->di - pr->near_lo;
   } else {
     // receiver at y = ny-1 pulls from above: nearest source x_r - c_px - di - 1 + near_hi
     ry = v.ny - 1;
-    rx = wrapi(x + cpx + pr->di + 1 - pr->near_hi, v.nx);
+    xx = x + cpx + pr->di + 1 - pr->near_hi;
   }
-  const long long r = rx + (long long)v.nx * (ry + (long long)v.ny * rz);
-  own = v.owner[r];
-  return r;
+  rx = crossing ? wrapi(xx, v.nx) : wrap1(xx, v.nx);
+  return rx + (long long)v.nx * (ry + (long long)v.ny * rz);
 }
 
+// Links of one particle in two passes: the block first collects its solid
+// nodes near the mapped surface into shared memory, then its threads take
+// (node, direction) work items, so every lane does the same work.
+constexpr int LINK_NODES_MAX = 2048;
+
 template <int P>
-__global__ void __launch_bounds__(256) k_links(View v, const typename Store<P>::T* __restrict__ f) {
+__global__ void __launch_bounds__(256) k_links(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 15];
-  __shared__ int s_count;
-  const int i = blockIdx.x;
-  if (threadIdx.x == 0) s_count = 0;
+  __shared__ int s_count, s_nodes;
+  __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
+  const int g = blockIdx.x;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  const int i = g - B.part_off[bx];
+  const typename Store<P>::T* __restrict__ f = static_cast<const typename Store<P>::T*>(fin_of(v));
+  if (threadIdx.x == 0) { s_count = 0; s_nodes = 0; }
   __syncthreads();
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
@@ -235,62 +263,83 @@ __global__ void __launch_bounds__(256) k_links(View v, const typename Store<P>::
   const int off = v.link_off[i], cap = v.link_cap[i];
   ImgBox b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
-  TC acc[15];
-#pragma unroll
-  for (int k = 0; k < 15; ++k) acc[k] = 0;
   // A link's receiver lies within sqrt(2) of its solid node, or -- across a
   // Lees-Edwards plane, where the receiver is the node whose nearest source is
   // s -- within sqrt(1.5^2 + 1) = 1.80; deeper solid nodes cannot have links.
   const TC inner = am > (TC)2 ? am - (TC)2 : (TC)0;
+  bool overflow = false;
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int x, int y, int z, long long s, TC sdx, TC sdy, TC sdz, int) {
     const TC d2 = sdx * sdx + sdy * sdy + sdz * sdz;
     if (!(d2 < am * am) || d2 < inner * inner) return;
     if (v.owner[s] != i) return;
-    for (int p = 1; p < 19; ++p) {
-      int rx, ry, rz, own;
-      bool crossing;
-      const long long r = link_target(v, pr, x, y, z, p, rx, ry, rz, crossing, own);
-      // warp-aggregated slot in the particle's link segment (non-crossing fluid links)
-      const bool want = own < 0 && !crossing;
-      const unsigned act = __activemask();
-      const unsigned bal = __ballot_sync(act, want);
-      if (bal) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(bal) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&s_count, __popc(bal));
-        base = __shfl_sync(act, base, leader);
-        if (want) {
-          const int slot = base + __popc(bal & ((1u << lane) - 1u));
+    const int k = atomicAdd(&s_nodes, 1);
+    if (k < LINK_NODES_MAX) s_node[k] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
+    else overflow = true;
+  });
+  if (overflow) atomicOr(v.err, ERR_LINKS);
+  __syncthreads();
+  const int nn = min(s_nodes, LINK_NODES_MAX);
+  TC acc[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) acc[k] = 0;
+  const int items = nn * 18;
+  const int lane = threadIdx.x & 31;
+  // round the loop up to whole warps so the ballot below sees full warps
+  const int items_r = (items + 31) & ~31;
+  for (int t = threadIdx.x; t < items_r; t += blockDim.x) {
+    const bool valid = t < items;
+    int x = 0, y = 0, z = 0, p = 1;
+    if (valid) {
+      const uint32_t w = s_node[t / 18];
+      p = 1 + t % 18;
+      x = (int)(w & 2047u); y = (int)((w >> 11) & 2047u); z = (int)(w >> 22);
+    }
+    int rx, ry, rz;
+    bool crossing;
+    const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);
+    const int ow = valid ? v.owner[r] : i;
+    // slot in the particle's link segment for non-crossing fluid links
+    const bool want = valid && ow < 0 && !crossing;
+    const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (bal) {
+      const int leader = __ffs(bal) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&s_count, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const int slot = base + __popc(bal & ((1u << lane) - 1u));
+        // a link that does not fit is not set (its bit could never be cleared)
+        if (slot < cap) {
           atomicOr(v.mask + r, 1u << p);
-          if (slot < cap) v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
+          v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
         }
       }
-      if (own == i) continue;
-      const int q = D3Q19::opp(p);
-      const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
-      TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
-      const int k = le_image_v(v, dx, dy, dz, delta);
-      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
-      const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
-      const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
-      const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
-      const TC wqq = wq<TC>(q);
-      TC mag;
-      if (own < 0) {
-        const TC nq = S::load(f, (long long)q * v.ncell + r, wqq * rho0, (TC)v.inv_scale);
-        mag = (TC)2 * nq - (TC)6 * wqq * rho0 * cu;
-      } else {
-        mag = (TC)2 * wqq * rho0;   // another particle's node: fluid at rest
-      }
-      const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
-      acc[0] += fx; acc[1] += fy; acc[2] += fz;
-      acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
-      acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
-      acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
-      acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
     }
-  });
+    if (ow == i) continue;
+    const int q = D3Q19::opp(p);
+    const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+    TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
+    const int k = le_image_v(v, dx, dy, dz, delta);
+    const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+    const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+    const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+    const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
+    const TC wqq = wq<TC>(q);
+    // fluid receiver: momentum exchange; another particle's node: fluid at rest
+    TC mag;
+    if (ow < 0) {
+      const TC nq = S::load(f, (long long)q * v.ncell + r, wqq * rho0, (TC)v.inv_scale);
+      mag = (TC)2 * nq - (TC)6 * wqq * rho0 * cu;
+    } else {
+      mag = (TC)2 * wqq * rho0;
+    }
+    const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
+    acc[0] += fx; acc[1] += fy; acc[2] += fz;
+    acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
+    acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
+    acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
+    acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+  }
   block_sum<TC, 15>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -318,55 +367,36 @@ __global__ void k_init_pop(View v, typename Store<P>::T* __restrict__ f) {
 
 using namespace susp_dev;
 
-#define SUSP_DISPATCH(prec, KER, grid, block, stream, ...)                                        \
-  switch (prec) {                                                                                \
-    case 0: KER<0><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
-    case 1: KER<1><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
-    case 2: KER<2><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                              \
-    default: KER<3><<<grid, block, 0, stream>>>(__VA_ARGS__); break;                             \
-  }
-
 template <int P> using PT = typename Store<P>::T;
 
-void launch_claim(int prec, const View& v, cudaStream_t s) {
-  if (v.n == 0) return;
+void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s) {
+  if (nparts == 0) return;
   switch (prec) {
-    case 0: k_claim<0><<<v.n, 128, 0, s>>>(v); break;
-    case 1: k_claim<1><<<v.n, 128, 0, s>>>(v); break;
-    case 2: k_claim<2><<<v.n, 128, 0, s>>>(v); break;
-    default: k_claim<3><<<v.n, 128, 0, s>>>(v); break;
+    case 0: k_claim<0><<<nparts, 128, 0, s>>>(B); break;
+    case 1: k_claim<1><<<nparts, 128, 0, s>>>(B); break;
+    case 2: k_claim<2><<<nparts, 128, 0, s>>>(B); break;
+    default: k_claim<3><<<nparts, 128, 0, s>>>(B); break;
   }
 }
 
-void launch_node_update(int prec, const View& v, void* f, cudaStream_t s) {
-  if (v.n == 0) return;
+// Node-map update after the particles moved: uncover, then cover.
+void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s) {
+  if (nparts == 0) return;
   switch (prec) {
-    case 0:
-      k_uncover<0><<<v.n, 256, 0, s>>>(v, (PT<0>*)f);
-      k_cover<0><<<v.n, 256, 0, s>>>(v, (const PT<0>*)f);
-      break;
-    case 1:
-      k_uncover<1><<<v.n, 256, 0, s>>>(v, (PT<1>*)f);
-      k_cover<1><<<v.n, 256, 0, s>>>(v, (const PT<1>*)f);
-      break;
-    case 2:
-      k_uncover<2><<<v.n, 256, 0, s>>>(v, (PT<2>*)f);
-      k_cover<2><<<v.n, 256, 0, s>>>(v, (const PT<2>*)f);
-      break;
-    default:
-      k_uncover<3><<<v.n, 256, 0, s>>>(v, (PT<3>*)f);
-      k_cover<3><<<v.n, 256, 0, s>>>(v, (const PT<3>*)f);
-      break;
+    case 0: k_uncover<0><<<nparts, 256, 0, s>>>(B); k_cover<0><<<nparts, 256, 0, s>>>(B); break;
+    case 1: k_uncover<1><<<nparts, 256, 0, s>>>(B); k_cover<1><<<nparts, 256, 0, s>>>(B); break;
+    case 2: k_uncover<2><<<nparts, 256, 0, s>>>(B); k_cover<2><<<nparts, 256, 0, s>>>(B); break;
+    default: k_uncover<3><<<nparts, 256, 0, s>>>(B); k_cover<3><<<nparts, 256, 0, s>>>(B); break;
   }
 }
 
-void launch_links(int prec, const View& v, const void* f, cudaStream_t s) {
-  if (v.n == 0) return;
+void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s) {
+  if (nparts == 0) return;
   switch (prec) {
-    case 0: k_links<0><<<v.n, 256, 0, s>>>(v, (const PT<0>*)f); break;
-    case 1: k_links<1><<<v.n, 256, 0, s>>>(v, (const PT<1>*)f); break;
-    case 2: k_links<2><<<v.n, 256, 0, s>>>(v, (const PT<2>*)f); break;
-    default: k_links<3><<<v.n, 256, 0, s>>>(v, (const PT<3>*)f); break;
+    case 0: k_links<0><<<nparts, 256, 0, s>>>(B); break;
+    case 1: k_links<1><<<nparts, 256, 0, s>>>(B); break;
+    case 2: k_links<2><<<nparts, 256, 0, s>>>(B); break;
+    default: k_links<3><<<nparts, 256, 0, s>>>(B); break;
   }
 }
 

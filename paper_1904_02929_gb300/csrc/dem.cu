@@ -17,13 +17,19 @@
 // d -= k (Delta, L_y, 0), and b's image moves with U_b + k U_LE e_x.
 // Integration (Eq. 1): semi-implicit Euler with the hydrodynamic link force
 // held over the sub-steps; Lees-Edwards wrap of the centres at the end.
+#include <cooperative_groups.h>
+
 #include "susp_dev.cuh"
 
 namespace susp_dev {
 
-__global__ void k_cell_count(View v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= v.n) return;
+__global__ void k_cell_count(Batch B) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B.part_off[B.nbox]) return;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  if (v.brute || !v.move) return;
+  const int i = g - B.part_off[bx];
   double x = v.R[3 * i], y = v.R[3 * i + 1], z = v.R[3 * i + 2];
   x -= v.nx * floor(x * v.inv_nx_d);
   z -= v.nz * floor(z * v.inv_nz_d);
@@ -34,11 +40,23 @@ __global__ void k_cell_count(View v) {
   const int c = cx + v.ncx * (cy + v.ncy * cz);
   v.pcell[i] = c;
   atomicAdd(v.cell_cnt + c, 1);
+  // cells searched around i during this step's sub-steps; the rows beyond the
+  // Lees-Edwards planes are shifted by -/+ Delta
+  const double delta = v.proto->delta;
+  double xb = x + delta, xa = x - delta;
+  xb -= v.nx * floor(xb * v.inv_nx_d);
+  xa -= v.nx * floor(xa * v.inv_nx_d);
+  int* pc = v.pcx + 8 * i;
+  pc[0] = cx; pc[1] = cy; pc[2] = cz;
+  pc[3] = min(max((int)floor(xb * v.inv_csx), 0), v.ncx - 1);
+  pc[4] = min(max((int)floor(xa * v.inv_csx), 0), v.ncx - 1);
 }
 
-// Exclusive scan of the cell counts (one block of 1024 threads).
-__global__ void k_cell_scan(View v) {
+// Exclusive scan of one box's cell counts per block (1024 threads).
+__global__ void k_cell_scan(Batch B) {
   __shared__ int part[1024];
+  const View& v = B.views[blockIdx.x];
+  if (v.brute || !v.move || v.n == 0) return;
   const int nc = v.ncells, T = blockDim.x, t = threadIdx.x;
   const int chunk = (nc + T - 1) / T;
   const int b0 = t * chunk, b1 = min(nc, b0 + chunk);
@@ -62,18 +80,27 @@ __global__ void k_cell_scan(View v) {
   if (t == T - 1) v.cell_start[nc] = part[T - 1];
 }
 
-__global__ void k_cell_fill(View v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= v.n) return;
+__global__ void k_cell_fill(Batch B) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B.part_off[B.nbox]) return;
+  const int bx = box_of(B.part_off, B.nbox, g);
+  const View& v = B.views[bx];
+  if (v.brute || !v.move) return;
+  const int i = g - B.part_off[bx];
   const int c = v.pcell[i];
   const int slot = atomicAdd(v.cell_cnt + c, 1);
   v.cell_ids[v.cell_start[c] + slot] = i;
 }
 
-// Sort each cell's ids ascending so the gather order is deterministic.
-__global__ void k_cell_sort(View v) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= v.ncells) return;
+// Sort each cell's ids ascending so the gather order is deterministic; the
+// counts are cleared for the next step's count.
+__global__ void k_cell_sort(Batch B) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B.cell_off[B.nbox]) return;
+  const int bx = box_of(B.cell_off, B.nbox, g);
+  const View& v = B.views[bx];
+  if (v.brute || !v.move) return;
+  const int c = g - B.cell_off[bx];
   const int s = v.cell_start[c], e = v.cell_start[c + 1];
   for (int a = s + 1; a < e; ++a) {
     const int key = v.cell_ids[a];
@@ -81,6 +108,7 @@ __global__ void k_cell_sort(View v) {
     while (b >= s && v.cell_ids[b] > key) { v.cell_ids[b + 1] = v.cell_ids[b]; --b; }
     v.cell_ids[b + 1] = key;
   }
+  v.cell_cnt[c] = 0;
 }
 
 template <typename T>
@@ -105,40 +133,41 @@ struct PairOut {
   int touching;
 };
 
-// Minimum-image displacement R_b - R_a in FP64 (positions are FP64 on every
-// path); returns false when the pair is out of range.
-__device__ inline bool pair_geometry(const View& v, int a, int b, double delta, double d[3], int& k,
-                                     double& h) {
-  d[0] = v.R[3 * b] - v.R[3 * a];
-  d[1] = v.R[3 * b + 1] - v.R[3 * a + 1];
-  d[2] = v.R[3 * b + 2] - v.R[3 * a + 2];
-  k = (int)floor(d[1] * v.inv_ny_d + 0.5);
-  d[1] -= k * (double)v.ny;
-  d[0] -= k * delta;
-  d[0] -= v.nx * floor(d[0] * v.inv_nx_d + 0.5);
-  d[2] -= v.nz * floor(d[2] * v.inv_nz_d + 0.5);
-  const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  const double rsum = v.rad[a] + v.rad[b];
-  const double lim = rsum + v.hrange + 1e-9;
+// Minimum-image displacement R_b - R_a: the centre difference is taken in
+// FP64 (positions are FP64 on every path), the rest in precision T; returns
+// false when the pair is out of range.
+template <typename T>
+__device__ inline bool pair_geometry(const View& v, const double* __restrict__ Rs, int a, int b, T delta,
+                                     T d[3], int& k, T& h) {
+  d[0] = (T)(Rs[3 * b] - Rs[3 * a]);
+  d[1] = (T)(Rs[3 * b + 1] - Rs[3 * a + 1]);
+  d[2] = (T)(Rs[3 * b + 2] - Rs[3 * a + 2]);
+  const T fnx = (T)v.nx, fny = (T)v.ny, fnz = (T)v.nz;
+  k = (int)floor(d[1] * sel<T>(v.inv_ny_d, v.inv_ny_f) + (T)0.5);
+  d[1] -= (T)k * fny;
+  d[0] -= (T)k * delta;
+  d[0] -= fnx * floor(d[0] * sel<T>(v.inv_nx_d, v.inv_nx_f) + (T)0.5);
+  d[2] -= fnz * floor(d[2] * sel<T>(v.inv_nz_d, v.inv_nz_f) + (T)0.5);
+  const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const T rsum = (T)(v.rad[a] + v.rad[b]);
+  const T lim = rsum + (T)v.hrange + (T)1e-6;
   if (!(d2 < lim * lim)) return false;   // cheap rejection before the square root
   h = sqrt(d2) - rsum;
-  return (h < v.hrange) || (h < 0.0);
+  return (h < (T)v.hrange) || (h < (T)0);
 }
 
 // Full interaction of the canonical pair (a, b) in precision T, given the
-// minimum-image displacement.
+// minimum-image displacement d and gap h.
 template <typename T>
-__device__ void pair_interact(const View& v, int a, int b, const double dd[3], int k, double hd,
-                              const int* hcnt, const int* hpart, const double* hval, T ule, T dt,
-                              PairOut<T>& o) {
-  const T d[3] = {(T)dd[0], (T)dd[1], (T)dd[2]};
+__device__ void pair_interact(const View& v, const double* __restrict__ Us, const double* __restrict__ Ws,
+                              int a, int b, const T d[3], int k, T h, const int* hcnt, const int* hpart,
+                              const double* hval, T ule, T dt, PairOut<T>& o) {
   const T ra = (T)v.rad[a], rb = (T)v.rad[b];
   const T dist = sqrt(dot3(d, d));
-  const T h = (T)hd;
-  const T uab[3] = {(T)(v.U[3 * a] - v.U[3 * b]) - (T)k * ule, (T)(v.U[3 * a + 1] - v.U[3 * b + 1]),
-                    (T)(v.U[3 * a + 2] - v.U[3 * b + 2])};
-  const T wa[3] = {(T)v.W[3 * a], (T)v.W[3 * a + 1], (T)v.W[3 * a + 2]};
-  const T wb[3] = {(T)v.W[3 * b], (T)v.W[3 * b + 1], (T)v.W[3 * b + 2]};
+  const T uab[3] = {(T)(Us[3 * a] - Us[3 * b]) - (T)k * ule, (T)(Us[3 * a + 1] - Us[3 * b + 1]),
+                    (T)(Us[3 * a + 2] - Us[3 * b + 2])};
+  const T wa[3] = {(T)Ws[3 * a], (T)Ws[3 * a + 1], (T)Ws[3 * a + 2]};
+  const T wb[3] = {(T)Ws[3 * b], (T)Ws[3 * b + 1], (T)Ws[3 * b + 2]};
   const T n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
   for (int c = 0; c < 3; ++c) {
     o.Fa[c] = o.Ta[c] = o.Tb[c] = o.Fc[c] = o.Fr[c] = o.ht[c] = (T)0;
@@ -148,7 +177,7 @@ __device__ void pair_interact(const View& v, int a, int b, const double dd[3], i
   o.touching = 0;
   // ---- contact
   const T overlap = ra + rb - dist;
-  if (hd < 0.0) {
+  if (h < (T)0) {
     T ht[3] = {0, 0, 0};
     const int m = hcnt[a];
     for (int s = 0; s < m; ++s)
@@ -188,7 +217,7 @@ __device__ void pair_interact(const View& v, int a, int b, const double dd[3], i
     o.touching = 1;
   }
   // ---- double-layer repulsion
-  if (v.F0 > 0.0 && hd < 10.0 * v.debye) {
+  if (v.F0 > 0.0 && h < (T)(10.0 * v.debye)) {
     const T fr = (T)v.F0 * exp(-(h > (T)0 ? h : (T)0) / (T)v.debye);
     for (int c = 0; c < 3; ++c) {
       o.Fr[c] = -fr * n[c];
@@ -196,7 +225,7 @@ __device__ void pair_interact(const View& v, int a, int b, const double dd[3], i
     }
   }
   // ---- lubrication correction
-  if (v.lub_cut > 0.0 && hd < v.lub_cut) {
+  if (v.lub_cut > 0.0 && h < (T)v.lub_cut) {
     const T hh = h < (T)0 ? (T)0 : h;
     const T sc = (T)2 / (ra + rb);
     const T xi = sc * hh, xc = sc * (T)v.lub_cut, dl = sc * (T)v.lub_delta;
@@ -236,24 +265,91 @@ __device__ inline T warp_sum(T x) {
   return x;
 }
 
-// One warp per particle i; the lanes split the candidate partners (one
-// neighbour cell per lane, or a strided slice of all particles in brute-force
-// mode).  Forces are summed per lane and reduced across the warp.
+struct SpringTables {
+  const int* hcnt_old;
+  const int* hpart_old;
+  const double* hval_old;
+  int* hcnt_new;
+  int* hpart_new;
+  double* hval_new;
+};
+
+// Pair forces on particle i, computed by one warp: the lanes split the
+// candidate partners (one neighbour cell per lane, or a strided slice of all
+// particles in brute-force mode); sums are reduced across the warp and lane 0
+// writes them.  slot: this warp's shared counter of new spring slots.
+struct State {
+  const double *R, *U, *W;   // read: positions and velocities at the sub-step start
+  double *Rn, *Un, *Wn;      // write: after the sub-step
+};
+
+template <typename TC>
+__device__ inline void write_plb(const View& v, int i, const double* R, const double* U, const double* W) {
+  TC* pp = reinterpret_cast<TC*>(v.plb) + 12 * i;
+  for (int c = 0; c < 3; ++c) {
+    pp[c] = (TC)R[c];
+    pp[3 + c] = (TC)U[c];
+    pp[6 + c] = (TC)W[c];
+  }
+}
+
+// Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
+// the write state, with the pair force and torque (F, T); at the last sub-step
+// the Lees-Edwards wrap of the centre, the speed check and the compute-type copy.
+// Velocities are updated in precision T; positions always in FP64.
 template <typename T>
-__global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ hcnt_old,
-                                               const int* __restrict__ hpart_old,
-                                               const double* __restrict__ hval_old, int* hcnt_new,
-                                               int* hpart_new, double* hval_new, double dt_d, int sample) {
-  __shared__ int s_slot[4];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * 4 + wib;
-  if (lane == 0) s_slot[wib] = 0;
+__device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
+                                     double dt, bool last, bool plb_double) {
+  double R[3], U[3], W[3];
+  const T im = (T)v.inv_m[i], iI = (T)v.inv_I[i], dtt = (T)dt;
+  for (int c = 0; c < 3; ++c) {
+    const T F = (T)v.Fh[3 * i + c] + (T)v.Fcov[3 * i + c] + Fp[c];
+    const T Tq = (T)v.Th[3 * i + c] + (T)v.Tcov[3 * i + c] + Tp[c];
+    U[c] = (double)((T)S.U[3 * i + c] + dtt * F * im);
+    W[c] = (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
+  }
+  if (v.quasi2d) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
+  for (int c = 0; c < 3; ++c) R[c] = S.R[3 * i + c] + dt * U[c];
+  if (last) {
+    const Proto* pr = v.proto;
+    if (R[1] >= v.ny) { R[1] -= v.ny; R[0] -= pr->delta_n; U[0] -= pr->ule; }
+    else if (R[1] < 0.0) { R[1] += v.ny; R[0] += pr->delta_n; U[0] += pr->ule; }
+    if (R[0] < 0.0) R[0] += v.nx; else if (R[0] >= v.nx) R[0] -= v.nx;
+    if (R[2] < 0.0) R[2] += v.nz; else if (R[2] >= v.nz) R[2] -= v.nz;
+    const T sp2 = (T)(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    bool bad = !(sp2 < (T)0.25);
+    // Centres stay finite and inside the box whatever the dynamics did: the
+    // node-map kernels index the lattice from them.  x can still be one
+    // period out after a Lees-Edwards crossing at the x boundary; anything
+    // else out of range means the step was unstable.
+    const int Ls[3] = {v.nx, v.ny, v.nz};
+    for (int c = 0; c < 3; ++c) {
+      if (R[c] >= 0.0 && R[c] < Ls[c]) continue;
+      if (c != 0 || !isfinite(R[c])) bad = true;
+      R[c] = isfinite(R[c]) ? R[c] - Ls[c] * floor(R[c] / Ls[c]) : 0.0;
+      if (!(R[c] >= 0.0 && R[c] < Ls[c])) R[c] = 0.0;
+    }
+    if (bad) atomicOr(v.err, ERR_UNSTABLE);
+    if (plb_double) write_plb<double>(v, i, R, U, W);
+    else write_plb<float>(v, i, R, U, W);
+  }
+  for (int c = 0; c < 3; ++c) {
+    S.Rn[3 * i + c] = R[c];
+    S.Un[3 * i + c] = U[c];
+    S.Wn[3 * i + c] = W[c];
+  }
+}
+
+template <typename T>
+__device__ void pairs_of(const View& v, int i, const SpringTables& st, const State& S, T dt, int sample,
+                         bool last, int* slot) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) *slot = 0;
   __syncwarp();
-  if (i >= v.n) return;
   const Proto* pr = v.proto;
-  const double delta = pr->delta;
+  const double delta_d = pr->delta;
+  const T delta = (T)delta_d;
   const T ule = (T)pr->ule;
-  const T dt = (T)dt_d;
   T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   T cv[9], rv[9];
   for (int c = 0; c < 9; ++c) { cv[c] = (T)0; rv[c] = (T)0; }
@@ -264,18 +360,18 @@ __global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ h
   auto visit = [&](int j) {
     if (j == i) return;
     const int a = i < j ? i : j, b = i < j ? j : i;
-    double dd[3], hd;
+    T d[3], h;
     int k;
-    if (!pair_geometry(v, a, b, delta, dd, k, hd)) return;
+    if (!pair_geometry<T>(v, S.R, a, b, delta, d, k, h)) return;
     PairOut<T> o;
-    pair_interact<T>(v, a, b, dd, k, hd, hcnt_old, hpart_old, hval_old, ule, dt, o);
+    pair_interact<T>(v, S.U, S.W, a, b, d, k, h, st.hcnt_old, st.hpart_old, st.hval_old, ule, dt, o);
     if (i == a) {
       for (int c = 0; c < 3; ++c) { F[c] += o.Fa[c]; Tq[c] += o.Ta[c]; }
       if (o.touching) {
-        const int slot = atomicAdd(&s_slot[wib], 1);
-        if (slot < v.K) {
-          hpart_new[a * v.K + slot] = b;
-          for (int c = 0; c < 3; ++c) hval_new[3 * (a * v.K + slot) + c] = (double)o.ht[c];
+        const int sl = atomicAdd(slot, 1);
+        if (sl < v.K) {
+          st.hpart_new[a * v.K + sl] = b;
+          for (int c = 0; c < 3; ++c) st.hval_new[3 * (a * v.K + sl) + c] = (double)o.ht[c];
         } else {
           atomicOr(v.err, ERR_PAIRS);
         }
@@ -312,19 +408,13 @@ __global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ h
     const int dyc = lane / 9 - 1, dxc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
     const int zlo = v.ncz >= 3 ? -1 : 0, zhi = v.ncz >= 2 ? 1 : 0;
     if (dzc >= zlo && dzc <= zhi) {
-      double x = v.R[3 * i], y = v.R[3 * i + 1], z = v.R[3 * i + 2];
-      x -= v.nx * floor(x * v.inv_nx_d);
-      z -= v.nz * floor(z * v.inv_nz_d);
-      const int cy = min(max((int)floor(y * v.inv_csy), 0), v.ncy - 1);
-      const int cz = min(max((int)floor(z * v.inv_csz), 0), v.ncz - 1);
-      int yc = cy + dyc;
-      double xs = x;
-      if (yc < 0) { yc += v.ncy; xs = x + delta; }
-      else if (yc >= v.ncy) { yc -= v.ncy; xs = x - delta; }
-      xs -= v.nx * floor(xs * v.inv_nx_d);
-      const int cxs = min(max((int)floor(xs * v.inv_csx), 0), v.ncx - 1);
+      // i's cell at the step start: the lists stay valid over the sub-steps
+      const int* pc = v.pcx + 8 * i;
+      int yc = pc[1] + dyc, cxs = pc[0];
+      if (yc < 0) { yc += v.ncy; cxs = pc[3]; }
+      else if (yc >= v.ncy) { yc -= v.ncy; cxs = pc[4]; }
       const int xc = wrapi(cxs + dxc, v.ncx);
-      const int zc = wrapi(cz + dzc, v.ncz);
+      const int zc = wrapi(pc[2] + dzc, v.ncz);
       const int c = xc + v.ncx * (yc + v.ncy * zc);
       const int s0 = v.cell_start[c], e0 = v.cell_start[c + 1];
       for (int t = s0; t < e0; ++t) visit(v.cell_ids[t]);
@@ -337,51 +427,74 @@ __global__ void __launch_bounds__(128) k_pairs(View v, const int* __restrict__ h
   }
   __syncwarp();
   if (lane == 0) {
-    for (int c = 0; c < 3; ++c) { v.Fp[3 * i + c] = (double)F[c]; v.Tp[3 * i + c] = (double)Tq[c]; }
-    const int m = s_slot[wib];
-    hcnt_new[i] = m < v.K ? m : v.K;
+    integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8);
+    const int m = *slot;
+    st.hcnt_new[i] = m < v.K ? m : v.K;
     if (sample) {
       for (int c = 0; c < 9; ++c) { v.cvir_part[9 * i + c] = (double)cv[c]; v.rvir_part[9 * i + c] = (double)rv[c]; }
       v.ncont_part[i] = ncont;
     }
   }
+  __syncwarp();
 }
 
 template <typename TC>
 __device__ inline void write_plb(const View& v, int i) {
-  TC* pp = reinterpret_cast<TC*>(v.plb) + 12 * i;
-  for (int c = 0; c < 3; ++c) {
-    pp[c] = (TC)v.R[3 * i + c];
-    pp[3 + c] = (TC)v.U[3 * i + c];
-    pp[6 + c] = (TC)v.W[3 * i + c];
-  }
+  write_plb<TC>(v, i, v.R + 3 * i, v.U + 3 * i, v.W + 3 * i);
 }
 
-__global__ void k_integrate(View v, double dt, int last, int plb_double) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= v.n) return;
-  double* R = v.R + 3 * i;
-  double* U = v.U + 3 * i;
-  double* W = v.W + 3 * i;
-  const double im = v.inv_m[i], iI = v.inv_I[i];
-  for (int c = 0; c < 3; ++c) {
-    const double F = v.Fh[3 * i + c] + v.Fcov[3 * i + c] + v.Fp[3 * i + c];
-    const double T = v.Th[3 * i + c] + v.Tcov[3 * i + c] + v.Tp[3 * i + c];
-    U[c] += dt * F * im;
-    W[c] += dt * T * iI;
+// All particle sub-steps of one lattice step, for every box, in one
+// cooperative launch.  Per sub-step each warp computes one particle's pair
+// forces from the state buffer read in that sub-step and its lane 0
+// integrates the particle into the other buffer, so one grid-wide barrier per
+// sub-step suffices; boxes with fewer sub-steps idle in the later rounds.  The
+// final state ends in the canonical buffer (R, U, W).
+template <typename T>
+__global__ void __launch_bounds__(128) k_dem_step(Batch B) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ int s_slot[4];
+  const int wib = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * 4 + wib, nwarps = gridDim.x * 4;
+  const int ntot = B.part_off[B.nbox];
+  bool any_odd = false;
+  for (int b = 0; b < B.nbox; ++b) {
+    const View& v = B.views[b];
+    if (v.move && v.n > 0 && (v.nsub & 1)) any_odd = true;
   }
-  if (v.quasi2d) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
-  for (int c = 0; c < 3; ++c) R[c] += dt * U[c];
-  if (!last) return;
-  const Proto* pr = v.proto;
-  if (R[1] >= v.ny) { R[1] -= v.ny; R[0] -= pr->delta_n; U[0] -= pr->ule; }
-  else if (R[1] < 0.0) { R[1] += v.ny; R[0] += pr->delta_n; U[0] += pr->ule; }
-  R[0] -= v.nx * floor(R[0] / v.nx);
-  R[2] -= v.nz * floor(R[2] / v.nz);
-  const double sp = sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-  if (!(sp < 0.5)) atomicOr(v.err, ERR_UNSTABLE);
-  if (plb_double) write_plb<double>(v, i);
-  else write_plb<float>(v, i);
+  if (any_odd) {
+    // odd sub-step count: the first sub-step reads a copy in the second buffer
+    const int gthr = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    for (int g = gthr; g < ntot; g += nthr) {
+      const int bx = box_of(B.part_off, B.nbox, g);
+      const View& v = B.views[bx];
+      if (!v.move || !(v.nsub & 1)) continue;
+      const int i = g - B.part_off[bx];
+      for (int c = 0; c < 3; ++c) {
+        v.R2[3 * i + c] = v.R[3 * i + c]; v.U2[3 * i + c] = v.U[3 * i + c]; v.W2[3 * i + c] = v.W[3 * i + c];
+      }
+    }
+    grid.sync();
+  }
+  for (int sub = 0; sub < B.max_nsub; ++sub) {
+    for (int g = gwarp; g < ntot; g += nwarps) {
+      const int bx = box_of(B.part_off, B.nbox, g);
+      const View& v = B.views[bx];
+      const int nsub = v.nsub;
+      if (!v.move || sub >= nsub) continue;
+      const int i = g - B.part_off[bx];
+      const SpringTables st0{v.hcnt0, v.hpart0, v.hval0, v.hcnt1, v.hpart1, v.hval1};
+      const SpringTables st1{v.hcnt1, v.hpart1, v.hval1, v.hcnt0, v.hpart0, v.hval0};
+      const int parity0 = (int)((v.proto->t * (long long)nsub) & 1);
+      const SpringTables& st = ((parity0 ^ sub) & 1) ? st1 : st0;
+      // sub-step s reads A when (nsub - s) is even, so the last write lands in A
+      const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W};
+      const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
+      const State& S = ((nsub - sub) & 1) ? toA : toB;
+      pairs_of<T>(v, i, st, S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1, &s_slot[wib]);
+    }
+    if (sub + 1 < B.max_nsub) grid.sync();
+  }
 }
 
 __global__ void k_write_plb(View v, int plb_double) {
@@ -400,31 +513,36 @@ void launch_write_plb(const View& v, int plb_double, cudaStream_t s) {
   k_write_plb<<<(v.n + 127) / 128, 128, 0, s>>>(v, plb_double);
 }
 
-// One particle sub-step: (at sub-step 0) the cell list, then the pair
-// interactions and the integration.  The cell list stays valid over the
-// sub-steps of a lattice step: the cells are at least one lattice unit larger
-// than the interaction range and a particle moves less than 0.5 per step.
-void launch_dem_substep(const View& v, int parity, int sub, int plb_double, cudaStream_t s) {
-  if (v.n == 0) return;
-  const int nb = (v.n + 127) / 128;
-  if (!v.brute && sub == 0) {
-    cudaMemsetAsync(v.cell_cnt, 0, sizeof(int) * v.ncells, s);
-    k_cell_count<<<nb, 128, 0, s>>>(v);
-    k_cell_scan<<<1, 1024, 0, s>>>(v);
-    k_cell_fill<<<nb, 128, 0, s>>>(v);
-    k_cell_sort<<<(v.ncells + 127) / 128, 128, 0, s>>>(v);
+// Co-resident block count of the cooperative particle kernel for n particles.
+int dem_grid_blocks(int plb_double, int n) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (plb_double) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<double>, 128, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<float>, 128, 0);
+  if (per < 1) per = 1;
+  if (sms < 1) sms = 1;
+  const int want = (n + 3) / 4;
+  const int cap = sms * per;
+  return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
+// All particle sub-steps of one lattice step for every box of the batch: the
+// cell lists (valid for every sub-step: the cells are at least one lattice
+// unit wider than the interaction range and a particle moves less than 0.5
+// per step), then one cooperative launch for the pair forces and integrations.
+cudaError_t launch_dem_step(const Batch& B, int nparts, int ncells, int plb_double, int grid, cudaStream_t s) {
+  if (nparts == 0) return cudaSuccess;
+  const int nb = (nparts + 127) / 128;
+  if (ncells > 0) {
+    k_cell_count<<<nb, 128, 0, s>>>(B);
+    k_cell_scan<<<B.nbox, 1024, 0, s>>>(B);
+    k_cell_fill<<<nb, 128, 0, s>>>(B);
+    k_cell_sort<<<(ncells + 127) / 128, 128, 0, s>>>(B);
   }
-  const int* hc_old = parity ? v.hcnt1 : v.hcnt0;
-  const int* hp_old = parity ? v.hpart1 : v.hpart0;
-  const double* hv_old = parity ? v.hval1 : v.hval0;
-  int* hc_new = parity ? v.hcnt0 : v.hcnt1;
-  int* hp_new = parity ? v.hpart0 : v.hpart1;
-  double* hv_new = parity ? v.hval0 : v.hval1;
-  const double dt = 1.0 / v.nsub;
-  const int pb = (v.n + 3) / 4;
+  Batch bb = B;
+  void* args[] = {&bb};
   if (plb_double)
-    k_pairs<double><<<pb, 128, 0, s>>>(v, hc_old, hp_old, hv_old, hc_new, hp_new, hv_new, dt, sub == 0);
-  else
-    k_pairs<float><<<pb, 128, 0, s>>>(v, hc_old, hp_old, hv_old, hc_new, hp_new, hv_new, dt, sub == 0);
-  k_integrate<<<nb, 128, 0, s>>>(v, dt, sub == v.nsub - 1, plb_double);
+    return cudaLaunchCooperativeKernel((const void*)k_dem_step<double>, dim3(grid), dim3(128), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_dem_step<float>, dim3(grid), dim3(128), args, 0, s);
 }

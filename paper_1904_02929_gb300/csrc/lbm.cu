@@ -100,66 +100,46 @@ __device__ __forceinline__ typename Store<P>::C le_pull(const View& v, const typ
   return val;
 }
 
-// Plain pull of population p, or (mask bit p set) the node's own population q
-// = -p, which becomes the bounce-back value once the wall term is added.
+// Plain pull of population p from r - c_p (32-bit node offsets: interior
+// offsets are fixed sums of the precomputed x / z wrap deltas and -c_py nx).
+// Where r - c_p is solid the value read is that node's stored rest state; the
+// bounce-back value replaces it below.
 template <int P, int p, bool BND>
 __device__ __forceinline__ void pull_one(const View& v, const typename Store<P>::T* __restrict__ fin,
                                          const typename Store<P>::C* __restrict__ plb,
-                                         const Proto* __restrict__ pr, uint32_t m, int x, int y,
-                                         int z, int xm, int xp, int zm, int zp, long long idx,
+                                         const Proto* __restrict__ pr, int x, int y, int z, int idx,
+                                         int dxm, int dxp, int dzm, int dzp,
                                          typename Store<P>::C rho0, typename Store<P>::C (&n)[19]) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
-  constexpr int q = D3Q19::opp(p);
   const int sy = y - cpy;
   if (BND && cpy != 0 && (sy < 0 || sy >= v.ny)) {
     n[p] = le_pull<P, p>(v, fin, plb, pr, x, y, z, idx);
     return;
   }
-  const long long nc = v.ncell;
-  if ((m >> p) & 1u) {
-    n[p] = S::load(fin, (long long)q * nc + idx, (TC)D3Q19::w(q) * rho0, (TC)v.inv_scale);
-  } else {
-    const int sx = cpx == 1 ? xm : (cpx == -1 ? xp : x);
-    const int sz = cpz == 1 ? zm : (cpz == -1 ? zp : z);
-    const long long sidx = sx + (long long)v.nx * (sy + (long long)v.ny * sz);
-    n[p] = S::load(fin, (long long)p * nc + sidx, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
-  }
+  const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * v.nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
+  n[p] = S::load(fin + (size_t)p * (size_t)v.ncell, idx + off, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
 }
 
 template <int P, int p, bool BND>
 struct PullAll {
   __device__ __forceinline__ static void run(const View& v, const typename Store<P>::T* __restrict__ fin,
                                              const typename Store<P>::C* __restrict__ plb,
-                                             const Proto* __restrict__ pr, uint32_t m, int x, int y,
-                                             int z, int xm, int xp, int zm, int zp, long long idx,
+                                             const Proto* __restrict__ pr, int x, int y, int z, int idx,
+                                             int dxm, int dxp, int dzm, int dzp,
                                              typename Store<P>::C rho0, typename Store<P>::C (&n)[19]) {
-    pull_one<P, p, BND>(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
-    PullAll<P, p + 1, BND>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
+    pull_one<P, p, BND>(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
+    PullAll<P, p + 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
   }
 };
 template <int P, bool BND>
 struct PullAll<P, 19, BND> {
   __device__ __forceinline__ static void run(const View&, const typename Store<P>::T* __restrict__,
                                              const typename Store<P>::C* __restrict__,
-                                             const Proto* __restrict__, uint32_t, int, int, int, int,
-                                             int, int, int, long long, typename Store<P>::C,
-                                             typename Store<P>::C (&)[19]) {}
+                                             const Proto* __restrict__, int, int, int, int, int, int,
+                                             int, int, typename Store<P>::C, typename Store<P>::C (&)[19]) {}
 };
-
-template <typename TC>
-__device__ __forceinline__ void add_at(TC (&n)[19], int p, TC val) {
-  switch (p) {
-#define SUSP_ADD_CASE(k) case k: n[k] += val; break;
-    SUSP_ADD_CASE(1) SUSP_ADD_CASE(2) SUSP_ADD_CASE(3) SUSP_ADD_CASE(4) SUSP_ADD_CASE(5)
-    SUSP_ADD_CASE(6) SUSP_ADD_CASE(7) SUSP_ADD_CASE(8) SUSP_ADD_CASE(9) SUSP_ADD_CASE(10)
-    SUSP_ADD_CASE(11) SUSP_ADD_CASE(12) SUSP_ADD_CASE(13) SUSP_ADD_CASE(14) SUSP_ADD_CASE(15)
-    SUSP_ADD_CASE(16) SUSP_ADD_CASE(17) SUSP_ADD_CASE(18)
-#undef SUSP_ADD_CASE
-    default: break;
-  }
-}
 
 // Directions whose pull crosses a Lees-Edwards plane at y = 0 (c_py = +1) and
 // at y = ny-1 (c_py = -1); their mask bits are never set.
@@ -177,12 +157,13 @@ __host__ __device__ constexpr uint32_t crossing_bits(int sign) {
 template <int P, bool BND>
 __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::T* __restrict__ fin,
                                         typename Store<P>::T* __restrict__ fout, int x, int y, int z,
-                                        typename Store<P>::C (&acc)[6]) {
+                                        int dzm, int dzp, typename Store<P>::C (&acc)[6],
+                                        typename Store<P>::C* corr) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   const int nx = v.nx;
-  const long long idx = x + (long long)nx * (y + (long long)v.ny * z);
-  const long long nc = v.ncell;
+  const int idx = x + nx * (y + v.ny * z);
+  const size_t nc = (size_t)v.ncell;
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   const uint32_t m = v.mask[idx];
   if (m & 1u) {
@@ -190,31 +171,56 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
     // every stored sector complete (no read-for-ownership of partial sectors)
 #pragma unroll
     for (int q = 0; q < 19; ++q)
-      fout[(long long)q * nc + idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+      fout[q * nc + idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
     return;
   }
-  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  const int zm = z == 0 ? v.nz - 1 : z - 1, zp = z == v.nz - 1 ? 0 : z + 1;
+  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
   const Proto* pr = v.proto;
   const TC* plb = reinterpret_cast<const TC*>(v.plb);
   TC n[19];
   n[0] = S::load(fin, idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
-  PullAll<P, 1, BND>::run(v, fin, plb, pr, m, x, y, z, xm, xp, zm, zp, idx, rho0, n);
-  // moving-wall terms of the bounce-back links (few per node, one code copy)
+  PullAll<P, 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
+  // Moving bounce-back (Eq. 7) for the set mask bits: n_p = n*_q(r) + wall
+  // term, q = -p.  For links to one particle i, u_b . c_q with u_b at
+  // r + c_q / 2 equals ub0 . c_q with ub0 the rigid-body velocity at the node
+  // (the c_q / 2 part of the arm drops out of (Omega x arm) . c_q), so ub0 is
+  // formed once per node.  Values are staged in shared memory (dynamic index).
   uint32_t links = m & ~1u;
   if (BND) {
     if (y == 0) links &= ~crossing_bits(1);
     if (y == v.ny - 1) links &= ~crossing_bits(-1);
   }
+  const uint32_t corr_bits = links;
   if (links) {
     const TC delta = sel<TC>(pr->delta, pr->delta_f), ule = sel<TC>(pr->ule, pr->ule_f);
+    const TC w6 = (TC)6 * rho0;
+    const int p0 = __ffs(links) - 1;
+    const int i0 = v.owner[wrap1(x - D3Q19::cx(p0), nx) + nx * ((y - D3Q19::cy(p0)) + v.ny * wrap1(z - D3Q19::cz(p0), v.nz))];
+    const TC* pp = plb + 12 * i0;
+    TC rx = (TC)x - pp[0], ry = (TC)y - pp[1], rz = (TC)z - pp[2];
+    const int k0 = le_image_v(v, rx, ry, rz, delta);
+    const TC ubx = pp[3] + (pp[7] * rz - pp[8] * ry) + (TC)k0 * ule;
+    const TC uby = pp[4] + (pp[8] * rx - pp[6] * rz);
+    const TC ubz = pp[5] + (pp[6] * ry - pp[7] * rx);
     while (links) {
       const int p = __ffs(links) - 1;
       links &= links - 1;
-      const int sx = wrapi(x - D3Q19::cx(p), nx), sy = y - D3Q19::cy(p), sz = wrapi(z - D3Q19::cz(p), v.nz);
-      const int i = v.owner[sx + (long long)nx * (sy + (long long)v.ny * sz)];
-      add_at(n, p, wall_term<TC>(v, plb, i, x, y, z, D3Q19::opp(p), delta, ule, rho0));
+      const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+      const int q = D3Q19::opp(p);
+      const int i = p == p0 ? i0 : v.owner[wrap1(x - cpx, nx) + nx * ((y - cpy) + v.ny * wrap1(z - cpz, v.nz))];
+      const TC self = S::load(fin + (size_t)q * nc, idx, (TC)wq<TC>(q) * rho0, (TC)v.inv_scale);
+      TC wterm;
+      if (i == i0) {
+        // -6 C^q rho0 (u_b . c_q) = +6 C^p rho0 (ub0 . c_p)
+        wterm = w6 * wq<TC>(p) * (ubx * (TC)cpx + uby * (TC)cpy + ubz * (TC)cpz);
+      } else {
+        wterm = wall_term<TC>(v, plb, i, x, y, z, q, delta, ule, rho0);
+      }
+      corr[(p - 1) * 256 + threadIdx.x] = self + wterm;
     }
+#pragma unroll
+    for (int p = 1; p < 19; ++p)
+      if ((corr_bits >> p) & 1u) n[p] = corr[(p - 1) * 256 + threadIdx.x];
   }
   TC rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
@@ -228,14 +234,22 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   if (!(rho > (TC)0)) atomicOr(v.err, ERR_UNSTABLE);
   const TC inv = (TC)1 / rho;
   const TC omega = sel<TC>(v.omega_d, v.omega_f);
-  const TC gx = sel<TC>(v.g[0], v.g_f[0]), gy = sel<TC>(v.g[1], v.g_f[1]), gz = sel<TC>(v.g[2], v.g_f[2]);
+  const TC jj = jx * jx + jy * jy + jz * jz;
+  TC o[19];
 #pragma unroll
   for (int q = 0; q < 19; ++q) {
-    const TC fe = feq<TC>(q, rho, jx, jy, jz, inv);
-    const TC gc = gx * (TC)D3Q19::cx(q) + gy * (TC)D3Q19::cy(q) + gz * (TC)D3Q19::cz(q);
-    const TC o = n[q] - omega * (n[q] - fe) + (TC)3 * (TC)D3Q19::w(q) * gc;
-    fout[(long long)q * nc + idx] = S::enc(o, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+    const TC jc = jx * (TC)D3Q19::cx(q) + jy * (TC)D3Q19::cy(q) + jz * (TC)D3Q19::cz(q);
+    const TC fe = (TC)D3Q19::w(q) * (rho + (TC)3 * jc + (TC)4.5 * jc * jc * inv - (TC)1.5 * jj * inv);
+    o[q] = n[q] - omega * (n[q] - fe);
   }
+  if (v.has_g) {
+    const TC gx = sel<TC>(v.g[0], v.g_f[0]), gy = sel<TC>(v.g[1], v.g_f[1]), gz = sel<TC>(v.g[2], v.g_f[2]);
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      o[q] += (TC)3 * (TC)D3Q19::w(q) * (gx * (TC)D3Q19::cx(q) + gy * (TC)D3Q19::cy(q) + gz * (TC)D3Q19::cz(q));
+  }
+#pragma unroll
+  for (int q = 0; q < 19; ++q) fout[q * nc + idx] = S::enc(o[q], (TC)D3Q19::w(q) * rho0, (TC)v.scale);
   const TC vf = sel<TC>(v.vf_d, v.vf_f);
   const TC third = rho / (TC)3;
   acc[0] += vf * (pxx - jx * jx * inv - third);
@@ -246,35 +260,79 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   acc[5] += vf * (pyz - jy * jz * inv);
 }
 
-// Persistent grid over 32 (x) by 8 (y) tiles of the lattice, z slowest; each
-// block sums its nodes' viscous stress once, at the end.
+// Persistent grid over the 32 (x) by 8 (y) tiles of every box (z slowest
+// within a box); each block takes a contiguous range of tiles, sums its nodes'
+// viscous stress per box and adds it to the box's accumulator when its range
+// leaves the box.
 template <int P>
-__global__ void __launch_bounds__(256) k_collide_stream(View v, const typename Store<P>::T* __restrict__ fin,
-                                                        typename Store<P>::T* __restrict__ fout) {
+__global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   using TC = typename Store<P>::C;
+  using T = typename Store<P>::T;
   __shared__ TC red[32 * 6];
-  TC acc[6] = {0, 0, 0, 0, 0, 0};
-  const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
-  const int tiles_per_plane = ntx * nty;
-  const long long ntiles = (long long)tiles_per_plane * v.nz;
+  __shared__ TC corr[18 * 256];   // staged bounce-back values, [direction - 1][thread]
+  const int total = B.tile_off[B.nbox];
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
+  if (t0 >= t1) return;
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int z = (int)(t / tiles_per_plane);
-    const int r = (int)(t - (long long)z * tiles_per_plane);
-    const int ty = r / ntx, tx = r - ty * ntx;
-    const int x = tx * 32 + lx, y = ty * 8 + ly;
-    if (x < v.nx && y < v.ny) {
-      // a warp covers one x row, so this branch is warp-uniform
-      if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, acc);
-      else lb_node<P, false>(v, fin, fout, x, y, z, acc);
+  int b = box_of(B.tile_off, B.nbox, t0);
+  for (int t = t0; t < t1; ++b) {
+    const View& v = B.views[b];
+    const int base = B.tile_off[b], te = min(t1, B.tile_off[b + 1]);
+    const T* __restrict__ fin = static_cast<const T*>(fin_of(v));
+    T* __restrict__ fout = static_cast<T*>(fout_of(v));
+    const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
+    const int tiles_per_plane = ntx * nty;
+    const int nxny = v.nx * v.ny;
+    TC acc[6] = {0, 0, 0, 0, 0, 0};
+    for (; t < te; ++t) {
+      const int lt = t - base;
+      const int z = lt / tiles_per_plane;
+      const int r = lt - z * tiles_per_plane;
+      const int ty = r / ntx, tx = r - ty * ntx;
+      const int x = tx * 32 + lx, y = ty * 8 + ly;
+      const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
+      if (x < v.nx && y < v.ny) {
+        // a warp covers one x row, so this branch is warp-uniform
+        if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc, corr);
+        else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc, corr);
+      }
     }
-  }
-  block_sum<TC, 6>(acc, red);
-  if (threadIdx.x == 0) {
-    double* out = v.visc_part + 6LL * blockIdx.x;
+    block_sum<TC, 6>(acc, red);
+    if (threadIdx.x == 0)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) out[k] = (double)acc[k];
+      for (int k = 0; k < 6; ++k) atomicAdd(v.visc_acc + k, (double)acc[k]);
   }
+}
+
+// Moments (rho, j) of the two Lees-Edwards boundary planes of every box, read
+// by the crossing pulls of the same step: plane 0 is y = 0, plane 1 is y = ny-1.
+template <int P>
+__global__ void k_plane_moments_b(Batch B) {
+  using TC = typename Store<P>::C;
+  using T = typename Store<P>::T;
+  using S = Store<P>;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B.plane_off[B.nbox]) return;
+  const int b = box_of(B.plane_off, B.nbox, g);
+  const View& v = B.views[b];
+  const T* __restrict__ fin = static_cast<const T*>(fin_of(v));
+  const int per = v.nx * v.nz;
+  const int l = g - B.plane_off[b];
+  const int plane = l / per, r = l - plane * per;
+  const int x = r % v.nx, z = r / v.nx;
+  const int y = plane ? v.ny - 1 : 0;
+  const long long idx = x + (long long)v.nx * (y + (long long)v.ny * z);
+  TC rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    const TC f = S::load(fin, (long long)q * v.ncell + idx, (TC)D3Q19::w(q) * sel<TC>(v.rho0, v.rho0_f),
+                         (TC)v.inv_scale);
+    rho += f;
+    jx += f * (TC)D3Q19::cx(q); jy += f * (TC)D3Q19::cy(q); jz += f * (TC)D3Q19::cz(q);
+  }
+  TC* pm = reinterpret_cast<TC*>(v.plane_mom) + 4 * ((long long)plane * per + r);
+  pm[0] = rho; pm[1] = jx; pm[2] = jy; pm[3] = jz;
 }
 
 // Moments (rho, j) of the two Lees-Edwards boundary planes, read by the
@@ -325,31 +383,27 @@ int lb_grid_blocks(int prec, int nx, int ny, int nz) {
   }
   if (e != cudaSuccess || per < 1) per = 1;
   if (sms < 1) sms = 1;
-  const int tiles = lb_blocks(nx, ny, nz);
-  const int g = sms * per;
-  return g < tiles ? g : tiles;
+  (void)nx; (void)ny; (void)nz;
+  return sms * per;
 }
 
-void launch_plane_moments(int prec, const View& v, const void* fin, cudaStream_t s) {
-  const long long per = 2LL * v.nx * v.nz;
-  const int pb = (int)((per + 255) / 256);
+void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s) {
+  const int pb = (total + 255) / 256;
+  if (pb == 0) return;
   switch (prec) {
-    case 0: k_plane_moments<0><<<pb, 256, 0, s>>>(v, (const double*)fin); break;
-    case 1: k_plane_moments<1><<<pb, 256, 0, s>>>(v, (const float*)fin); break;
-    case 2: k_plane_moments<2><<<pb, 256, 0, s>>>(v, (const __half*)fin); break;
-    default: k_plane_moments<3><<<pb, 256, 0, s>>>(v, (const __nv_bfloat16*)fin); break;
+    case 0: k_plane_moments_b<0><<<pb, 256, 0, s>>>(B); break;
+    case 1: k_plane_moments_b<1><<<pb, 256, 0, s>>>(B); break;
+    case 2: k_plane_moments_b<2><<<pb, 256, 0, s>>>(B); break;
+    default: k_plane_moments_b<3><<<pb, 256, 0, s>>>(B); break;
   }
 }
 
-void launch_collide_stream(int prec, const View& v, const void* fin, void* fout, cudaStream_t s) {
-  const int nb = v.nblk_lb;
+void launch_collide_stream(int prec, const Batch& B, int grid, cudaStream_t s) {
   switch (prec) {
-    case 0: k_collide_stream<0><<<nb, 256, 0, s>>>(v, (const double*)fin, (double*)fout); break;
-    case 1: k_collide_stream<1><<<nb, 256, 0, s>>>(v, (const float*)fin, (float*)fout); break;
-    case 2: k_collide_stream<2><<<nb, 256, 0, s>>>(v, (const __half*)fin, (__half*)fout); break;
-    default:
-      k_collide_stream<3><<<nb, 256, 0, s>>>(v, (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout);
-      break;
+    case 0: k_collide_stream<0><<<grid, 256, 0, s>>>(B); break;
+    case 1: k_collide_stream<1><<<grid, 256, 0, s>>>(B); break;
+    case 2: k_collide_stream<2><<<grid, 256, 0, s>>>(B); break;
+    default: k_collide_stream<3><<<grid, 256, 0, s>>>(B); break;
   }
 }
 

@@ -18,9 +18,13 @@ struct D3Q19 {
   //   cx = 0 1 -1 0 0 0 0 1 -1 1 -1 1 -1 1 -1 0 0 0 0
   //   cy = 0 0 0 1 -1 0 0 1 -1 -1 1 0 0 0 0 1 -1 1 -1
   //   cz = 0 0 0 0 0 1 -1 0 0 0 0 1 -1 -1 1 1 -1 -1 1
-  __host__ __device__ static constexpr int cx(int q) { return (int)((0x1548889549ULL >> (2 * q)) & 3) - 1; }
-  __host__ __device__ static constexpr int cy(int q) { return (int)((0x895609495ULL >> (2 * q)) & 3) - 1; }
-  __host__ __device__ static constexpr int cz(int q) { return (int)((0x20a0954955ULL >> (2 * q)) & 3) - 1; }
+  // (directions 0-15 in the first 32-bit word, 16-18 in the second)
+  __host__ __device__ static constexpr int unpack(unsigned a, unsigned b, int q) {
+    return (int)(((q < 16 ? a >> (2 * q) : b >> (2 * (q - 16)))) & 3u) - 1;
+  }
+  __host__ __device__ static constexpr int cx(int q) { return unpack(0x48889549u, 0x15u, q); }
+  __host__ __device__ static constexpr int cy(int q) { return unpack(0x95609495u, 0x8u, q); }
+  __host__ __device__ static constexpr int cz(int q) { return unpack(0xa0954955u, 0x20u, q); }
   // opposite direction: pairs (1,2) (3,4) ... (17,18)
   __host__ __device__ static constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
   __host__ __device__ static constexpr double w(int q) {
@@ -88,20 +92,24 @@ struct View {
   int nx, ny, nz;
   long long ncell;
   double tau, rho0, g[3];
+  int has_g;                    // nonzero body force
   float inv_scale, scale;       // deviation storage scale (P = 2, 3)
   // per-node constants in both precisions (no FP64 arithmetic on the FP32 paths)
   double omega_d, vf_d;         // 1/tau and -(1 - 1/(2 tau))
   float omega_f, vf_f, rho0_f, g_f[3];
   double inv_nx_d, inv_ny_d, inv_nz_d;   // reciprocal box lengths
   float inv_nx_f, inv_ny_f, inv_nz_f;
+  void* fa;                     // population buffers; step t reads fa when t is even
+  void* fb;
+  double* visc_acc;             // [6] viscous-stress sum of the current step
   uint32_t* mask;               // bit 0 solid, bit p: pull source of p is solid (not LE-crossing)
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
-  double* visc_part;            // [nblk][6]
-  int nblk_lb;                  // blocks of the (persistent) collide-stream grid
   // particles
   int n;
   double *R, *U, *W, *rad, *amap, *mass, *inert, *inv_m, *inv_I;
+  double *R2, *U2, *W2;           // second state buffer of the particle sub-steps
+  int* pcx;                       // [n][8] cell of each particle at the step start (x, y, z, x of the rows across the planes)
   void* plb;                    // [n][12] compute-type copy: R, U, W (and pad)
   double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
   double *slet_part, *cvir_part, *rvir_part;   // [n][9]
@@ -130,12 +138,41 @@ struct View {
 
 enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
 
+// A set of boxes stepped together (one box for the single-box API).  Work of
+// every kernel is numbered across the boxes; the prefix tables map a global
+// work index (collide-stream tile, particle, plane node, cell) to its box.
+struct Batch {
+  const View* __restrict__ views;   // [nbox], device
+  const int* __restrict__ tile_off;   // [nbox + 1] collide-stream tiles (32 x 8 nodes)
+  const int* __restrict__ part_off;   // [nbox + 1] particles
+  const int* __restrict__ plane_off;  // [nbox + 1] Lees-Edwards plane nodes (2 nx nz)
+  const int* __restrict__ cell_off;   // [nbox + 1] cell-list cells
+  int nbox;
+  int max_nsub;
+};
+
+// Box owning global work index g (off is an ascending prefix table).
+__device__ __forceinline__ int box_of(const int* __restrict__ off, int nbox, int g) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Select the double or float copy of a constant for compute type T.
 template <typename T> __device__ __forceinline__ T sel(double d, float f);
 template <> __device__ __forceinline__ double sel<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float sel<float>(double, float f) { return f; }
 
+// Population buffer holding n*(t) for the box's current step counter.
+__device__ __forceinline__ void* fin_of(const View& v) { return (v.proto->t & 1) ? v.fb : v.fa; }
+__device__ __forceinline__ void* fout_of(const View& v) { return (v.proto->t & 1) ? v.fa : v.fb; }
+
 __host__ __device__ inline int wrapi(int v, int L) { int r = v % L; return r < 0 ? r + L : r; }
+// Periodic wrap of an index at most one period outside [0, L).
+__host__ __device__ __forceinline__ int wrap1(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
 // Lees-Edwards minimum image of d = p - R for a particle centre R: returns k,
 // the image R + k (delta, ny, 0) moving with U + k U_LE e_x.  Multiplies by the

@@ -7,9 +7,12 @@ monolayer phi) and lists the lattice sizes and physical parameters of each
 workload.  It contains none of the lattice-Boltzmann or particle arithmetic,
 so both the CUDA path and the CPU oracle can take their inputs from here.
 
-Placement: random positions, then repeated pairwise pushes of overlapping
-spheres until every gap is at least ``min_gap`` (a soft-sphere relaxation;
-random sequential addition alone jams near phi ~ 0.38 in 3D).
+Placement: random positions with the radii shrunk to a dilute packing, then
+the radii grown to full size in a few stages, each stage minimising the
+harmonic overlap energy sum max(0, a_i + a_j + gap - d_ij)^2 with L-BFGS, and a
+final pass of pairwise pushes until every gap is at least ``min_gap`` (a
+soft-sphere relaxation; random sequential addition alone jams near
+phi ~ 0.38 in 3D, and plain pushes converge slowly near phi ~ 0.58).
 """
 from __future__ import annotations
 
@@ -18,10 +21,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-try:  # neighbour search for the push relaxation
+try:  # neighbour search and minimiser of the relaxation
     from scipy.spatial import cKDTree
+    from scipy.optimize import minimize
 except Exception:  # pragma: no cover - scipy is present on both machines
     cKDTree = None
+    minimize = None
 
 
 def bidisperse_radii(n: int, a_min: float, ratio: float = 1.4) -> np.ndarray:
@@ -83,13 +88,55 @@ def _relax(x, r, L, quasi2d, min_gap, max_iter):
     return False
 
 
+def _minimise(x, r, L, quasi2d, gap, iters=2000):
+    """L-BFGS on the harmonic overlap energy (periodic box); returns new x."""
+    n = r.size
+    reach = 2.0 * r.max() + gap
+    dim = 2 if quasi2d else 3
+    z0 = x[:, 2].copy()
+
+    def unpack(v):
+        y = x.copy()
+        y[:, :dim] = v.reshape(n, dim)
+        if quasi2d:
+            y[:, 2] = z0
+        return y
+
+    def energy(v):
+        y = unpack(v) % L
+        tree = cKDTree(y, boxsize=L * (1 + 1e-12))
+        pairs = tree.query_pairs(reach, output_type="ndarray")
+        g = np.zeros_like(y)
+        if len(pairs) == 0:
+            return 0.0, g[:, :dim].ravel()
+        i, j = pairs[:, 0], pairs[:, 1]
+        d = _wrap(y[j] - y[i], L)
+        dist = np.sqrt((d * d).sum(1))
+        ov = r[i] + r[j] + gap - dist
+        m = ov > 0
+        if not m.any():
+            return 0.0, g[:, :dim].ravel()
+        i, j, d, dist, ov = i[m], j[m], d[m], dist[m], ov[m]
+        nv = d / np.maximum(dist, 1e-12)[:, None]
+        # dE/dx_j = -2 ov n, dE/dx_i = +2 ov n
+        f = 2.0 * ov[:, None] * nv
+        np.add.at(g, i, f)
+        np.add.at(g, j, -f)
+        return float((ov * ov).sum()), g[:, :dim].ravel()
+
+    res = minimize(energy, x[:, :dim].ravel(), jac=True, method="L-BFGS-B",
+                   options=dict(maxiter=iters, ftol=1e-16, gtol=1e-12))
+    return unpack(res.x) % L
+
+
 def place_spheres(box, radii, seed: int, quasi2d: bool = False, min_gap: float = 0.05,
                   max_iter: int = 400) -> np.ndarray:
     """Non-overlapping centres (gap >= min_gap) in a periodic box.
 
-    Radii are grown from a dilute packing to their final size in small steps,
-    relaxing overlaps after each step, so dense packings (phi_3 ~ 0.58) form
-    without jamming the pushes."""
+    Radii are grown from a dilute packing to their final size in a few
+    stages, minimising the overlap energy after each, then the remaining
+    small overlaps are pushed apart, so dense packings (phi_3 ~ 0.58) form
+    in seconds."""
     rng = np.random.default_rng(seed)
     L = np.asarray(box, dtype=np.float64)
     r = np.asarray(radii, dtype=np.float64)
@@ -107,16 +154,13 @@ def place_spheres(box, radii, seed: int, quasi2d: bool = False, min_gap: float =
     scale = min(1.0, (0.25 / max(phi, 1e-9)) ** (1.0 / dim))
     if not _relax(x, r * scale, L, quasi2d, min_gap * scale, max_iter):
         raise RuntimeError("sphere placement did not converge")
-    grow = 1.01
-    while scale < 1.0:
-        trial = min(1.0, scale * grow)
-        xt = x.copy()
-        if _relax(xt, r * trial, L, quasi2d, min_gap * trial, max_iter):
-            x, scale = xt, trial
-        else:
-            grow = 1.0 + 0.5 * (grow - 1.0)
-            if grow - 1.0 < 1e-5:
-                raise RuntimeError("sphere placement did not converge")
+    # the minimiser aims at a wider gap so that its residual overlaps are
+    # far below min_gap; the pushes then close what is left
+    target = 1.5 * min_gap + 0.02
+    for s in np.linspace(scale, 1.0, 5)[1:]:
+        x = _minimise(x, r * s, L, quasi2d, target * s)
+    if not _relax(x, r, L, quasi2d, min_gap, 20 * max_iter):
+        raise RuntimeError("sphere placement did not converge")
     x %= L
     if quasi2d:
         x[:, 2] = L[2] / 2.0

@@ -98,8 +98,31 @@ def library() -> C.CDLL:
         L.susp_fluid_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                               C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p]
+        L.susp_set_graphs.restype = C.c_int
+        L.susp_set_graphs.argtypes = [C.c_void_p, C.c_int]
         L.susp_destroy.restype = None
         L.susp_destroy.argtypes = [C.c_void_p]
+        L.susp_batch_workspace_bytes.restype = C.c_size_t
+        L.susp_batch_workspace_bytes.argtypes = [C.c_int]
+        L.susp_batch_create.restype = C.c_int
+        L.susp_batch_create.argtypes = [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+        L.susp_batch_attach.restype = C.c_int
+        L.susp_batch_attach.argtypes = [C.c_void_p, C.c_void_p]
+        L.susp_batch_detach.restype = C.c_int
+        L.susp_batch_detach.argtypes = [C.c_void_p, C.c_void_p]
+        L.susp_batch_size.restype = C.c_int
+        L.susp_batch_size.argtypes = [C.c_void_p]
+        L.susp_batch_step.restype = C.c_int
+        L.susp_batch_step.argtypes = [C.c_void_p, C.c_int]
+        L.susp_batch_profile.restype = C.c_int
+        L.susp_batch_profile.argtypes = [C.c_void_p, C.c_int]
+        L.susp_batch_profile_read.restype = C.c_int
+        L.susp_batch_profile_read.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+        L.susp_batch_errors.restype = C.c_int
+        L.susp_batch_errors.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.c_int]
+        L.susp_batch_destroy.restype = None
+        L.susp_batch_destroy.argtypes = [C.c_void_p]
         L.susp_last_error.restype = C.c_char_p
         L.susp_last_error.argtypes = []
         _lib = L
@@ -211,8 +234,60 @@ def susp_fluid_step_noalloc(nx, ny, nz, tau, delta, u_le, f_in_ptr, f_out_ptr, v
            "susp_fluid_step_noalloc")
 
 
+def susp_set_graphs(h, enable: bool) -> None:
+    _check(library().susp_set_graphs(h, int(bool(enable))), "susp_set_graphs")
+
+
 def susp_destroy(h) -> None:
     library().susp_destroy(h)
+
+
+def susp_batch_workspace_bytes(max_boxes: int) -> int:
+    return int(library().susp_batch_workspace_bytes(int(max_boxes)))
+
+
+def susp_batch_create(max_boxes: int, dev_workspace: int, nbytes: int, stream: int) -> C.c_void_p:
+    b = C.c_void_p()
+    _check(library().susp_batch_create(int(max_boxes), C.c_void_p(dev_workspace), nbytes,
+                                       C.c_void_p(stream), C.byref(b)), "susp_batch_create")
+    return b
+
+
+def susp_batch_attach(b, h) -> None:
+    _check(library().susp_batch_attach(b, h), "susp_batch_attach")
+
+
+def susp_batch_detach(b, h) -> None:
+    _check(library().susp_batch_detach(b, h), "susp_batch_detach")
+
+
+def susp_batch_size(b) -> int:
+    return int(library().susp_batch_size(b))
+
+
+def susp_batch_step(b, nsteps: int) -> None:
+    _check(library().susp_batch_step(b, int(nsteps)), "susp_batch_step")
+
+
+def susp_batch_profile(b, enable: bool) -> None:
+    _check(library().susp_batch_profile(b, int(bool(enable))), "susp_batch_profile")
+
+
+def susp_batch_profile_read(b):
+    ms = C.c_double(0.0)
+    n = C.c_int(0)
+    _check(library().susp_batch_profile_read(b, C.byref(ms), C.byref(n)), "susp_batch_profile_read")
+    return float(ms.value), int(n.value)
+
+
+def susp_batch_errors(b, n: int):
+    out = (C.c_int * max(n, 1))()
+    _check(library().susp_batch_errors(b, out, int(max(n, 1))), "susp_batch_errors")
+    return [int(out[k]) for k in range(n)]
+
+
+def susp_batch_destroy(b) -> None:
+    library().susp_batch_destroy(b)
 
 
 def susp_last_error() -> str:
@@ -257,7 +332,10 @@ def make_shear(kind=0, rate=0.0, gamma0=0.0, omega=0.0, theta=0.0) -> susp_shear
 
 
 class Suspension:
-    """One box on the current CUDA device; workspace held as a torch tensor."""
+    """One box on the current CUDA device; workspace held as a torch tensor.
+
+    All work goes to ``self.stream`` (a new torch stream unless one is given);
+    the calls that return host data synchronise it."""
 
     def __init__(self, nx, ny, nz, radius=(), pos=(), stream=None, **kw):
         import torch
@@ -272,7 +350,8 @@ class Suspension:
         self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.ws.data_ptr()
         self.ptr = (base + 255) & ~255
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        # a stream of its own: the legacy default stream cannot be graph-captured
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         self.h = susp_create(self.p, self.ptr, self.nbytes, self.stream.cuda_stream)
         del keep
 
@@ -306,10 +385,70 @@ class Suspension:
     def info(self):
         return susp_get_info(self.h)
 
+    def set_graphs(self, enable: bool):
+        susp_set_graphs(self.h, enable)
+
     def close(self):
         if getattr(self, "h", None):
             susp_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Boxes stepped in lockstep by one launch sequence (include/susp.h,
+    "batches").  Holds the descriptor workspace and a stream of its own; keeps
+    its members alive while they are attached."""
+
+    def __init__(self, max_boxes, stream=None):
+        import torch
+        self.max_boxes = int(max_boxes)
+        self.nbytes = susp_batch_workspace_bytes(self.max_boxes)
+        if self.nbytes == 0:
+            raise SuspError(SUSP_EINVAL, "susp_batch_workspace_bytes")
+        self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        self.ptr = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.b = susp_batch_create(self.max_boxes, self.ptr, self.nbytes, self.stream.cuda_stream)
+        self.members = []
+
+    def attach(self, box: Suspension, shear=None):
+        """Attach a box; ``shear`` (if given) is set as its protocol first."""
+        if shear is not None:
+            box.step(0, shear)
+        susp_batch_attach(self.b, box.h)
+        self.members.append(box)
+
+    def detach(self, box: Suspension):
+        susp_batch_detach(self.b, box.h)
+        self.members.remove(box)
+
+    def __len__(self):
+        return susp_batch_size(self.b)
+
+    def step(self, nsteps=1):
+        susp_batch_step(self.b, nsteps)
+
+    def errors(self):
+        """Device status of each member, in ``self.members`` order."""
+        return susp_batch_errors(self.b, len(self.members))
+
+    def profile(self, enable: bool):
+        susp_batch_profile(self.b, enable)
+
+    def profile_read(self):
+        return susp_batch_profile_read(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            susp_batch_destroy(self.b)
+            self.b = None
+            self.members = []
 
     def __del__(self):
         try:

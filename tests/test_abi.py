@@ -81,3 +81,26 @@ def test_step_rejects_bad_arguments_on_host():
     lib = S.library()
     sh = S.make_shear(kind=3)
     assert lib.susp_step(None, 1, C.byref(sh)) == S.SUSP_EINVAL
+
+
+def test_batch_workspace_bytes_on_host():
+    assert S.susp_batch_workspace_bytes(0) == 0
+    one, many = S.susp_batch_workspace_bytes(1), S.susp_batch_workspace_bytes(64)
+    assert 0 < one < many and many % 256 == 0
+
+
+def test_serving_requests_and_footprint_on_host():
+    from paper_1904_02929_gb300 import inputs as I
+    from paper_1904_02929_gb300 import serve as V
+    w = I.config_small()
+    pool = [I.Workload("s", w.nx, w.ny, w.nz, w.radius, w.pos, dict(w.params))]
+    reqs = V.poisson_requests(pool, rate=20.0, duration=50.0, steps=1000, seed=3)
+    t = np.array([r.arrival for r in reqs])
+    assert (np.diff(t) > 0).all() and t.max() < 50.0
+    assert abs(len(reqs) / 50.0 - 20.0) < 3.0            # ~1000 arrivals, sd ~ 32
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 0.05) < 0.005 and abs(gaps.std() / gaps.mean() - 1.0) < 0.1
+    kinds = {r.shear["kind"] for r in reqs}
+    assert kinds == {0, 1}
+    p, keep = S.make_params(w.nx, w.ny, w.nz, w.radius, w.pos, precision="bf16", **w.params)
+    assert V.footprint(reqs[0], "bf16") == S.susp_workspace_bytes(p)
