@@ -45,14 +45,13 @@ size_t csize(int prec) { return prec == 0 ? 8 : 4; }
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t fa, fb, mask, owner, pm, vacc, views, tabs;
+  size_t fa, fb, owner, pm, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
-  size_t slet, cvir, rvir, ncont, links, loff, lcap, lcnt;
-  size_t cstart, ccnt, cids, pcell;
+  size_t slet, cvir, rvir, ncont;
+  size_t cstart, ccnt, cids, pcell, pj, ph, pcnt;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
   size_t sums, hist, counters, proto, err;
   size_t total;
-  long long nlinks;
   int ncx, ncy, ncz, brute, ncells;
   double csx, csy, csz, hrange;
 };
@@ -100,7 +99,6 @@ void make_layout(const susp_params* p, Layout& L) {
   auto take = [&](size_t bytes) { size_t r = o; o += al(bytes); return r; };
   L.fa = take(19 * nc * esize(prec));
   L.fb = take(19 * nc * esize(prec));
-  L.mask = take(4 * nc);
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
   L.vacc = take(6 * 8);
@@ -114,14 +112,6 @@ void make_layout(const susp_params* p, Layout& L) {
   L.Fh = take(24 * nn); L.Th = take(24 * nn); L.Fcov = take(24 * nn); L.Tcov = take(24 * nn);
   L.Fp = take(24 * nn); L.Tp = take(24 * nn);
   L.slet = take(72 * nn); L.cvir = take(72 * nn); L.rvir = take(72 * nn); L.ncont = take(4 * nn);
-  long long nl = 0;
-  for (int i = 0; i < n; ++i) {
-    double am = p->a_map_ratio * p->radius[i] + 1.0;
-    nl += (long long)ceil(6.0 * 4.0 * KPI * am * am) + 64;
-  }
-  L.nlinks = nl;
-  L.links = take(4 * (nl > 0 ? nl : 1));
-  L.loff = take(4 * nn); L.lcap = take(4 * nn); L.lcnt = take(4 * nn);
   // cell list geometry
   double amax = 0.0;
   for (int i = 0; i < n; ++i) amax = std::max(amax, p->radius[i]);
@@ -133,6 +123,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.ncx = ncx; L.ncy = ncy; L.ncz = ncz;
   L.ncells = ncx * ncy * ncz;
   L.csx = (double)p->nx / ncx; L.csy = (double)p->ny / ncy; L.csz = (double)p->nz / ncz;
+  L.pj = take(4 * (size_t)nn * PAIR_SLOTS); L.ph = take(24 * (size_t)nn * PAIR_SLOTS); L.pcnt = take(4 * nn);
   L.cstart = take(4 * (L.ncells + 1)); L.ccnt = take(4 * L.ncells);
   L.cids = take(4 * nn); L.pcell = take(4 * nn);
   L.hc0 = take(4 * nn); L.hp0 = take(4 * (size_t)nn * HSLOTS); L.hv0 = take(24 * (size_t)nn * HSLOTS);
@@ -183,30 +174,32 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
 }
 
 // End of step t, one block per box: sum the per-particle stress partials
-// (one warp per quantity, fixed order) and the step's viscous stress, add them
-// to the compensated time sums, then advance the protocol to t+1.
-__global__ void __launch_bounds__(256) k_finalize(Batch B) {
+// (each thread accumulates a strided set of particles, then one fixed-order
+// block reduction) and the step's viscous stress, add them to the compensated
+// time sums, then advance the protocol to t+1.
+__global__ void __launch_bounds__(512) k_finalize(Batch B) {
   const View& v = B.views[blockIdx.x];
+  __shared__ double red[16 * 28];
   __shared__ double tot[37];
   // quantity k: 0-5 viscous, 6-14 stresslet, 15-23 contact virial,
   // 24 contact count, 25-33 repulsive virial (34-36 unused)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = warp; k < 37; k += nw) {
-    double t = 0.0;
-    if (k < 6) {
-      if (lane == 0) t = v.visc_acc[k];
-    } else if (k < 15) {
-      for (int i = lane; i < v.n; i += 32) t += v.slet_part[9 * i + (k - 6)];
-    } else if (k < 24) {
-      for (int i = lane; i < v.n; i += 32) t += v.cvir_part[9 * i + (k - 15)];
-    } else if (k == 24) {
-      for (int i = lane; i < v.n; i += 32) t += (double)v.ncont_part[i];
-    } else if (k < 34) {
-      for (int i = lane; i < v.n; i += 32) t += v.rvir_part[9 * i + (k - 25)];
-    }
+  double a[28];   // 0-8 stresslet, 9-17 contact virial, 18-26 repulsive virial, 27 count
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) tot[k] = t;
+  for (int k = 0; k < 28; ++k) a[k] = 0.0;
+  for (int i = threadIdx.x; i < v.n; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      a[k] += v.slet_part[9 * i + k];
+      a[9 + k] += v.cvir_part[9 * i + k];
+      a[18 + k] += v.rvir_part[9 * i + k];
+    }
+    a[27] += (double)v.ncont_part[i];
+  }
+  block_sum<double, 28>(a, red);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 6; ++k) tot[k] = v.visc_acc[k];
+    for (int k = 0; k < 9; ++k) { tot[6 + k] = a[k]; tot[15 + k] = a[9 + k]; tot[25 + k] = a[18 + k]; }
+    tot[24] = a[27];
   }
   __syncthreads();
   if (threadIdx.x < 6) v.visc_acc[threadIdx.x] = 0.0;
@@ -337,7 +330,7 @@ static cudaError_t eng_enqueue(Engine& e, cudaEvent_t ev0, cudaEvent_t ev1) {
   launch_collide_stream(e.prec, e.B, e.lb_grid, s);
   if (ev1) cudaEventRecord(ev1, s);
   if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
-  k_finalize<<<e.nbox, 256, 0, s>>>(e.B);
+  k_finalize<<<e.nbox, 512, 0, s>>>(e.B);
   launch_node_update(e.prec, e.B, e.nparts, s);
   launch_links(e.prec, e.B, e.nparts, s);
   return err != cudaSuccess ? err : cudaGetLastError();
@@ -481,7 +474,7 @@ static cudaStream_t stream_of(const susp* h) { return h->batch ? h->batch->eng.s
 static susp_status err_status(int err) {
   if (err & ERR_OVERLAP) return fail(SUSP_EOVERLAP, "two mapped spheres claimed one node");
   if (err & ERR_UNSTABLE) return fail(SUSP_EUNSTABLE, "non-positive density or particle speed >= 0.5");
-  if (err & ERR_LINKS) return fail(SUSP_ENOMEM, "boundary-link table full");
+  if (err & ERR_LINKS) return fail(SUSP_ENOMEM, "particle surface larger than the link kernel stages");
   if (err & ERR_PAIRS) return fail(SUSP_ENOMEM, "tangential-spring table full");
   return SUSP_OK;
 }
@@ -556,7 +549,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.inv_nx_f = (float)v.inv_nx_d; v.inv_ny_f = (float)v.inv_ny_d; v.inv_nz_f = (float)v.inv_nz_d;
   v.fa = w + L.fa; v.fb = w + L.fb;
   v.visc_acc = (double*)(w + L.vacc);
-  v.mask = (uint32_t*)(w + L.mask); v.owner = (int*)(w + L.owner);
+  v.owner = (int*)(w + L.owner);
   v.plane_mom = w + L.pm;
   v.n = n;
   v.R = (double*)(w + L.R); v.U = (double*)(w + L.U); v.W = (double*)(w + L.W);
@@ -571,13 +564,12 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.Fp = (double*)(w + L.Fp); v.Tp = (double*)(w + L.Tp);
   v.slet_part = (double*)(w + L.slet); v.cvir_part = (double*)(w + L.cvir);
   v.rvir_part = (double*)(w + L.rvir); v.ncont_part = (int*)(w + L.ncont);
-  v.links = (uint32_t*)(w + L.links); v.link_off = (int*)(w + L.loff);
-  v.link_cap = (int*)(w + L.lcap); v.link_cnt = (int*)(w + L.lcnt);
   v.ncx = L.ncx; v.ncy = L.ncy; v.ncz = L.ncz; v.brute = L.brute; v.ncells = L.ncells;
   v.csx = L.csx; v.csy = L.csy; v.csz = L.csz;
   v.inv_csx = 1.0 / L.csx; v.inv_csy = 1.0 / L.csy; v.inv_csz = 1.0 / L.csz;
   v.cell_start = (int*)(w + L.cstart); v.cell_cnt = (int*)(w + L.ccnt);
   v.cell_ids = (int*)(w + L.cids); v.pcell = (int*)(w + L.pcell);
+  v.pj = (int*)(w + L.pj); v.ph = (double*)(w + L.ph); v.pcnt = (int*)(w + L.pcnt);
   v.K = HSLOTS;
   v.hcnt0 = (int*)(w + L.hc0); v.hpart0 = (int*)(w + L.hp0); v.hval0 = (double*)(w + L.hv0);
   v.hcnt1 = (int*)(w + L.hc1); v.hpart1 = (int*)(w + L.hp1); v.hval1 = (double*)(w + L.hv1);
@@ -623,7 +615,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   cudaStream_t s = e.stream;
   susp_status st = SUSP_OK;
   // zero everything past the populations, then fill
-  st = cuda_check(cudaMemsetAsync(w + L.mask, 0, L.total - L.mask, s), "memset workspace");
+  st = cuda_check(cudaMemsetAsync(w + L.owner, 0, L.total - L.owner, s), "memset workspace");
   if (st) { delete h; return st; }
   cudaMemsetAsync(v.owner, 0xff, 4 * v.ncell, s);
   cudaMemcpyAsync(w + L.views, &v, sizeof(View), cudaMemcpyHostToDevice, s);
@@ -638,14 +630,8 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
       x -= L * floor(x / L);
       if (!(x >= 0.0 && x < L)) x = 0.0;
     }
-  std::vector<int> off(n), cap(n);
   if (n > 0) {
-    long long acc = 0;
     for (int i = 0; i < n; ++i) {
-      double am = amap[i] + 1.0;
-      cap[i] = (int)ceil(6.0 * 4.0 * KPI * am * am) + 64;
-      off[i] = (int)acc;
-      acc += cap[i];
       im[i] = 1.0 / mass[i];
       iI[i] = 1.0 / inert[i];
     }
@@ -658,8 +644,6 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
     cudaMemcpyAsync(v.inert, inert.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inv_m, im.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inv_I, iI.data(), 8 * n, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(v.link_off, off.data(), 4 * n, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(v.link_cap, cap.data(), 4 * n, cudaMemcpyHostToDevice, s);
   }
   Proto pr;
   memset(&pr, 0, sizeof pr);

@@ -11,12 +11,17 @@
 //   k_links:   for every solid node s of the particle and direction p, the
 //              fluid node r that pulls population p from s (r = s + c_p, or
 //              across a Lees-Edwards plane the node whose nearest source is
-//              s) forms a boundary link; the link sets bit p of r's mask (for
-//              non-crossing links) and contributes the momentum exchange
-//              f = [2 n*_q(r) - 6 C^q rho0 (u_b . c_q)] c_q,  q = -p (Eq. 6),
-//              to F^h (Eq. 9), (r_b - R) x f to T^h (Eq. 10) and
-//              (r_b - R)_a f_b to the particle stresslet (sigma^h).  A node
-//              of another particle in place of r counts as fluid at rest
+//              s) forms a boundary link.  It contributes the momentum
+//              exchange f = [2 n*_q(r) - 6 C^q rho0 (u_b . c_q)] c_q, q = -p
+//              (Eq. 6), to F^h (Eq. 9), (r_b - R) x f to T^h (Eq. 10) and
+//              (r_b - R)_a f_b to the particle stresslet (sigma^h); and for a
+//              link that does not cross a Lees-Edwards plane it stores the
+//              bounce-back value of Eq. 7, n*_q(r) - 6 C^q rho0 (u_b . c_q),
+//              in the population slot p of the solid node s.  That slot is
+//              exactly what the next collide-stream pulls for (r, p) (r - c_p
+//              = s), and no other receiver pulls it, so the lattice kernel
+//              streams plainly over solid sources.  A node of another
+//              particle in place of r counts as fluid at rest
 //              (f = 2 C^q rho0 c_q): when two mapped spheres come closer than
 //              one lattice spacing their solid nodes touch, and without this
 //              the rest pressure on each particle would not balance.
@@ -105,8 +110,7 @@ __global__ void k_claim(Batch B) {
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
     if (dx * dx + dy * dy + dz * dz < am * am) {
       const int old = atomicCAS(v.owner + c, -1, i);
-      if (old == -1) atomicOr(v.mask + c, 1u);
-      else if (old != i) atomicOr(v.err, ERR_OVERLAP);
+      if (old != -1 && old != i) atomicOr(v.err, ERR_OVERLAP);
     }
   });
 }
@@ -121,12 +125,6 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   const View& v = B.views[bx];
   const int i = g - B.part_off[bx];
   typename Store<P>::T* __restrict__ f = static_cast<typename Store<P>::T*>(fin_of(v));
-  // clear the mask bits of last step's links of this particle
-  const int off = v.link_off[i], nl = v.link_cnt[i];
-  for (int k = threadIdx.x; k < nl; k += blockDim.x) {
-    const uint32_t L = v.links[off + k];
-    atomicAnd(v.mask + (L >> 5), ~(1u << (L & 31u)));
-  }
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
@@ -150,7 +148,6 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
       f[(long long)q * v.ncell + c] =
           S::enc(feq<TC>(q, rho0, jx, jy, jz, inv), (TC)D3Q19::w(q) * rho0, (TC)v.scale);
     v.owner[c] = -1;
-    atomicAnd(v.mask + c, ~1u);
     acc[0] -= jx; acc[1] -= jy; acc[2] -= jz;
     acc[3] -= dy * jz - dz * jy; acc[4] -= dz * jx - dx * jz; acc[5] -= dx * jy - dy * jx;
   });
@@ -190,7 +187,6 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
     if (own == i) return;
     const int old = own == -1 ? atomicCAS(v.owner + c, -1, i) : own;
     if (old != -1) { atomicOr(v.err, ERR_OVERLAP); return; }
-    atomicOr(v.mask + c, 1u);
     TC jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
@@ -245,14 +241,14 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 15];
-  __shared__ int s_count, s_nodes;
+  __shared__ int s_nodes;
   __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
   const int i = g - B.part_off[bx];
-  const typename Store<P>::T* __restrict__ f = static_cast<const typename Store<P>::T*>(fin_of(v));
-  if (threadIdx.x == 0) { s_count = 0; s_nodes = 0; }
+  typename Store<P>::T* __restrict__ f = static_cast<typename Store<P>::T*>(fin_of(v));
+  if (threadIdx.x == 0) s_nodes = 0;
   __syncthreads();
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
@@ -260,7 +256,6 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   const Proto* pr = v.proto;
   const TC delta = pdelta<TC>(pr), ule = pule<TC>(pr);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  const int off = v.link_off[i], cap = v.link_cap[i];
   ImgBox b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   // A link's receiver lies within sqrt(2) of its solid node, or -- across a
@@ -283,38 +278,14 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) acc[k] = 0;
   const int items = nn * 18;
-  const int lane = threadIdx.x & 31;
-  // round the loop up to whole warps so the ballot below sees full warps
-  const int items_r = (items + 31) & ~31;
-  for (int t = threadIdx.x; t < items_r; t += blockDim.x) {
-    const bool valid = t < items;
-    int x = 0, y = 0, z = 0, p = 1;
-    if (valid) {
-      const uint32_t w = s_node[t / 18];
-      p = 1 + t % 18;
-      x = (int)(w & 2047u); y = (int)((w >> 11) & 2047u); z = (int)(w >> 22);
-    }
+  for (int t = threadIdx.x; t < items; t += blockDim.x) {
+    const uint32_t w = s_node[t / 18];
+    const int p = 1 + t % 18;
+    const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
     int rx, ry, rz;
     bool crossing;
     const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);
-    const int ow = valid ? v.owner[r] : i;
-    // slot in the particle's link segment for non-crossing fluid links
-    const bool want = valid && ow < 0 && !crossing;
-    const unsigned bal = __ballot_sync(0xffffffffu, want);
-    if (bal) {
-      const int leader = __ffs(bal) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(&s_count, __popc(bal));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (want) {
-        const int slot = base + __popc(bal & ((1u << lane) - 1u));
-        // a link that does not fit is not set (its bit could never be cleared)
-        if (slot < cap) {
-          atomicOr(v.mask + r, 1u << p);
-          v.links[off + slot] = ((uint32_t)r << 5) | (uint32_t)p;
-        }
-      }
-    }
+    const int ow = v.owner[r];
     if (ow == i) continue;
     const int q = D3Q19::opp(p);
     const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
@@ -325,11 +296,17 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
     const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
     const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
     const TC wqq = wq<TC>(q);
-    // fluid receiver: momentum exchange; another particle's node: fluid at rest
+    // fluid receiver: momentum exchange and the bounce-back value for the
+    // next pull; another particle's node: fluid at rest
     TC mag;
     if (ow < 0) {
       const TC nq = S::load(f, (long long)q * v.ncell + r, wqq * rho0, (TC)v.inv_scale);
-      mag = (TC)2 * nq - (TC)6 * wqq * rho0 * cu;
+      const TC wall = (TC)6 * wqq * rho0 * cu;
+      mag = (TC)2 * nq - wall;
+      if (!crossing) {
+        const long long sidx = x + (long long)v.nx * (y + (long long)v.ny * z);
+        f[(long long)p * v.ncell + sidx] = S::enc(nq - wall, (TC)D3Q19::w(p) * rho0, (TC)v.scale);
+      }
     } else {
       mag = (TC)2 * wqq * rho0;
     }
@@ -347,8 +324,6 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       v.Th[3 * i + a] = (double)acc[3 + a];
     }
     for (int a = 0; a < 9; ++a) v.slet_part[9 * i + a] = (double)acc[6 + a];
-    if (s_count > cap) atomicOr(v.err, ERR_LINKS);
-    v.link_cnt[i] = s_count < cap ? s_count : cap;
   }
 }
 

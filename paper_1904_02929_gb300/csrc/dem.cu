@@ -1,9 +1,10 @@
 // dem.cu — particle sub-steps: cell list, pair interactions, integration.
 //
-// Pair interactions (one thread per particle, gathering over the 27 cells
-// around it; every pair is evaluated by both partners in the canonical
-// orientation a = min(i, j), b = max(i, j) so the two results are bitwise
-// equal and opposite, with no atomics):
+// Pair interactions (one warp per particle over its candidate partners,
+// collected once per lattice step from the 27 cells around it; every pair is
+// evaluated by both partners in the canonical orientation a = min(i, j),
+// b = max(i, j) so the two results are bitwise equal and opposite, with no
+// atomics):
 //   contact (Sec. 2, Eq. 11, 11t): F_n = kn delta_n + eta_n v_n along -n,
 //     tangential spring delta_t (kept per pair in a table owned by a),
 //     rotated into the tangent plane and advanced by v_t dt, F_t = -kt delta_t
@@ -157,11 +158,12 @@ __device__ inline bool pair_geometry(const View& v, const double* __restrict__ R
 }
 
 // Full interaction of the canonical pair (a, b) in precision T, given the
-// minimum-image displacement d and gap h.
+// minimum-image displacement d, gap h and the pair's tangential spring as it
+// stood after the previous sub-step (zero for a new contact).
 template <typename T>
 __device__ void pair_interact(const View& v, const double* __restrict__ Us, const double* __restrict__ Ws,
-                              int a, int b, const T d[3], int k, T h, const int* hcnt, const int* hpart,
-                              const double* hval, T ule, T dt, PairOut<T>& o) {
+                              int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
+                              PairOut<T>& o) {
   const T ra = (T)v.rad[a], rb = (T)v.rad[b];
   const T dist = sqrt(dot3(d, d));
   const T uab[3] = {(T)(Us[3 * a] - Us[3 * b]) - (T)k * ule, (T)(Us[3 * a + 1] - Us[3 * b + 1]),
@@ -178,13 +180,7 @@ __device__ void pair_interact(const View& v, const double* __restrict__ Us, cons
   // ---- contact
   const T overlap = ra + rb - dist;
   if (h < (T)0) {
-    T ht[3] = {0, 0, 0};
-    const int m = hcnt[a];
-    for (int s = 0; s < m; ++s)
-      if (hpart[a * v.K + s] == b) {
-        for (int c = 0; c < 3; ++c) ht[c] = (T)hval[3 * (a * v.K + s) + c];
-        break;
-      }
+    T ht[3] = {spring[0], spring[1], spring[2]};
     const T ws[3] = {ra * wa[0] + rb * wb[0], ra * wa[1] + rb * wb[1], ra * wa[2] + rb * wb[2]};
     T rot[3];
     cross3(ws, n, rot);
@@ -265,19 +261,7 @@ __device__ inline T warp_sum(T x) {
   return x;
 }
 
-struct SpringTables {
-  const int* hcnt_old;
-  const int* hpart_old;
-  const double* hval_old;
-  int* hcnt_new;
-  int* hpart_new;
-  double* hval_new;
-};
-
-// Pair forces on particle i, computed by one warp: the lanes split the
-// candidate partners (one neighbour cell per lane, or a strided slice of all
-// particles in brute-force mode); sums are reduced across the warp and lane 0
-// writes them.  slot: this warp's shared counter of new spring slots.
+// State buffers of one sub-step.
 struct State {
   const double *R, *U, *W;   // read: positions and velocities at the sub-step start
   double *Rn, *Un, *Wn;      // write: after the sub-step
@@ -340,15 +324,103 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
   }
 }
 
-template <typename T>
-__device__ void pairs_of(const View& v, int i, const SpringTables& st, const State& S, T dt, int sample,
-                         bool last, int* slot) {
+// Spring table of one step boundary: per particle a, its touching partners
+// b > a and their tangential springs.  Step t reads table t & 1 and writes
+// table (t + 1) & 1.
+struct SpringTable {
+  int* cnt;
+  int* part;
+  double* val;
+};
+__device__ inline SpringTable spring_table(const View& v, long long t) {
+  return (t & 1) ? SpringTable{v.hcnt1, v.hpart1, v.hval1} : SpringTable{v.hcnt0, v.hpart0, v.hval0};
+}
+
+// Candidate partners of particle i for one lattice step, collected by one
+// warp at the step start: every particle whose centre lies within
+// a_i + a_j + (interaction range) + 1 (particles move less than 0.5 per step,
+// so no pair that interacts during the step is missed).  Entry c of the
+// particle's scratch row holds the partner index and the pair's tangential
+// spring, initialised from the spring table.  Returns the count (all lanes).
+__device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) *slot = 0;
-  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  const double* R = v.R;
+  const double Rx = R[3 * i], Ry = R[3 * i + 1], Rz = R[3 * i + 2];
+  const double ai = v.rad[i];
+  const double delta = v.proto->delta;
+  const double skin = v.hrange + 1.0;
+  int* pj = v.pj + (long long)i * PAIR_SLOTS;
+  double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+  int base = 0;
+  auto consider = [&](int j, bool valid) {
+    bool take = false;
+    if (valid && j != i) {
+      double dx = R[3 * j] - Rx, dy = R[3 * j + 1] - Ry, dz = R[3 * j + 2] - Rz;
+      le_image<double>(dx, dy, dz, delta, v.nx, v.ny, v.nz, v.inv_nx_d, v.inv_ny_d, v.inv_nz_d);
+      const double lim = ai + v.rad[j] + skin;
+      take = dx * dx + dy * dy + dz * dz < lim * lim;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (take) {
+      const int c = base + __popc(bal & lt);
+      if (c < PAIR_SLOTS) {
+        pj[c] = j;
+        // the spring of the canonical pair lives in the table of a = min(i, j)
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+        const int m = old.cnt[a];
+        for (int s = 0; s < m; ++s)
+          if (old.part[a * v.K + s] == b) {
+            h0 = old.val[3 * (a * v.K + s)]; h1 = old.val[3 * (a * v.K + s) + 1]; h2 = old.val[3 * (a * v.K + s) + 2];
+            break;
+          }
+        ph[3 * c] = h0; ph[3 * c + 1] = h1; ph[3 * c + 2] = h2;
+      }
+    }
+    base += __popc(bal);
+  };
+  if (v.brute) {
+    for (int j0 = 0; j0 < v.n; j0 += 32) consider(j0 + lane, j0 + lane < v.n);
+  } else {
+    // lane l < 27 owns neighbour cell l of i's cell at the step start; the
+    // lanes walk their cells' entries in lockstep rounds
+    int s0 = 0, cnt = 0;
+    if (lane < 27) {
+      const int dyc = lane / 9 - 1, dxc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
+      const int zlo = v.ncz >= 3 ? -1 : 0, zhi = v.ncz >= 2 ? 1 : 0;
+      if (dzc >= zlo && dzc <= zhi) {
+        const int* pc = v.pcx + 8 * i;
+        int yc = pc[1] + dyc, cxs = pc[0];
+        if (yc < 0) { yc += v.ncy; cxs = pc[3]; }
+        else if (yc >= v.ncy) { yc -= v.ncy; cxs = pc[4]; }
+        const int xc = wrapi(cxs + dxc, v.ncx);
+        const int zc = wrapi(pc[2] + dzc, v.ncz);
+        const int c = xc + v.ncx * (yc + v.ncy * zc);
+        s0 = v.cell_start[c];
+        cnt = v.cell_start[c + 1] - s0;
+      }
+    }
+    const int rounds = __reduce_max_sync(0xffffffffu, cnt);
+    for (int r = 0; r < rounds; ++r) consider(r < cnt ? v.cell_ids[s0 + r] : -1, r < cnt);
+  }
+  if (base > PAIR_SLOTS && lane == 0) atomicOr(v.err, ERR_PAIRS);
+  return base < PAIR_SLOTS ? base : PAIR_SLOTS;
+}
+
+// Pair forces on particle i for one sub-step, computed by one warp: lane l
+// takes candidates l and l + 32, evaluates each pair in its canonical
+// orientation (a = min, b = max; both partners compute bitwise the same
+// result, so no atomics) and carries the pair's spring in the scratch row.
+// Sums are reduced across the warp; lane 0 integrates.  At the box's last
+// sub-step the particle's touching pairs with larger partners go to the
+// spring table of the next step.
+template <typename T>
+__device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample, bool last,
+                         const SpringTable& next) {
+  const int lane = threadIdx.x & 31;
   const Proto* pr = v.proto;
-  const double delta_d = pr->delta;
-  const T delta = (T)delta_d;
+  const T delta = (T)pr->delta;
   const T ule = (T)pr->ule;
   T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   T cv[9], rv[9];
@@ -356,68 +428,53 @@ __device__ void pairs_of(const View& v, int i, const SpringTables& st, const Sta
   int ncont = 0;
   const double pi = 3.14159265358979323846;
   const double dth = pi / v.nbins;
-
-  auto visit = [&](int j) {
-    if (j == i) return;
+  int* pj = v.pj + (long long)i * PAIR_SLOTS;
+  double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+  bool keep[PAIR_SLOTS / 32] = {};   // touching pair with i = a after this sub-step
+#pragma unroll
+  for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
+    const int c = lane + 32 * slot;
+    if (c >= npairs) continue;
+    const int j = pj[c];
     const int a = i < j ? i : j, b = i < j ? j : i;
     T d[3], h;
     int k;
-    if (!pair_geometry<T>(v, S.R, a, b, delta, d, k, h)) return;
-    PairOut<T> o;
-    pair_interact<T>(v, S.U, S.W, a, b, d, k, h, st.hcnt_old, st.hpart_old, st.hval_old, ule, dt, o);
-    if (i == a) {
-      for (int c = 0; c < 3; ++c) { F[c] += o.Fa[c]; Tq[c] += o.Ta[c]; }
-      if (o.touching) {
-        const int sl = atomicAdd(slot, 1);
-        if (sl < v.K) {
-          st.hpart_new[a * v.K + sl] = b;
-          for (int c = 0; c < 3; ++c) st.hval_new[3 * (a * v.K + sl) + c] = (double)o.ht[c];
-        } else {
-          atomicOr(v.err, ERR_PAIRS);
+    bool touching = false;
+    if (pair_geometry<T>(v, S.R, a, b, delta, d, k, h)) {
+      const T spring[3] = {(T)ph[3 * c], (T)ph[3 * c + 1], (T)ph[3 * c + 2]};
+      PairOut<T> o;
+      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, o);
+      touching = o.touching != 0;
+      for (int x = 0; x < 3; ++x) ph[3 * c + x] = touching ? (double)o.ht[x] : 0.0;
+      if (i == a) {
+        for (int x = 0; x < 3; ++x) { F[x] += o.Fa[x]; Tq[x] += o.Ta[x]; }
+        keep[slot] = touching;
+        if (sample) {
+          const T r[3] = {-o.d[0], -o.d[1], -o.d[2]};
+          if (touching) {
+            for (int x = 0; x < 3; ++x)
+              for (int y = 0; y < 3; ++y) cv[3 * x + y] += (T)0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
+            double th = atan2((double)r[1], (double)r[0]);
+            const double tx = -sin(th), ty = cos(th);
+            if (th < 0.0) th += pi;
+            if (th >= pi) th -= pi;
+            int bin = (int)floor(th / dth);
+            if (bin >= v.nbins) bin = v.nbins - 1;
+            if (bin < 0) bin = 0;
+            atomicAdd(v.hist + 3 * bin, 1.0);
+            atomicAdd(v.hist + 3 * bin + 1, (double)o.fn);
+            atomicAdd(v.hist + 3 * bin + 2, (double)o.Fc[0] * tx + (double)o.Fc[1] * ty);
+            ++ncont;
+          }
+          if (v.F0 > 0.0)
+            for (int x = 0; x < 3; ++x)
+              for (int y = 0; y < 3; ++y) rv[3 * x + y] += (T)0.5 * (r[x] * o.Fr[y] + r[y] * o.Fr[x]);
         }
-      }
-      if (sample) {
-        const T r[3] = {-o.d[0], -o.d[1], -o.d[2]};
-        if (o.touching) {
-          for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) cv[3 * x + y] += (T)0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
-          double th = atan2((double)r[1], (double)r[0]);
-          const double tx = -sin(th), ty = cos(th);
-          if (th < 0.0) th += pi;
-          if (th >= pi) th -= pi;
-          int bin = (int)floor(th / dth);
-          if (bin >= v.nbins) bin = v.nbins - 1;
-          if (bin < 0) bin = 0;
-          atomicAdd(v.hist + 3 * bin, 1.0);
-          atomicAdd(v.hist + 3 * bin + 1, (double)o.fn);
-          atomicAdd(v.hist + 3 * bin + 2, (double)o.Fc[0] * tx + (double)o.Fc[1] * ty);
-          ++ncont;
-        }
-        if (v.F0 > 0.0)
-          for (int x = 0; x < 3; ++x)
-            for (int y = 0; y < 3; ++y) rv[3 * x + y] += (T)0.5 * (r[x] * o.Fr[y] + r[y] * o.Fr[x]);
+      } else {
+        for (int x = 0; x < 3; ++x) { F[x] -= o.Fa[x]; Tq[x] += o.Tb[x]; }
       }
     } else {
-      for (int c = 0; c < 3; ++c) { F[c] -= o.Fa[c]; Tq[c] += o.Tb[c]; }
-    }
-  };
-
-  if (v.brute) {
-    for (int j = lane; j < v.n; j += 32) visit(j);
-  } else if (lane < 27) {
-    const int dyc = lane / 9 - 1, dxc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
-    const int zlo = v.ncz >= 3 ? -1 : 0, zhi = v.ncz >= 2 ? 1 : 0;
-    if (dzc >= zlo && dzc <= zhi) {
-      // i's cell at the step start: the lists stay valid over the sub-steps
-      const int* pc = v.pcx + 8 * i;
-      int yc = pc[1] + dyc, cxs = pc[0];
-      if (yc < 0) { yc += v.ncy; cxs = pc[3]; }
-      else if (yc >= v.ncy) { yc -= v.ncy; cxs = pc[4]; }
-      const int xc = wrapi(cxs + dxc, v.ncx);
-      const int zc = wrapi(pc[2] + dzc, v.ncz);
-      const int c = xc + v.ncx * (yc + v.ncy * zc);
-      const int s0 = v.cell_start[c], e0 = v.cell_start[c + 1];
-      for (int t = s0; t < e0; ++t) visit(v.cell_ids[t]);
+      ph[3 * c] = 0.0; ph[3 * c + 1] = 0.0; ph[3 * c + 2] = 0.0;
     }
   }
   for (int c = 0; c < 3; ++c) { F[c] = warp_sum(F[c]); Tq[c] = warp_sum(Tq[c]); }
@@ -425,11 +482,30 @@ __device__ void pairs_of(const View& v, int i, const SpringTables& st, const Sta
     for (int c = 0; c < 9; ++c) { cv[c] = warp_sum(cv[c]); rv[c] = warp_sum(rv[c]); }
     for (int o = 16; o > 0; o >>= 1) ncont += __shfl_xor_sync(0xffffffffu, ncont, o);
   }
+  if (last) {
+    // touching pairs (i, b > i) in candidate order -> next step's table
+    int base = 0;
+#pragma unroll
+    for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
+      const unsigned bal = __ballot_sync(0xffffffffu, keep[slot]);
+      if (keep[slot]) {
+        const int m = base + __popc(bal & ((1u << lane) - 1u));
+        const int c = lane + 32 * slot;
+        if (m < v.K) {
+          next.part[i * v.K + m] = pj[c];
+          for (int x = 0; x < 3; ++x) next.val[3 * (i * v.K + m) + x] = ph[3 * c + x];
+        }
+      }
+      base += __popc(bal);
+    }
+    if (lane == 0) {
+      next.cnt[i] = base < v.K ? base : v.K;
+      if (base > v.K) atomicOr(v.err, ERR_PAIRS);
+    }
+  }
   __syncwarp();
   if (lane == 0) {
     integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8);
-    const int m = *slot;
-    st.hcnt_new[i] = m < v.K ? m : v.K;
     if (sample) {
       for (int c = 0; c < 9; ++c) { v.cvir_part[9 * i + c] = (double)cv[c]; v.rvir_part[9 * i + c] = (double)rv[c]; }
       v.ncont_part[i] = ncont;
@@ -453,17 +529,28 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_dem_step(Batch B) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ int s_slot[4];
   const int wib = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * 4 + wib, nwarps = gridDim.x * 4;
   const int ntot = B.part_off[B.nbox];
+  // candidate partners of every moving particle at the step start
+  for (int g = gwarp; g < ntot; g += nwarps) {
+    const int bx = box_of(B.part_off, B.nbox, g);
+    const View& v = B.views[bx];
+    if (!v.move) continue;
+    const int i = g - B.part_off[bx];
+    const int np = collect_pairs(v, i, spring_table(v, v.proto->t));
+    if ((threadIdx.x & 31) == 0) v.pcnt[i] = np;
+  }
   bool any_odd = false;
   for (int b = 0; b < B.nbox; ++b) {
     const View& v = B.views[b];
     if (v.move && v.n > 0 && (v.nsub & 1)) any_odd = true;
   }
   if (any_odd) {
-    // odd sub-step count: the first sub-step reads a copy in the second buffer
+    // odd sub-step count: the first sub-step reads a copy in the second
+    // buffer (and writes the canonical one, so every warp's candidate search
+    // above must be done first)
+    grid.sync();
     const int gthr = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     for (int g = gthr; g < ntot; g += nthr) {
       const int bx = box_of(B.part_off, B.nbox, g);
@@ -483,15 +570,12 @@ __global__ void __launch_bounds__(128) k_dem_step(Batch B) {
       const int nsub = v.nsub;
       if (!v.move || sub >= nsub) continue;
       const int i = g - B.part_off[bx];
-      const SpringTables st0{v.hcnt0, v.hpart0, v.hval0, v.hcnt1, v.hpart1, v.hval1};
-      const SpringTables st1{v.hcnt1, v.hpart1, v.hval1, v.hcnt0, v.hpart0, v.hval0};
-      const int parity0 = (int)((v.proto->t * (long long)nsub) & 1);
-      const SpringTables& st = ((parity0 ^ sub) & 1) ? st1 : st0;
       // sub-step s reads A when (nsub - s) is even, so the last write lands in A
       const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W};
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
-      pairs_of<T>(v, i, st, S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1, &s_slot[wib]);
+      pairs_of<T>(v, i, v.pcnt[i], S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1,
+                  spring_table(v, v.proto->t + 1));
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }

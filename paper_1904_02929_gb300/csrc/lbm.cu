@@ -2,24 +2,29 @@
 //
 // Per fluid node r and direction p the post-streaming population is
 //   n_p(r, t+1) = n*_p(r - c_p, t)                          (Eq. 3, pull form)
-// with three exceptions:
-//   * the source r - c_p is solid: moving bounce-back (Eq. 7, 8)
+// with two exceptions:
+//   * the source r - c_p = s is solid: moving bounce-back (Eq. 7, 8)
 //       n_p(r, t+1) = n*_q(r, t) - 6 C^q rho0 (u_b . c_q),  q = -p,
-//       u_b = U + Omega x (r_b - R), r_b = r + c_q / 2;
+//       u_b = U + Omega x (r_b - R), r_b = r + c_q / 2.
+//     The boundary-link kernel, which runs after the node map is updated,
+//     stores this value in the slot p of s (each such slot has exactly one
+//     receiver), so the pull reads it like any other population;
 //   * the source lies beyond a Lees-Edwards plane (y = 0 from below or
 //     y = ny-1 from above): the image box is shifted by -/+ Delta in x and
 //     moves with -/+ U_LE, so the value is linearly interpolated between the
 //     two nodes straddling x - c_px +/- Delta on the opposite plane and
 //     Galilean-shifted by n^eq(rho, j -/+ rho U_LE e_x) - n^eq(rho, j);
-//     the nearer of the two nodes decides solid (bounce-back) or fluid, and
-//     a solid farther node leaves the nearer one alone as the source;
-//   * solid nodes are skipped.
-// Then the BGK collision (Eq. 4, 5 with every non-conserved mode relaxed by
-// 1/tau) and an optional uniform body force 3 C^q (g . c_q).  Each block also
-// sums the viscous stress -(1 - 1/(2 tau)) Pi^neq of its fluid nodes.
+//     the nearer of the two nodes decides solid (bounce-back, evaluated
+//     here) or fluid, and a solid farther node leaves the nearer one alone
+//     as the source.
+// Solid nodes store the rest state (their slots are rewritten by the link
+// kernel where a receiver needs them).  Then the BGK collision (Eq. 4, 5
+// with every non-conserved mode relaxed by 1/tau) and an optional uniform
+// body force 3 C^q (g . c_q).  Each block also sums the viscous stress
+// -(1 - 1/(2 tau)) Pi^neq of its fluid nodes.
 //
 // Bytes per fluid node and step: 19 loads + 19 stores of the storage type
-// plus the 4-byte node mask (algorithmic 2 * 19 * s).
+// plus the 4-byte owner word (algorithmic 2 * 19 * s).
 #include "susp_dev.cuh"
 
 namespace susp_dev {
@@ -102,8 +107,7 @@ __device__ __forceinline__ typename Store<P>::C le_pull(const View& v, const typ
 
 // Plain pull of population p from r - c_p (32-bit node offsets: interior
 // offsets are fixed sums of the precomputed x / z wrap deltas and -c_py nx).
-// Where r - c_p is solid the value read is that node's stored rest state; the
-// bounce-back value replaces it below.
+// Where r - c_p is solid the slot holds the bounce-back value.
 template <int P, int p, bool BND>
 __device__ __forceinline__ void pull_one(const View& v, const typename Store<P>::T* __restrict__ fin,
                                          const typename Store<P>::C* __restrict__ plb,
@@ -141,32 +145,21 @@ struct PullAll<P, 19, BND> {
                                              int, int, typename Store<P>::C, typename Store<P>::C (&)[19]) {}
 };
 
-// Directions whose pull crosses a Lees-Edwards plane at y = 0 (c_py = +1) and
-// at y = ny-1 (c_py = -1); their mask bits are never set.
-__host__ __device__ constexpr uint32_t crossing_bits(int sign) {
-  uint32_t b = 0;
-  for (int p = 1; p < 19; ++p)
-    if (D3Q19::cy(p) == sign) b |= 1u << p;
-  return b;
-}
-
-// One lattice node: pull (Eq. 3) with bounce-back (Eq. 7) and Lees-Edwards
-// planes, BGK collision (Eq. 4, 5), store, viscous-stress accumulation.
-// BND: the node lies on a Lees-Edwards plane (y = 0 or ny-1); interior rows
-// compile without the plane code.
+// One lattice node: pull (Eq. 3; bounce-back values sit in the solid
+// sources' slots) with the Lees-Edwards planes, BGK collision (Eq. 4, 5),
+// store, viscous-stress accumulation.  BND: the node lies on a Lees-Edwards
+// plane (y = 0 or ny-1); interior rows compile without the plane code.
 template <int P, bool BND>
 __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::T* __restrict__ fin,
                                         typename Store<P>::T* __restrict__ fout, int x, int y, int z,
-                                        int dzm, int dzp, typename Store<P>::C (&acc)[6],
-                                        typename Store<P>::C* corr) {
+                                        int dzm, int dzp, typename Store<P>::C (&acc)[6]) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   const int nx = v.nx;
   const int idx = x + nx * (y + v.ny * z);
   const size_t nc = (size_t)v.ncell;
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  const uint32_t m = v.mask[idx];
-  if (m & 1u) {
+  if (v.owner[idx] >= 0) {
     // solid node: its populations are undefined; writing the rest state keeps
     // every stored sector complete (no read-for-ownership of partial sectors)
 #pragma unroll
@@ -180,48 +173,6 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   TC n[19];
   n[0] = S::load(fin, idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
   PullAll<P, 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
-  // Moving bounce-back (Eq. 7) for the set mask bits: n_p = n*_q(r) + wall
-  // term, q = -p.  For links to one particle i, u_b . c_q with u_b at
-  // r + c_q / 2 equals ub0 . c_q with ub0 the rigid-body velocity at the node
-  // (the c_q / 2 part of the arm drops out of (Omega x arm) . c_q), so ub0 is
-  // formed once per node.  Values are staged in shared memory (dynamic index).
-  uint32_t links = m & ~1u;
-  if (BND) {
-    if (y == 0) links &= ~crossing_bits(1);
-    if (y == v.ny - 1) links &= ~crossing_bits(-1);
-  }
-  const uint32_t corr_bits = links;
-  if (links) {
-    const TC delta = sel<TC>(pr->delta, pr->delta_f), ule = sel<TC>(pr->ule, pr->ule_f);
-    const TC w6 = (TC)6 * rho0;
-    const int p0 = __ffs(links) - 1;
-    const int i0 = v.owner[wrap1(x - D3Q19::cx(p0), nx) + nx * ((y - D3Q19::cy(p0)) + v.ny * wrap1(z - D3Q19::cz(p0), v.nz))];
-    const TC* pp = plb + 12 * i0;
-    TC rx = (TC)x - pp[0], ry = (TC)y - pp[1], rz = (TC)z - pp[2];
-    const int k0 = le_image_v(v, rx, ry, rz, delta);
-    const TC ubx = pp[3] + (pp[7] * rz - pp[8] * ry) + (TC)k0 * ule;
-    const TC uby = pp[4] + (pp[8] * rx - pp[6] * rz);
-    const TC ubz = pp[5] + (pp[6] * ry - pp[7] * rx);
-    while (links) {
-      const int p = __ffs(links) - 1;
-      links &= links - 1;
-      const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
-      const int q = D3Q19::opp(p);
-      const int i = p == p0 ? i0 : v.owner[wrap1(x - cpx, nx) + nx * ((y - cpy) + v.ny * wrap1(z - cpz, v.nz))];
-      const TC self = S::load(fin + (size_t)q * nc, idx, (TC)wq<TC>(q) * rho0, (TC)v.inv_scale);
-      TC wterm;
-      if (i == i0) {
-        // -6 C^q rho0 (u_b . c_q) = +6 C^p rho0 (ub0 . c_p)
-        wterm = w6 * wq<TC>(p) * (ubx * (TC)cpx + uby * (TC)cpy + ubz * (TC)cpz);
-      } else {
-        wterm = wall_term<TC>(v, plb, i, x, y, z, q, delta, ule, rho0);
-      }
-      corr[(p - 1) * 256 + threadIdx.x] = self + wterm;
-    }
-#pragma unroll
-    for (int p = 1; p < 19; ++p)
-      if ((corr_bits >> p) & 1u) n[p] = corr[(p - 1) * 256 + threadIdx.x];
-  }
   TC rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
   for (int q = 0; q < 19; ++q) {
@@ -269,7 +220,6 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   using TC = typename Store<P>::C;
   using T = typename Store<P>::T;
   __shared__ TC red[32 * 6];
-  __shared__ TC corr[18 * 256];   // staged bounce-back values, [direction - 1][thread]
   const int total = B.tile_off[B.nbox];
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
@@ -294,8 +244,8 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
       const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
       if (x < v.nx && y < v.ny) {
         // a warp covers one x row, so this branch is warp-uniform
-        if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc, corr);
-        else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc, corr);
+        if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc);
+        else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc);
       }
     }
     block_sum<TC, 6>(acc, red);

@@ -102,7 +102,6 @@ struct View {
   void* fa;                     // population buffers; step t reads fa when t is even
   void* fb;
   double* visc_acc;             // [6] viscous-stress sum of the current step
-  uint32_t* mask;               // bit 0 solid, bit p: pull source of p is solid (not LE-crossing)
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
   // particles
@@ -114,13 +113,15 @@ struct View {
   double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
   double *slet_part, *cvir_part, *rvir_part;   // [n][9]
   int* ncont_part;              // [n]
-  uint32_t* links;              // per-particle segments of (cell << 5 | p)
-  int *link_off, *link_cap, *link_cnt;
   // cell list
   int ncx, ncy, ncz, brute;
   double csx, csy, csz, inv_csx, inv_csy, inv_csz;
   int *cell_start, *cell_cnt, *cell_ids, *pcell;
   int ncells;
+  // per-step candidate partners and their springs: [n][PAIR_SLOTS]
+  int* pj;
+  double* ph;                   // [n][PAIR_SLOTS][3]
+  int* pcnt;                    // [n]
   // tangential-spring table: per particle a, partners b > a
   int K;
   int *hcnt0, *hpart0, *hcnt1, *hpart1;
@@ -135,6 +136,10 @@ struct View {
   Proto* proto;
   int* err;
 };
+
+// ERR_LINKS: a particle has more surface nodes than the link kernel stages.
+// Candidate partners per particle and lattice step (two per lane of a warp).
+constexpr int PAIR_SLOTS = 64;
 
 enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
 
