@@ -164,12 +164,19 @@ typedef struct {
 susp_status susp_get_info(susp *h, susp_info *info);
 
 /* Instrumentation (no counterpart in the paper): when enabled, each step
- * brackets its collide-stream launch with CUDA events on the handle's stream
- * (at most 4096 steps per window).  susp_profile_read synchronises and
+ * records CUDA events on the handle's stream at its stage boundaries (at
+ * most 4096 steps per window).  susp_profile_read synchronises and
  * returns the summed launch time in ms and the number of launches, then
  * starts a new window. */
 susp_status susp_profile(susp *h, int enable);
 susp_status susp_profile_read(susp *h, double *ms_total, int *launches);
+/* The same window split by stage: ms[6] receives the summed times of (0) the
+ * Lees-Edwards plane moments, (1) the collide-stream, (2) the particle
+ * sub-steps with their cell list, (3) the stress / protocol finalisation,
+ * (4) the node-map update (uncover, cover) and (5) the boundary links; *steps
+ * the number of profiled steps.  Synchronises and starts a new window (it
+ * shares the window with susp_profile_read). */
+susp_status susp_profile_stages(susp *h, double *ms, int *steps);
 
 /* Allocation-free fluid step.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory or hand the library a
@@ -237,6 +244,7 @@ susp_status susp_batch_step(susp_batch *b, int nsteps);
 /* As susp_profile / susp_profile_read, for the batch's collide-stream launch. */
 susp_status susp_batch_profile(susp_batch *b, int enable);
 susp_status susp_batch_profile_read(susp_batch *b, double *ms_total, int *launches);
+susp_status susp_batch_profile_stages(susp_batch *b, double *ms, int *steps);
 /* Device error status of every attached box, in attach order (the order
  * detaching keeps), into status[0 .. susp_batch_size(b)); n is the array's
  * length.  One gather launch and one copy for the whole batch; synchronises

@@ -203,22 +203,25 @@ __global__ void __launch_bounds__(512) k_finalize(Batch B) {
   }
   __syncthreads();
   if (threadIdx.x < 6) v.visc_acc[threadIdx.x] = 0.0;
-  if (threadIdx.x != 0) return;
-  // visc partials: xx yy zz xy xz yz -> full 3x3
-  const double vs[9] = {tot[0], tot[3], tot[4], tot[3], tot[1], tot[5], tot[4], tot[5], tot[2]};
-  double* S = v.sums;
-  double* Cc = v.sums + 36;
-  for (int k = 0; k < 36; ++k) {
+  if (threadIdx.x < 36) {
+    // compensated time sums, one entry per thread; the viscous partials are
+    // xx yy zz xy xz yz, expanded to the full 3 x 3
+    const int k = threadIdx.x;
     double x;
-    if (k < 9) x = vs[k];
-    else if (k < 18) x = tot[6 + (k - 9)];
+    if (k < 9) {
+      const int vmap[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
+      x = tot[vmap[k]];
+    } else if (k < 18) x = tot[6 + (k - 9)];
     else if (k < 27) x = v.move ? tot[15 + (k - 18)] : 0.0;
     else x = v.move ? tot[25 + (k - 27)] : 0.0;
+    double* S = v.sums;
+    double* Cc = v.sums + 36;
     const double y = x - Cc[k];
     const double t = S[k] + y;
     Cc[k] = (t - S[k]) - y;
     S[k] = t;
   }
+  if (threadIdx.x != 0) return;
   v.counters[0] += 1ULL;
   if (v.move) v.counters[1] += (unsigned long long)(tot[24] + 0.5);
   // protocol: t -> t+1
@@ -246,7 +249,7 @@ struct GraphSlot {
   bool valid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t n0 = nullptr, n1 = nullptr;   // event-record nodes around the collide-stream
+  cudaGraphNode_t nodes[7] = {};   // event-record nodes at the stage boundaries (profiled graph)
 };
 
 static const int PROF_MAX = 4096;
@@ -320,19 +323,29 @@ static void eng_drop_graphs(Engine& e) {
   }
 }
 
-// The launches of one lattice step; ev0 / ev1 (optional) bracket the
-// collide-stream launch.
-static cudaError_t eng_enqueue(Engine& e, cudaEvent_t ev0, cudaEvent_t ev1) {
+// Stage boundaries recorded when a step is profiled: start, after the plane
+// moments, the collide-stream, the particle sub-steps (cell list included),
+// the finalisation, the node-map update, and the boundary links.
+static const int NEV = 7;
+
+// The launches of one lattice step; evs (optional, NEV events) mark the stage
+// boundaries.
+static cudaError_t eng_enqueue(Engine& e, const cudaEvent_t* evs) {
   cudaStream_t s = e.stream;
   cudaError_t err = cudaSuccess;
+  if (evs) cudaEventRecord(evs[0], s);
   launch_plane_moments(e.prec, e.B, e.nplane, s);
-  if (ev0) cudaEventRecord(ev0, s);
+  if (evs) cudaEventRecord(evs[1], s);
   launch_collide_stream(e.prec, e.B, e.lb_grid, s);
-  if (ev1) cudaEventRecord(ev1, s);
+  if (evs) cudaEventRecord(evs[2], s);
   if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
+  if (evs) cudaEventRecord(evs[3], s);
   k_finalize<<<e.nbox, 512, 0, s>>>(e.B);
+  if (evs) cudaEventRecord(evs[4], s);
   launch_node_update(e.prec, e.B, e.nparts, s);
+  if (evs) cudaEventRecord(evs[5], s);
   launch_links(e.prec, e.B, e.nparts, s);
+  if (evs) cudaEventRecord(evs[6], s);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
 
@@ -346,14 +359,14 @@ static bool eng_capture(Engine& e, int timed) {
     cudaGetLastError();
     return false;
   }
-  cudaError_t le = eng_enqueue(e, timed ? e.ev[0] : nullptr, timed ? e.ev[1] : nullptr);
+  cudaError_t le = eng_enqueue(e, timed ? e.ev.data() : nullptr);
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   if (le != cudaSuccess || ce != cudaSuccess || !graph) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
     return false;
   }
-  g.n0 = g.n1 = nullptr;
+  for (auto& n : g.nodes) n = nullptr;
   if (timed) {
     size_t nn = 0;
     cudaGraphGetNodes(graph, nullptr, &nn);
@@ -364,13 +377,14 @@ static bool eng_capture(Engine& e, int timed) {
       if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
       cudaEvent_t ev = nullptr;
       cudaGraphEventRecordNodeGetEvent(nd, &ev);
-      if (ev == e.ev[0]) g.n0 = nd;
-      if (ev == e.ev[1]) g.n1 = nd;
+      for (int k = 0; k < NEV; ++k)
+        if (ev == e.ev[k]) g.nodes[k] = nd;
     }
-    if (!g.n0 || !g.n1) {
-      cudaGraphDestroy(graph);
-      return false;
-    }
+    for (int k = 0; k < NEV; ++k)
+      if (!g.nodes[k]) {
+        cudaGraphDestroy(graph);
+        return false;
+      }
   }
   if (cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -385,22 +399,20 @@ static bool eng_capture(Engine& e, int timed) {
 static susp_status eng_step(Engine& e, int nsteps) {
   for (int it = 0; it < nsteps; ++it) {
     const int timed = (e.prof && e.prof_n < PROF_MAX) ? 1 : 0;
-    cudaEvent_t ev0 = timed ? e.ev[2 * e.prof_n] : nullptr, ev1 = timed ? e.ev[2 * e.prof_n + 1] : nullptr;
+    const cudaEvent_t* evs = timed ? e.ev.data() + (size_t)NEV * e.prof_n : nullptr;
     bool done = false;
     if (e.use_graphs && e.stream != nullptr) {
       if (!e.graphs[timed].valid && !eng_capture(e, timed)) e.use_graphs = false;
       if (e.use_graphs) {
         GraphSlot& g = e.graphs[timed];
-        if (timed) {
-          cudaGraphExecEventRecordNodeSetEvent(g.exec, g.n0, ev0);
-          cudaGraphExecEventRecordNodeSetEvent(g.exec, g.n1, ev1);
-        }
+        if (timed)
+          for (int k = 0; k < NEV; ++k) cudaGraphExecEventRecordNodeSetEvent(g.exec, g.nodes[k], evs[k]);
         done = cudaGraphLaunch(g.exec, e.stream) == cudaSuccess;
         if (!done) { cudaGetLastError(); e.use_graphs = false; }
       }
     }
     if (!done) {
-      susp_status st = cuda_check(eng_enqueue(e, ev0, ev1), "step launch");
+      susp_status st = cuda_check(eng_enqueue(e, evs), "step launch");
       if (st) return st;
     }
     if (timed) ++e.prof_n;
@@ -410,7 +422,7 @@ static susp_status eng_step(Engine& e, int nsteps) {
 
 static susp_status eng_profile(Engine& e, int enable) {
   if (enable && e.ev.empty()) {
-    e.ev.resize(2 * PROF_MAX);
+    e.ev.resize((size_t)NEV * PROF_MAX);
     for (auto& x : e.ev) {
       susp_status st = cuda_check(cudaEventCreate(&x), "cudaEventCreate");
       if (st) return st;
@@ -421,19 +433,31 @@ static susp_status eng_profile(Engine& e, int enable) {
   return SUSP_OK;
 }
 
-static susp_status eng_profile_read(Engine& e, double* ms_total, int* launches) {
+// Summed stage times of the profiled steps (ms[NEV - 1]); starts a new window.
+static susp_status eng_profile_stages(Engine& e, double* ms, int* steps) {
   susp_status st = cuda_check(cudaStreamSynchronize(e.stream), "sync");
   if (st) return st;
-  double tot = 0.0;
-  for (int k = 0; k < e.prof_n; ++k) {
-    float ms = 0.0f;
-    st = cuda_check(cudaEventElapsedTime(&ms, e.ev[2 * k], e.ev[2 * k + 1]), "cudaEventElapsedTime");
-    if (st) return st;
-    tot += ms;
-  }
-  if (ms_total) *ms_total = tot;
-  if (launches) *launches = e.prof_n;
+  double tot[NEV - 1] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < e.prof_n; ++k)
+    for (int j = 0; j + 1 < NEV; ++j) {
+      float m = 0.0f;
+      st = cuda_check(cudaEventElapsedTime(&m, e.ev[(size_t)NEV * k + j], e.ev[(size_t)NEV * k + j + 1]),
+                      "cudaEventElapsedTime");
+      if (st) return st;
+      tot[j] += m;
+    }
+  if (ms)
+    for (int j = 0; j + 1 < NEV; ++j) ms[j] = tot[j];
+  if (steps) *steps = e.prof_n;
   e.prof_n = 0;
+  return SUSP_OK;
+}
+
+static susp_status eng_profile_read(Engine& e, double* ms_total, int* launches) {
+  double ms[NEV - 1];
+  susp_status st = eng_profile_stages(e, ms, launches);
+  if (st) return st;
+  if (ms_total) *ms_total = ms[1];
   return SUSP_OK;
 }
 
@@ -616,7 +640,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   susp_status st = SUSP_OK;
   // zero everything past the populations, then fill
   st = cuda_check(cudaMemsetAsync(w + L.owner, 0, L.total - L.owner, s), "memset workspace");
-  if (st) { delete h; return st; }
+  if (st) { eng_release(h->eng); delete h; return st; }
   cudaMemsetAsync(v.owner, 0xff, 4 * v.ncell, s);
   cudaMemcpyAsync(w + L.views, &v, sizeof(View), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + L.tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
@@ -651,7 +675,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   cudaMemcpyAsync(v.proto, &pr, sizeof pr, cudaMemcpyHostToDevice, s);
   // the copies above read pageable host memory: wait before it goes away
   st = cuda_check(cudaStreamSynchronize(s), "upload");
-  if (st) { delete h; return st; }
+  if (st) { eng_release(h->eng); delete h; return st; }
   k_proto_set<<<1, 1, 0, s>>>(v.proto, v.nx, 0, 0.0, 0.0, 0.0, 0.0);
   launch_init_pop(h->prec, v, v.fa, s);
   launch_init_pop(h->prec, v, v.fb, s);
@@ -659,9 +683,9 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   launch_claim(h->prec, e.B, n, s);
   refresh_links(h);
   st = cuda_check(cudaGetLastError(), "launch");
-  if (st) { delete h; return st; }
+  if (st) { eng_release(h->eng); delete h; return st; }
   st = device_status(h);
-  if (st) { delete h; return st; }
+  if (st) { eng_release(h->eng); delete h; return st; }
   *out = h;
   return SUSP_OK;
 }
@@ -930,6 +954,11 @@ susp_status susp_profile_read(susp* h, double* ms_total, int* launches) {
   return eng_profile_read(h->eng, ms_total, launches);
 }
 
+susp_status susp_profile_stages(susp* h, double* ms, int* steps) {
+  if (!h) return fail(SUSP_EINVAL, "NULL handle");
+  return eng_profile_stages(h->eng, ms, steps);
+}
+
 susp_status susp_set_graphs(susp* h, int enable) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
   susp_status st = cuda_check(cudaStreamSynchronize(h->eng.stream), "sync");
@@ -1057,6 +1086,11 @@ susp_status susp_batch_errors(susp_batch* b, int* status, int n) {
   for (int k = 0; k < nb; ++k) status[k] = (int)err_status(err[k]);
   g_err = keep;
   return SUSP_OK;
+}
+
+susp_status susp_batch_profile_stages(susp_batch* b, double* ms, int* steps) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  return eng_profile_stages(b->eng, ms, steps);
 }
 
 void susp_batch_destroy(susp_batch* b) {

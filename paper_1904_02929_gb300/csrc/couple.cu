@@ -278,10 +278,20 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) acc[k] = 0;
   const int items = nn * 18;
+  // a receiver deeper than a_map - 0.05 inside this particle's own mapped
+  // sphere is one of its solid nodes (the node map holds every node closer
+  // than a_map): no link, and no need to look it up
+  const TC deep = am > (TC)0.05 ? (am - (TC)0.05) * (am - (TC)0.05) : (TC)0;
   for (int t = threadIdx.x; t < items; t += blockDim.x) {
     const uint32_t w = s_node[t / 18];
     const int p = 1 + t % 18;
     const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
+    const int ryn = y + D3Q19::cy(p);
+    if (ryn >= 0 && ryn < v.ny) {
+      TC ex = (TC)(x + D3Q19::cx(p)) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p)) - Rz;
+      le_image_v(v, ex, ey, ez, delta);
+      if (ex * ex + ey * ey + ez * ez < deep) continue;
+    }
     int rx, ry, rz;
     bool crossing;
     const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);

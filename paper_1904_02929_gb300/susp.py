@@ -94,6 +94,10 @@ def library() -> C.CDLL:
         L.susp_profile.argtypes = [C.c_void_p, C.c_int]
         L.susp_profile_read.restype = C.c_int
         L.susp_profile_read.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+        L.susp_profile_stages.restype = C.c_int
+        L.susp_profile_stages.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+        L.susp_batch_profile_stages.restype = C.c_int
+        L.susp_batch_profile_stages.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
         L.susp_fluid_step_noalloc.restype = C.c_int
         L.susp_fluid_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                               C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -223,6 +227,24 @@ def susp_profile_read(h):
     n = C.c_int(0)
     _check(library().susp_profile_read(h, C.byref(ms), C.byref(n)), "susp_profile_read")
     return float(ms.value), int(n.value)
+
+
+STAGES = ("plane_moments", "collide_stream", "particles", "finalize", "node_map", "links")
+
+
+def susp_profile_stages(h):
+    ms = np.zeros(6)
+    n = C.c_int(0)
+    _check(library().susp_profile_stages(h, ms.ctypes.data_as(_D), C.byref(n)), "susp_profile_stages")
+    return dict(zip(STAGES, ms.tolist())), int(n.value)
+
+
+def susp_batch_profile_stages(b):
+    ms = np.zeros(6)
+    n = C.c_int(0)
+    _check(library().susp_batch_profile_stages(b, ms.ctypes.data_as(_D), C.byref(n)),
+           "susp_batch_profile_stages")
+    return dict(zip(STAGES, ms.tolist())), int(n.value)
 
 
 def susp_fluid_step_noalloc(nx, ny, nz, tau, delta, u_le, f_in_ptr, f_out_ptr, visc_out_ptr,
