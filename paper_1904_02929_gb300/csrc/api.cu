@@ -47,7 +47,6 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t fa, fb, owner, pm, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
-  size_t slet, cvir, rvir, ncont;
   size_t cstart, ccnt, cids, pcell, pj, ph, pcnt;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
   size_t sums, hist, counters, proto, err;
@@ -101,7 +100,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.fb = take(19 * nc * esize(prec));
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
-  L.vacc = take(6 * 8);
+  L.vacc = take(34 * 8);
   L.views = take(sizeof(View));
   L.tabs = take(4 * 2 * sizeof(int));   // the one-box batch tables
   L.R = take(24 * nn); L.U = take(24 * nn); L.W = take(24 * nn);
@@ -111,14 +110,15 @@ void make_layout(const susp_params* p, Layout& L) {
   L.plb = take(12 * csize(prec) * nn);
   L.Fh = take(24 * nn); L.Th = take(24 * nn); L.Fcov = take(24 * nn); L.Tcov = take(24 * nn);
   L.Fp = take(24 * nn); L.Tp = take(24 * nn);
-  L.slet = take(72 * nn); L.cvir = take(72 * nn); L.rvir = take(72 * nn); L.ncont = take(4 * nn);
   // cell list geometry
   double amax = 0.0;
   for (int i = 0; i < n; ++i) amax = std::max(amax, p->radius[i]);
   L.hrange = hrange_of(p);
   const double cmin = 2.0 * amax + L.hrange + 1.0;
   int ncx = (int)floor(p->nx / cmin), ncy = (int)floor(p->ny / cmin), ncz = (int)floor(p->nz / cmin);
-  if (ncx < 3 || ncy < 3) { ncx = ncy = ncz = 1; L.brute = 1; }
+  // up to BRUTE_PAIRS_MAX particles every warp scans all particles for its
+  // candidates (cheaper than building the cell list); beyond, the cell list
+  if (ncx < 3 || ncy < 3 || n <= BRUTE_PAIRS_MAX) { ncx = ncy = ncz = 1; L.brute = 1; }
   else { L.brute = 0; if (ncz < 1) ncz = 1; }
   L.ncx = ncx; L.ncy = ncy; L.ncz = ncz;
   L.ncells = ncx * ncy * ncz;
@@ -173,36 +173,17 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
   *pp = s;
 }
 
-// End of step t, one block per box: sum the per-particle stress partials
-// (each thread accumulates a strided set of particles, then one fixed-order
-// block reduction) and the step's viscous stress, add them to the compensated
-// time sums, then advance the protocol to t+1.
-__global__ void __launch_bounds__(512) k_finalize(Batch B) {
+// End of step t, one block per box: the step's sums (accumulated by the
+// collide-stream, boundary-link and particle kernels) go into the compensated
+// time sums and are cleared; then the protocol advances to t+1.
+__global__ void __launch_bounds__(64) k_finalize(Batch B) {
   const View& v = B.views[blockIdx.x];
-  __shared__ double red[16 * 28];
-  __shared__ double tot[37];
-  // quantity k: 0-5 viscous, 6-14 stresslet, 15-23 contact virial,
-  // 24 contact count, 25-33 repulsive virial (34-36 unused)
-  double a[28];   // 0-8 stresslet, 9-17 contact virial, 18-26 repulsive virial, 27 count
-#pragma unroll
-  for (int k = 0; k < 28; ++k) a[k] = 0.0;
-  for (int i = threadIdx.x; i < v.n; i += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      a[k] += v.slet_part[9 * i + k];
-      a[9 + k] += v.cvir_part[9 * i + k];
-      a[18 + k] += v.rvir_part[9 * i + k];
-    }
-    a[27] += (double)v.ncont_part[i];
-  }
-  block_sum<double, 28>(a, red);
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 6; ++k) tot[k] = v.visc_acc[k];
-    for (int k = 0; k < 9; ++k) { tot[6 + k] = a[k]; tot[15 + k] = a[9 + k]; tot[25 + k] = a[18 + k]; }
-    tot[24] = a[27];
-  }
+  __shared__ double tot[34];
+  // 0-5 viscous, 6-14 stresslet, 15-23 contact virial, 24 contact count,
+  // 25-33 repulsive virial
+  if (threadIdx.x < 34) tot[threadIdx.x] = v.step_acc[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x < 6) v.visc_acc[threadIdx.x] = 0.0;
+  if (threadIdx.x < 34) v.step_acc[threadIdx.x] = 0.0;
   if (threadIdx.x < 36) {
     // compensated time sums, one entry per thread; the viscous partials are
     // xx yy zz xy xz yz, expanded to the full 3 x 3
@@ -340,7 +321,7 @@ static cudaError_t eng_enqueue(Engine& e, const cudaEvent_t* evs) {
   if (evs) cudaEventRecord(evs[2], s);
   if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
   if (evs) cudaEventRecord(evs[3], s);
-  k_finalize<<<e.nbox, 512, 0, s>>>(e.B);
+  k_finalize<<<e.nbox, 64, 0, s>>>(e.B);
   if (evs) cudaEventRecord(evs[4], s);
   launch_node_update(e.prec, e.B, e.nparts, s);
   if (evs) cudaEventRecord(evs[5], s);
@@ -512,8 +493,10 @@ static susp_status device_status(susp* h) {
   return err_status(err);
 }
 
-// Rebuild the boundary links of this box from its current populations.
+// Rebuild the boundary links of this box from its current populations (the
+// stresslet sum they feed to the next finalisation starts again from zero).
 static void refresh_links(susp* h) {
+  cudaMemsetAsync(h->v.step_acc + 6, 0, 9 * sizeof(double), stream_of(h));
   launch_links(h->prec, h->eng.B, h->v.n, stream_of(h));
 }
 
@@ -572,7 +555,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.inv_nx_d = 1.0 / p->nx; v.inv_ny_d = 1.0 / p->ny; v.inv_nz_d = 1.0 / p->nz;
   v.inv_nx_f = (float)v.inv_nx_d; v.inv_ny_f = (float)v.inv_ny_d; v.inv_nz_f = (float)v.inv_nz_d;
   v.fa = w + L.fa; v.fb = w + L.fb;
-  v.visc_acc = (double*)(w + L.vacc);
+  v.step_acc = (double*)(w + L.vacc);
   v.owner = (int*)(w + L.owner);
   v.plane_mom = w + L.pm;
   v.n = n;
@@ -586,8 +569,6 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.Fh = (double*)(w + L.Fh); v.Th = (double*)(w + L.Th);
   v.Fcov = (double*)(w + L.Fcov); v.Tcov = (double*)(w + L.Tcov);
   v.Fp = (double*)(w + L.Fp); v.Tp = (double*)(w + L.Tp);
-  v.slet_part = (double*)(w + L.slet); v.cvir_part = (double*)(w + L.cvir);
-  v.rvir_part = (double*)(w + L.rvir); v.ncont_part = (int*)(w + L.ncont);
   v.ncx = L.ncx; v.ncy = L.ncy; v.ncz = L.ncz; v.brute = L.brute; v.ncells = L.ncells;
   v.csx = L.csx; v.csy = L.csy; v.csz = L.csz;
   v.inv_csx = 1.0 / L.csx; v.inv_csy = 1.0 / L.csy; v.inv_csz = 1.0 / L.csz;

@@ -235,8 +235,11 @@ __device__ __forceinline__ long long link_target_nr(const View& v, const Proto* 
 // nodes near the mapped surface into shared memory, then its threads take
 // (node, direction) work items, so every lane does the same work.
 constexpr int LINK_NODES_MAX = 2048;
+#ifndef LINK_UNROLL
+#define LINK_UNROLL 1
+#endif
 
-template <int P>
+template <int P, int UNR>
 __global__ void __launch_bounds__(256) k_links(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
@@ -282,50 +285,70 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   // sphere is one of its solid nodes (the node map holds every node closer
   // than a_map): no link, and no need to look it up
   const TC deep = am > (TC)0.05 ? (am - (TC)0.05) * (am - (TC)0.05) : (TC)0;
-  for (int t = threadIdx.x; t < items; t += blockDim.x) {
-    const uint32_t w = s_node[t / 18];
-    const int p = 1 + t % 18;
-    const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
-    const int ryn = y + D3Q19::cy(p);
-    if (ryn >= 0 && ryn < v.ny) {
-      TC ex = (TC)(x + D3Q19::cx(p)) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p)) - Rz;
-      le_image_v(v, ex, ey, ez, delta);
-      if (ex * ex + ey * ey + ez * ez < deep) continue;
-    }
-    int rx, ry, rz;
-    bool crossing;
-    const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);
-    const int ow = v.owner[r];
-    if (ow == i) continue;
-    const int q = D3Q19::opp(p);
-    const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
-    TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
-    const int k = le_image_v(v, dx, dy, dz, delta);
-    const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
-    const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
-    const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
-    const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
-    const TC wqq = wq<TC>(q);
-    // fluid receiver: momentum exchange and the bounce-back value for the
-    // next pull; another particle's node: fluid at rest
-    TC mag;
-    if (ow < 0) {
-      const TC nq = S::load(f, (long long)q * v.ncell + r, wqq * rho0, (TC)v.inv_scale);
-      const TC wall = (TC)6 * wqq * rho0 * cu;
-      mag = (TC)2 * nq - wall;
-      if (!crossing) {
-        const long long sidx = x + (long long)v.nx * (y + (long long)v.ny * z);
-        f[(long long)p * v.ncell + sidx] = S::enc(nq - wall, (TC)D3Q19::w(p) * rho0, (TC)v.scale);
+  // UNR items per thread and round; the receiver's owner word and its
+  // population q are loaded together (the population of a solid receiver is
+  // read and discarded), so an item waits for one memory latency
+  for (int t0 = threadIdx.x; t0 < items; t0 += UNR * blockDim.x) {
+    long long r[UNR], sidx[UNR];
+    int p[UNR], rxa[UNR], rya[UNR], rza[UNR], ow[UNR];
+    bool act[UNR], cross[UNR];
+    TC nq[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int t = t0 + u * blockDim.x;
+      act[u] = t < items;
+      p[u] = 1;
+      r[u] = 0; sidx[u] = 0; rxa[u] = rya[u] = rza[u] = 0; cross[u] = false;
+      if (!act[u]) continue;
+      const uint32_t w = s_node[t / 18];
+      p[u] = 1 + t % 18;
+      const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
+      const int ryn = y + D3Q19::cy(p[u]);
+      if (ryn >= 0 && ryn < v.ny) {
+        TC ex = (TC)(x + D3Q19::cx(p[u])) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p[u])) - Rz;
+        le_image_v(v, ex, ey, ez, delta);
+        if (ex * ex + ey * ey + ez * ez < deep) { act[u] = false; continue; }
       }
-    } else {
-      mag = (TC)2 * wqq * rho0;
+      r[u] = link_target_nr(v, pr, x, y, z, p[u], rxa[u], rya[u], rza[u], cross[u]);
+      sidx[u] = x + (long long)v.nx * (y + (long long)v.ny * z);
     }
-    const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
-    acc[0] += fx; acc[1] += fy; acc[2] += fz;
-    acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
-    acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
-    acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
-    acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int q = D3Q19::opp(p[u]);
+      ow[u] = act[u] ? v.owner[r[u]] : i;
+      nq[u] = act[u] ? S::load(f, (long long)q * v.ncell + r[u], wq<TC>(q) * rho0, (TC)v.inv_scale) : (TC)0;
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (!act[u] || ow[u] == i) continue;
+      const int q = D3Q19::opp(p[u]);
+      const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+      TC dx = (TC)rxa[u] + (TC)0.5 * cqx - Rx, dy = (TC)rya[u] + (TC)0.5 * cqy - Ry,
+         dz = (TC)rza[u] + (TC)0.5 * cqz - Rz;
+      const int k = le_image_v(v, dx, dy, dz, delta);
+      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+      const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+      const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+      const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
+      const TC wqq = wq<TC>(q);
+      // fluid receiver: momentum exchange and the bounce-back value for the
+      // next pull; another particle's node: fluid at rest
+      TC mag;
+      if (ow[u] < 0) {
+        const TC wall = (TC)6 * wqq * rho0 * cu;
+        mag = (TC)2 * nq[u] - wall;
+        if (!cross[u])
+          f[(long long)p[u] * v.ncell + sidx[u]] = S::enc(nq[u] - wall, (TC)D3Q19::w(p[u]) * rho0, (TC)v.scale);
+      } else {
+        mag = (TC)2 * wqq * rho0;
+      }
+      const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
+      acc[0] += fx; acc[1] += fy; acc[2] += fz;
+      acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
+      acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
+      acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
+      acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+    }
   }
   block_sum<TC, 15>(acc, red);
   if (threadIdx.x == 0) {
@@ -333,7 +356,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       v.Fh[3 * i + a] = (double)acc[a];
       v.Th[3 * i + a] = (double)acc[3 + a];
     }
-    for (int a = 0; a < 9; ++a) v.slet_part[9 * i + a] = (double)acc[6 + a];
+    for (int a = 0; a < 9; ++a) atomicAdd(v.step_acc + 6 + a, (double)acc[6 + a]);
   }
 }
 
@@ -378,10 +401,10 @@ void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s) {
 void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s) {
   if (nparts == 0) return;
   switch (prec) {
-    case 0: k_links<0><<<nparts, 256, 0, s>>>(B); break;
-    case 1: k_links<1><<<nparts, 256, 0, s>>>(B); break;
-    case 2: k_links<2><<<nparts, 256, 0, s>>>(B); break;
-    default: k_links<3><<<nparts, 256, 0, s>>>(B); break;
+    case 0: k_links<0, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
+    case 1: k_links<1, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
+    case 2: k_links<2, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
+    default: k_links<3, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
   }
 }
 

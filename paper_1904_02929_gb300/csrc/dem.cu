@@ -275,6 +275,7 @@ __device__ inline void write_plb(const View& v, int i, const double* R, const do
     pp[3 + c] = (TC)U[c];
     pp[6 + c] = (TC)W[c];
   }
+  pp[9] = (TC)v.rad[i];
 }
 
 // Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
@@ -342,6 +343,7 @@ __device__ inline SpringTable spring_table(const View& v, long long t) {
 // so no pair that interacts during the step is missed).  Entry c of the
 // particle's scratch row holds the partner index and the pair's tangential
 // spring, initialised from the spring table.  Returns the count (all lanes).
+template <typename T>
 __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -381,7 +383,44 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
     base += __popc(bal);
   };
   if (v.brute) {
-    for (int j0 = 0; j0 < v.n; j0 += 32) consider(j0 + lane, j0 + lane < v.n);
+    // every particle, from the compute-type copy (R, radius); a 0.01 margin
+    // covers its rounding, so the set still holds every interacting pair
+    const T* pl = reinterpret_cast<const T*>(v.plb);
+    const T px = pl[12 * i], py = pl[12 * i + 1], pz = pl[12 * i + 2], pa = pl[12 * i + 9];
+    const T dl = (T)delta, sk = (T)(skin + 0.01);
+    int rbase = 0;
+    for (int j0 = 0; j0 < v.n; j0 += 32) {
+      const int j = j0 + lane;
+      bool take = false;
+      if (j < v.n && j != i) {
+        T dx = pl[12 * j] - px, dy = pl[12 * j + 1] - py, dz = pl[12 * j + 2] - pz;
+        le_image_v<T>(v, dx, dy, dz, dl);
+        const T lim = pa + pl[12 * j + 9] + sk;
+        take = dx * dx + dy * dy + dz * dz < lim * lim;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, take);
+      if (take) {
+        const int c = rbase + __popc(bal & lt);
+        if (c < PAIR_SLOTS) pj[c] = j;
+      }
+      rbase += __popc(bal);
+    }
+    // springs of the candidates (lanes over the list)
+    const int m = rbase < PAIR_SLOTS ? rbase : PAIR_SLOTS;
+    __syncwarp();
+    for (int c = lane; c < m; c += 32) {
+      const int j = pj[c];
+      const int a = i < j ? i : j, b = i < j ? j : i;
+      double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+      const int mm = old.cnt[a];
+      for (int s = 0; s < mm; ++s)
+        if (old.part[a * v.K + s] == b) {
+          h0 = old.val[3 * (a * v.K + s)]; h1 = old.val[3 * (a * v.K + s) + 1]; h2 = old.val[3 * (a * v.K + s) + 2];
+          break;
+        }
+      ph[3 * c] = h0; ph[3 * c + 1] = h1; ph[3 * c + 2] = h2;
+    }
+    base = rbase;
   } else {
     // lane l < 27 owns neighbour cell l of i's cell at the step start; the
     // lanes walk their cells' entries in lockstep rounds
@@ -507,8 +546,11 @@ __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt,
   if (lane == 0) {
     integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8);
     if (sample) {
-      for (int c = 0; c < 9; ++c) { v.cvir_part[9 * i + c] = (double)cv[c]; v.rvir_part[9 * i + c] = (double)rv[c]; }
-      v.ncont_part[i] = ncont;
+      for (int c = 0; c < 9; ++c) {
+        atomicAdd(v.step_acc + 15 + c, (double)cv[c]);
+        if (v.F0 > 0.0) atomicAdd(v.step_acc + 25 + c, (double)rv[c]);
+      }
+      if (ncont) atomicAdd(v.step_acc + 24, (double)ncont);
     }
   }
   __syncwarp();
@@ -538,7 +580,7 @@ __global__ void __launch_bounds__(128) k_dem_step(Batch B) {
     const View& v = B.views[bx];
     if (!v.move) continue;
     const int i = g - B.part_off[bx];
-    const int np = collect_pairs(v, i, spring_table(v, v.proto->t));
+    const int np = collect_pairs<T>(v, i, spring_table(v, v.proto->t));
     if ((threadIdx.x & 31) == 0) v.pcnt[i] = np;
   }
   bool any_odd = false;

@@ -101,7 +101,8 @@ struct View {
   float inv_nx_f, inv_ny_f, inv_nz_f;
   void* fa;                     // population buffers; step t reads fa when t is even
   void* fb;
-  double* visc_acc;             // [6] viscous-stress sum of the current step
+  double* step_acc;             // [34] sums of the current step: 0-5 viscous (xx yy zz xy xz yz),
+                                //  6-14 stresslet, 15-23 contact virial, 24 contacts, 25-33 repulsive
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
   // particles
@@ -109,10 +110,8 @@ struct View {
   double *R, *U, *W, *rad, *amap, *mass, *inert, *inv_m, *inv_I;
   double *R2, *U2, *W2;           // second state buffer of the particle sub-steps
   int* pcx;                       // [n][8] cell of each particle at the step start (x, y, z, x of the rows across the planes)
-  void* plb;                    // [n][12] compute-type copy: R, U, W (and pad)
+  void* plb;                    // [n][12] compute-type copy: R, U, W, radius (and pad)
   double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
-  double *slet_part, *cvir_part, *rvir_part;   // [n][9]
-  int* ncont_part;              // [n]
   // cell list
   int ncx, ncy, ncz, brute;
   double csx, csy, csz, inv_csx, inv_csy, inv_csz;
@@ -140,6 +139,9 @@ struct View {
 // ERR_LINKS: a particle has more surface nodes than the link kernel stages.
 // Candidate partners per particle and lattice step (two per lane of a warp).
 constexpr int PAIR_SLOTS = 64;
+// Boxes with at most this many particles find candidates by scanning all
+// particles instead of through the cell list.
+constexpr int BRUTE_PAIRS_MAX = 4096;
 
 enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
 
