@@ -149,7 +149,8 @@ def batched_leg(ws, steps: int, warmup: int):
     """The 64-box sweep (edges 48-96, phi_3 0.45-0.58, mixed constant and
     oscillatory shear): BF16 deviation storage stepped as one batch (one
     launch sequence for all boxes, replayed as a CUDA graph) against the same
-    boxes in FP32 stepped one box per launch sequence, in turn on one stream.
+    boxes in FP32 stepped one box per launch sequence (plain launches, no
+    graph), in turn on one stream.
     Both run warmup + steps steps from rest with the stresses reset after the
     warm-up; the time-averaged shear stresses are compared box by box, and
     the smallest box against the FP64 oracle."""
@@ -184,7 +185,8 @@ def batched_leg(ws, steps: int, warmup: int):
     torch.cuda.synchronize()
     batch.profile(True)
     ms_b = timed(bs, lambda: batch.step(steps))
-    k1_ms, k1_n = batch.profile_read()
+    stages, k1_n = S.susp_batch_profile_stages(batch.b)
+    k1_ms = stages["collide_stream"]
     batch.profile(False)
     sb = [g.stress(S.TOTAL)[0][0, 1] for g in boxes]   # raises on any device error flag
     launches_b = 2 + 5 + 1 + 3                       # planes, collide, cell list + particles, finalize, node map + links
@@ -197,13 +199,15 @@ def batched_leg(ws, steps: int, warmup: int):
     ps = torch.cuda.Stream()
     plain = [S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, stream=ps, precision="fp32", **w.params)
              for w in ws]
+    for g in plain:
+        g.set_graphs(False)                         # plain launches, as a one-box code would issue them
     shears = [S.make_shear(**w.shear) for w in ws]
     for g, sh in zip(plain, shears):
         g.step(warmup, sh)
     for g in plain:
         g.stress_reset()
     for g, sh in zip(plain, shears):
-        g.step(1, sh)                               # graphs captured; one extra step like the batch
+        g.step(1, sh)                               # one extra step like the batch
     torch.cuda.synchronize()
 
     def run_plain():
@@ -233,10 +237,11 @@ def batched_leg(ws, steps: int, warmup: int):
         "value": mb, "unit": "MLUPS", "ms_per_step": ms_b / steps,
         "particle_steps_per_s": parts * steps / (ms_b / 1e3),
         "k_collide_stream_avg_ms": k1_ms / max(k1_n, 1),
+        "stage_us": {k: round(1e3 * v / max(k1_n, 1), 1) for k, v in stages.items()},
         "gpu_launches_per_step": launches_b, "workspace_bytes": mem_b,
         "l2": "not flushed: the boxes hold > 1.9 GB of populations, far above L2",
         "plain": {"storage": "fp32", "value": mp, "unit": "MLUPS", "ms_per_step": ms_p / steps,
-                  "launch": "one box per launch sequence (its own graph), boxes in turn on one stream"},
+                  "launch": "one box per launch sequence, no graph, boxes in turn on one stream"},
         "speedup_vs_plain": mb / mp,
         "stress_xy_rel_dev_vs_plain": {"max": max(dev), "median": float(np.median(dev))},
         "stress_xy_vs_oracle": {"box": w.name, "gpu_bf16": float(sb[k]), "oracle_f64": float(so),
@@ -244,24 +249,78 @@ def batched_leg(ws, steps: int, warmup: int):
     }
 
 
-def serving_leg(ws, duration: float = 5.0, rate: float = 20.0, steps: int = 1000,
-                budget: int = 2 << 30):
+def monolayer_leg(steps: int, warmup: int):
+    """Quasi-2D oscillatory shear at the paper's resolution: 512 x 512 x 28,
+    radii 5 / 7 (L_z = 4 a_max), phi = 0.70 (N = 1580), reduced amplitude
+    gamma0 = 0.1, FP16 deviation storage, FP32 compute: throughput and the
+    collide-stream roofline on a working set larger than L2 (no flush).  The
+    12-high variant with radii scaled to 3 / 2.14 is under-resolved (node
+    claims collide within tens of steps, in the oracle too)."""
+    import torch
+    from paper_1904_02929_gb300 import inputs
+    from paper_1904_02929_gb300 import susp as S
+    w = inputs.config_monolayer(seed=1003, phi=0.70, Lz=28, gamma0=0.1, precision="fp16")
+    g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp16", **w.params)
+    sh = S.make_shear(**w.shear)
+    g.step(warmup, sh)
+    nfluid = int((g.owner() < 0).sum())
+    S.susp_profile(g.h, True)
+    g.step(1, sh)
+    torch.cuda.synchronize()
+    S.susp_profile(g.h, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(g.stream):
+        a.record(g.stream)
+        g.step(steps, sh)
+        b.record(g.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    stages, n = S.susp_profile_stages(g.h)
+    S.susp_profile(g.h, False)
+    g.stress(S.TOTAL)                               # raises on any device error flag
+    info = g.info()
+    g.close()
+    k1 = stages["collide_stream"] / n
+    alg = 2 * 19 * 2 * nfluid
+    peak, kind = peak_hbm()
+    return {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "particles": w.n, "storage": "fp16",
+            "steps": steps, "value": w.ncell * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms / steps, "particle_steps_per_s": w.n * steps / (ms / 1e3),
+            "dem_substeps": info.dem_substeps,
+            "stage_us": {k: round(1e3 * v / n, 1) for k, v in stages.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_collide_stream<fp16>", "achieved": alg / (k1 / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
+                         "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+            "l2": "not flushed: 560 MB of populations per buffer, above L2"}
+
+
+def serving_leg(duration: float = 5.0, rate: float = 20.0, steps: int = 1000, budget: int = 4 << 30):
     """Poisson-arriving requests (rate per second, for ``duration`` seconds)
-    drawn from the sweep's boxes plus two quasi-2D 256 x 256 x 12 monolayers,
-    each ``steps`` lattice steps, served by continuous batching within an
-    HBM budget; latency percentiles and aggregate MLUPS."""
+    drawn 50 / 50 from quasi-2D 512 x 512 and 256 x 256 monolayers (phi
+    0.70 / 0.75 / 0.80) at the paper's resolution (radii 5 / 7, L_z = 28),
+    each ``steps`` lattice steps in FP16 deviation storage, served by
+    continuous batching within an HBM budget; latency percentiles and
+    aggregate MLUPS."""
     from paper_1904_02929_gb300 import inputs, serve
-    pool = list(ws)
-    for k, phi in enumerate((0.70, 0.80)):
-        m = inputs.config_monolayer(seed=3000 + k, phi=phi, Lx=256, Ly=256, Lz=12, precision="bf16")
-        pool.append(m)
-    reqs = serve.poisson_requests(pool, rate, duration, steps, seed=2024)
-    srv = serve.Server(budget, max_boxes=64, chunk=25, precision="bf16")
+    big = [inputs.config_monolayer(seed=3000 + k, phi=phi, Lz=28, precision="fp16")
+           for k, phi in enumerate((0.70, 0.75, 0.80))]
+    small = [inputs.config_monolayer(seed=3100 + k, phi=phi, Lx=256, Ly=256, Lz=28, precision="fp16")
+             for k, phi in enumerate((0.70, 0.75, 0.80))]
+    pool = big + small
+    # the reduced amplitudes of the protocol: at 512 lattice units of height
+    # the initial amplitude 1.0 would drive the Lees-Edwards image at 0.3 per
+    # step, far outside the lattice-Boltzmann Mach range
+    reqs = serve.poisson_requests(pool, rate, duration, steps, seed=1005, oscillatory_only=True,
+                                  amplitudes=(0.01, 0.1))
+    srv = serve.Server(budget, max_boxes=64, chunk=25, precision="fp16")
     srv.run(reqs)
     rep = srv.report()
     srv.close()
     rep.update({"arrival_rate_per_s": rate, "arrival_window_s": duration, "steps_per_request": steps,
-                "storage": "bf16", "pool": f"{len(ws)} sweep boxes (48-96 cubed) + 2 monolayers 256x256x12"})
+                "storage": "fp16",
+                "pool": "monolayers 512x512x28 and 256x256x28 (radii 5 / 7) at phi 0.70 / 0.75 / 0.80, drawn 50 / 50",
+                "protocol": "oscillatory, gamma0 in {0.01, 0.1}, omega 6e-4, theta in {0, pi/2}"})
     return rep
 
 
@@ -313,6 +372,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-monolayer", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -426,13 +486,13 @@ def main():
             "clocks": clk,
             "stress_xy_total": float(st[0][0, 1]),
         }
-        if world == 1 and not (args.no_batched and args.no_serve):
+        if world == 1 and not args.no_monolayer:
+            line["monolayer"] = monolayer_leg(args.batched_steps * 2, args.warmup)
+        if world == 1 and not args.no_batched:
             from paper_1904_02929_gb300 import inputs
-            sweep = inputs.batch_sweep()
-            if not args.no_batched:
-                line["batched"] = batched_leg(sweep, args.batched_steps, args.warmup)
-            if not args.no_serve:
-                line["serving"] = serving_leg(sweep)
+            line["batched"] = batched_leg(inputs.batch_sweep(), args.batched_steps, args.warmup)
+        if world == 1 and not args.no_serve:
+            line["serving"] = serving_leg()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line))

@@ -163,6 +163,16 @@ typedef struct {
 } susp_info;
 susp_status susp_get_info(susp *h, susp_info *info);
 
+/* Checkpoint and resume.  susp_save writes the box's whole state (device
+ * workspace plus the shear protocol in force) to host_buf; with host_buf NULL
+ * it only sets *bytes to the size needed.  susp_load restores a checkpoint
+ * into a handle created with the same parameters (lattice, particle count,
+ * precision; otherwise SUSP_EINVAL); stepping then continues exactly where
+ * the saved run was.  Both synchronise.  The format is this library's own
+ * (a header and the raw workspace, not portable across builds). */
+susp_status susp_save(susp *h, void *host_buf, size_t *bytes);
+susp_status susp_load(susp *h, const void *host_buf, size_t bytes);
+
 /* Instrumentation (no counterpart in the paper): when enabled, each step
  * records CUDA events on the handle's stream at its stage boundaries (at
  * most 4096 steps per window).  susp_profile_read synchronises and

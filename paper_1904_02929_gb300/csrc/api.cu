@@ -925,6 +925,75 @@ susp_status susp_get_info(susp* h, susp_info* info) {
   return SUSP_OK;
 }
 
+// ------------------------------------------------------------ checkpoints
+
+namespace {
+struct CkptHeader {
+  char magic[8];          // "SUSPCKP1"
+  uint64_t total;         // workspace bytes
+  int32_t nx, ny, nz, n, prec, have_shear;
+  susp_shear shear;
+};
+}  // namespace
+
+susp_status susp_save(susp* h, void* host_buf, size_t* bytes) {
+  if (!h || !bytes) return fail(SUSP_EINVAL, "NULL argument");
+  const size_t need = sizeof(CkptHeader) + h->L.total;
+  if (!host_buf) { *bytes = need; return SUSP_OK; }
+  if (*bytes < need) { *bytes = need; return fail(SUSP_ENOMEM, "checkpoint buffer too small"); }
+  susp_status st = device_status(h);
+  if (st) return st;
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, "SUSPCKP1", 8);
+  hd.total = h->L.total;
+  hd.nx = h->p.nx; hd.ny = h->p.ny; hd.nz = h->p.nz; hd.n = h->p.n; hd.prec = h->prec;
+  hd.have_shear = h->have_shear ? 1 : 0;
+  hd.shear = h->shear;
+  memcpy(host_buf, &hd, sizeof hd);
+  st = cuda_check(cudaMemcpy((char*)host_buf + sizeof hd, h->ws, h->L.total, cudaMemcpyDeviceToHost), "save");
+  if (st) return st;
+  *bytes = need;
+  return SUSP_OK;
+}
+
+susp_status susp_load(susp* h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return fail(SUSP_EINVAL, "NULL argument");
+  CkptHeader hd;
+  if (bytes < sizeof hd) return fail(SUSP_EINVAL, "checkpoint truncated");
+  memcpy(&hd, host_buf, sizeof hd);
+  if (memcmp(hd.magic, "SUSPCKP1", 8) != 0) return fail(SUSP_EINVAL, "not a checkpoint");
+  if (hd.total != h->L.total || hd.nx != h->p.nx || hd.ny != h->p.ny || hd.nz != h->p.nz || hd.n != h->p.n ||
+      hd.prec != h->prec)
+    return fail(SUSP_EINVAL, "checkpoint made for other parameters");
+  if (bytes < sizeof hd + hd.total) return fail(SUSP_EINVAL, "checkpoint truncated");
+  cudaStream_t s = stream_of(h);
+  susp_status st = cuda_check(cudaStreamSynchronize(s), "sync");
+  if (st) return st;
+  st = cuda_check(cudaMemcpy(h->ws, (const char*)host_buf + sizeof hd, hd.total, cudaMemcpyHostToDevice), "load");
+  if (st) return st;
+  // the one-box descriptor holds device addresses of this workspace
+  Engine& e = h->eng;
+  std::vector<int> tabs;
+  Engine tmp;
+  tmp.prec = h->prec;
+  eng_tables(tmp, std::vector<const View*>{&h->v}, tabs);
+  st = cuda_check(cudaMemcpy(h->ws + h->L.views, &h->v, sizeof(View), cudaMemcpyHostToDevice), "load view");
+  if (st) return st;
+  st = cuda_check(cudaMemcpy(h->ws + h->L.tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice), "load tables");
+  if (st) return st;
+  (void)e;
+  h->have_shear = hd.have_shear != 0;
+  h->shear = hd.shear;
+  if (h->p.n > 0) {
+    std::vector<double> r(h->p.n);
+    st = cuda_check(cudaMemcpy(r.data(), h->v.rad, 8 * r.size(), cudaMemcpyDeviceToHost), "load radii");
+    if (st) return st;
+    h->radius = r;
+  }
+  return device_status(h);
+}
+
 susp_status susp_profile(susp* h, int enable) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
   return eng_profile(h->eng, enable);

@@ -123,7 +123,9 @@ __device__ __forceinline__ void pull_one(const View& v, const typename Store<P>:
     return;
   }
   const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * v.nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
-  n[p] = S::load(fin + (size_t)p * (size_t)v.ncell, idx + off, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
+  // element index in 32 bits: 19 * ncell < 2^32 for every accepted box
+  const uint32_t e = (uint32_t)p * (uint32_t)v.ncell + (uint32_t)(idx + off);
+  n[p] = S::load(fin, e, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
 }
 
 template <int P, int p, bool BND>
@@ -157,50 +159,81 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   using S = Store<P>;
   const int nx = v.nx;
   const int idx = x + nx * (y + v.ny * z);
-  const size_t nc = (size_t)v.ncell;
+  const uint32_t nc = (uint32_t)v.ncell;   // 19 * ncell < 2^32 for every accepted box
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   if (v.owner[idx] >= 0) {
     // solid node: its populations are undefined; writing the rest state keeps
     // every stored sector complete (no read-for-ownership of partial sectors)
 #pragma unroll
     for (int q = 0; q < 19; ++q)
-      fout[q * nc + idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+      fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
     return;
   }
   const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
   const Proto* pr = v.proto;
   const TC* plb = reinterpret_cast<const TC*>(v.plb);
   TC n[19];
-  n[0] = S::load(fin, idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
+  n[0] = S::load(fin, (uint32_t)idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
   PullAll<P, 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
-  TC rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  // moments from the opposite pairs (q, q+1), q odd: sums s and differences d
+  TC sp[9], dp[9];
 #pragma unroll
-  for (int q = 0; q < 19; ++q) {
-    const TC cxq = (TC)D3Q19::cx(q), cyq = (TC)D3Q19::cy(q), czq = (TC)D3Q19::cz(q);
-    rho += n[q];
-    jx += n[q] * cxq; jy += n[q] * cyq; jz += n[q] * czq;
-    pxx += n[q] * cxq * cxq; pyy += n[q] * cyq * cyq; pzz += n[q] * czq * czq;
-    pxy += n[q] * cxq * cyq; pxz += n[q] * cxq * czq; pyz += n[q] * cyq * czq;
+  for (int k = 0; k < 9; ++k) { sp[k] = n[2 * k + 1] + n[2 * k + 2]; dp[k] = n[2 * k + 1] - n[2 * k + 2]; }
+  TC rho = n[0], jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int q = 2 * k + 1;
+    const int cxq = D3Q19::cx(q), cyq = D3Q19::cy(q), czq = D3Q19::cz(q);
+    rho += sp[k];
+    if (cxq) jx += cxq > 0 ? dp[k] : -dp[k];
+    if (cyq) jy += cyq > 0 ? dp[k] : -dp[k];
+    if (czq) jz += czq > 0 ? dp[k] : -dp[k];
+    if (cxq) pxx += sp[k];
+    if (cyq) pyy += sp[k];
+    if (czq) pzz += sp[k];
+    if (cxq && cyq) pxy += cxq * cyq > 0 ? sp[k] : -sp[k];
+    if (cxq && czq) pxz += cxq * czq > 0 ? sp[k] : -sp[k];
+    if (cyq && czq) pyz += cyq * czq > 0 ? sp[k] : -sp[k];
   }
   if (!(rho > (TC)0)) atomicOr(v.err, ERR_UNSTABLE);
   const TC inv = (TC)1 / rho;
   const TC omega = sel<TC>(v.omega_d, v.omega_f);
   const TC jj = jx * jx + jy * jy + jz * jz;
-  TC o[19];
-#pragma unroll
-  for (int q = 0; q < 19; ++q) {
-    const TC jc = jx * (TC)D3Q19::cx(q) + jy * (TC)D3Q19::cy(q) + jz * (TC)D3Q19::cz(q);
-    const TC fe = (TC)D3Q19::w(q) * (rho + (TC)3 * jc + (TC)4.5 * jc * jc * inv - (TC)1.5 * jj * inv);
-    o[q] = n[q] - omega * (n[q] - fe);
-  }
-  if (v.has_g) {
-    const TC gx = sel<TC>(v.g[0], v.g_f[0]), gy = sel<TC>(v.g[1], v.g_f[1]), gz = sel<TC>(v.g[2], v.g_f[2]);
-#pragma unroll
-    for (int q = 0; q < 19; ++q)
-      o[q] += (TC)3 * (TC)D3Q19::w(q) * (gx * (TC)D3Q19::cx(q) + gy * (TC)D3Q19::cy(q) + gz * (TC)D3Q19::cz(q));
+  // n^eq_q = C^q [rho + 3 j.c + 4.5 (j.c)^2 / rho - 1.5 j^2 / rho]; for an
+  // opposite pair the first, third and fourth terms are shared
+  const TC base = rho - (TC)1.5 * jj * inv;
+  const TC g0 = sel<TC>(v.g[0], v.g_f[0]), g1 = sel<TC>(v.g[1], v.g_f[1]), g2 = sel<TC>(v.g[2], v.g_f[2]);
+  const bool hg = v.has_g != 0;
+  {
+    const TC fe = (TC)D3Q19::w(0) * base;
+    const TC o = n[0] + omega * (fe - n[0]);
+    fout[idx] = S::enc(o, (TC)D3Q19::w(0) * rho0, (TC)v.scale);
   }
 #pragma unroll
-  for (int q = 0; q < 19; ++q) fout[q * nc + idx] = S::enc(o[q], (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+  for (int k = 0; k < 9; ++k) {
+    const int q = 2 * k + 1;
+    const int cxq = D3Q19::cx(q), cyq = D3Q19::cy(q), czq = D3Q19::cz(q);
+    TC jc = 0;
+    if (cxq) jc += cxq > 0 ? jx : -jx;
+    if (cyq) jc += cyq > 0 ? jy : -jy;
+    if (czq) jc += czq > 0 ? jz : -jz;
+    const TC w = (TC)D3Q19::w(q);
+    const TC sym = w * (base + (TC)4.5 * jc * jc * inv);
+    TC anti = (TC)3 * w * jc;
+    TC oq = n[q] + omega * (sym + anti - n[q]);
+    TC oo = n[q + 1] + omega * (sym - anti - n[q + 1]);
+    if (hg) {
+      TC gc = 0;
+      if (cxq) gc += cxq > 0 ? g0 : -g0;
+      if (cyq) gc += cyq > 0 ? g1 : -g1;
+      if (czq) gc += czq > 0 ? g2 : -g2;
+      const TC gq = (TC)3 * w * gc;
+      oq += gq;
+      oo -= gq;
+    }
+    fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc(oq, w * rho0, (TC)v.scale);
+    fout[(uint32_t)(q + 1) * nc + (uint32_t)idx] = S::enc(oo, w * rho0, (TC)v.scale);
+  }
   const TC vf = sel<TC>(v.vf_d, v.vf_f);
   const TC third = rho / (TC)3;
   acc[0] += vf * (pxx - jx * jx * inv - third);

@@ -37,25 +37,25 @@ struct D3Q19 {
 template <int P> struct Store;
 template <> struct Store<0> {
   using T = double; using C = double;
-  __device__ static C load(const T* f, long long i, C, C) { return f[i]; }
+  template <typename I> __device__ static C load(const T* f, I i, C, C) { return f[i]; }
   __device__ static T enc(C v, C, C) { return v; }
 };
 template <> struct Store<1> {
   using T = float; using C = float;
-  __device__ static C load(const T* f, long long i, C, C) { return __ldg(f + i); }
+  template <typename I> __device__ static C load(const T* f, I i, C, C) { return __ldg(f + i); }
   __device__ static T enc(C v, C, C) { return v; }
 };
 template <> struct Store<2> {
   using T = __half; using C = float;
   // value = base + stored / scale
-  __device__ static C load(const T* f, long long i, C base, C inv_scale) {
+  template <typename I> __device__ static C load(const T* f, I i, C base, C inv_scale) {
     return base + __half2float(f[i]) * inv_scale;
   }
   __device__ static T enc(C v, C base, C scale) { return __float2half_rn((v - base) * scale); }
 };
 template <> struct Store<3> {
   using T = __nv_bfloat16; using C = float;
-  __device__ static C load(const T* f, long long i, C base, C inv_scale) {
+  template <typename I> __device__ static C load(const T* f, I i, C base, C inv_scale) {
     return base + __bfloat162float(f[i]) * inv_scale;
   }
   __device__ static T enc(C v, C base, C scale) { return __float2bfloat16_rn((v - base) * scale); }

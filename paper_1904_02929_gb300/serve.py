@@ -204,12 +204,13 @@ class Server:
         self.batch.close()
 
 
-def poisson_requests(pool, rate: float, duration: float, steps: int, seed: int) -> list[Request]:
+def poisson_requests(pool, rate: float, duration: float, steps: int, seed: int,
+                     oscillatory_only: bool = False, amplitudes=(0.1, 1.0)) -> list[Request]:
     """Requests arriving as a Poisson process of the given rate over
     ``duration`` seconds, each a geometry drawn from ``pool`` (Workload
     objects) with a shear protocol drawn from the sweep's ranges: constant
-    rate 10^U(-5,-3), or oscillatory with amplitude {0.1, 1.0}, omega 6e-4
-    and phase {0, pi/2}."""
+    rate 10^U(-5,-3) (unless ``oscillatory_only``), or oscillatory (Eq. 16)
+    with an amplitude from ``amplitudes``, omega 6e-4 and phase {0, pi/2}."""
     rng = np.random.default_rng(seed)
     out, t, rid = [], 0.0, 0
     while True:
@@ -217,10 +218,10 @@ def poisson_requests(pool, rate: float, duration: float, steps: int, seed: int) 
         if t >= duration:
             break
         w = pool[int(rng.integers(len(pool)))]
-        if rng.random() < 0.5:
+        if not oscillatory_only and rng.random() < 0.5:
             sh = dict(kind=0, rate=float(10 ** rng.uniform(-5, -3)))
         else:
-            sh = dict(kind=1, gamma0=float(rng.choice([0.1, 1.0])), omega=6e-4,
+            sh = dict(kind=1, gamma0=float(rng.choice(list(amplitudes))), omega=6e-4,
                       theta=float(rng.choice([0.0, np.pi / 2])))
         out.append(Request(rid, w.nx, w.ny, w.nz, w.radius, w.pos, dict(w.params), sh, steps, t))
         rid += 1

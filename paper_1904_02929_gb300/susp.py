@@ -94,6 +94,10 @@ def library() -> C.CDLL:
         L.susp_profile.argtypes = [C.c_void_p, C.c_int]
         L.susp_profile_read.restype = C.c_int
         L.susp_profile_read.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+        L.susp_save.restype = C.c_int
+        L.susp_save.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]
+        L.susp_load.restype = C.c_int
+        L.susp_load.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
         L.susp_profile_stages.restype = C.c_int
         L.susp_profile_stages.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
         L.susp_batch_profile_stages.restype = C.c_int
@@ -227,6 +231,19 @@ def susp_profile_read(h):
     n = C.c_int(0)
     _check(library().susp_profile_read(h, C.byref(ms), C.byref(n)), "susp_profile_read")
     return float(ms.value), int(n.value)
+
+
+def susp_save(h) -> np.ndarray:
+    n = C.c_size_t(0)
+    _check(library().susp_save(h, None, C.byref(n)), "susp_save")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(library().susp_save(h, C.c_void_p(buf.ctypes.data), C.byref(n)), "susp_save")
+    return buf
+
+
+def susp_load(h, buf) -> None:
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(library().susp_load(h, C.c_void_p(buf.ctypes.data), buf.size), "susp_load")
 
 
 STAGES = ("plane_moments", "collide_stream", "particles", "finalize", "node_map", "links")
@@ -406,6 +423,12 @@ class Suspension:
 
     def info(self):
         return susp_get_info(self.h)
+
+    def save(self) -> np.ndarray:
+        return susp_save(self.h)
+
+    def load(self, buf):
+        susp_load(self.h, buf)
 
     def set_graphs(self, enable: bool):
         susp_set_graphs(self.h, enable)
