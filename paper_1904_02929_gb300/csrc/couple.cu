@@ -235,23 +235,22 @@ __device__ __forceinline__ long long link_target_nr(const View& v, const Proto* 
 // nodes near the mapped surface into shared memory, then its threads take
 // (node, direction) work items, so every lane does the same work.
 constexpr int LINK_NODES_MAX = 2048;
-#ifndef LINK_UNROLL
-#define LINK_UNROLL 1
-#endif
+constexpr int LINK_CHUNK = 4608;     // items screened per round (18 per thread of a 256-thread block)
 
-template <int P, int UNR>
+template <int P>
 __global__ void __launch_bounds__(256) k_links(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 15];
-  __shared__ int s_nodes;
+  __shared__ int s_nodes, s_items_n;
   __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
+  __shared__ uint32_t s_items[LINK_CHUNK];      // screened (node, direction) items of one chunk
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
   const int i = g - B.part_off[bx];
   typename Store<P>::T* __restrict__ f = static_cast<typename Store<P>::T*>(fin_of(v));
-  if (threadIdx.x == 0) s_nodes = 0;
+  if (threadIdx.x == 0) { s_nodes = 0; s_items_n = 0; }
   __syncthreads();
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
@@ -283,50 +282,55 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   const int items = nn * 18;
   // a receiver deeper than a_map - 0.05 inside this particle's own mapped
   // sphere is one of its solid nodes (the node map holds every node closer
-  // than a_map): no link, and no need to look it up
+  // than a_map): no link, and no need to look it up.  Items are screened in
+  // chunks; the survivors are compacted into shared memory so that full
+  // warps then process only candidate links (one memory round trip each).
   const TC deep = am > (TC)0.05 ? (am - (TC)0.05) * (am - (TC)0.05) : (TC)0;
-  // UNR items per thread and round; the receiver's owner word and its
-  // population q are loaded together (the population of a solid receiver is
-  // read and discarded), so an item waits for one memory latency
-  for (int t0 = threadIdx.x; t0 < items; t0 += UNR * blockDim.x) {
-    long long r[UNR], sidx[UNR];
-    int p[UNR], rxa[UNR], rya[UNR], rza[UNR], ow[UNR];
-    bool act[UNR], cross[UNR];
-    TC nq[UNR];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int t = t0 + u * blockDim.x;
-      act[u] = t < items;
-      p[u] = 1;
-      r[u] = 0; sidx[u] = 0; rxa[u] = rya[u] = rza[u] = 0; cross[u] = false;
-      if (!act[u]) continue;
-      const uint32_t w = s_node[t / 18];
-      p[u] = 1 + t % 18;
-      const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
-      const int ryn = y + D3Q19::cy(p[u]);
-      if (ryn >= 0 && ryn < v.ny) {
-        TC ex = (TC)(x + D3Q19::cx(p[u])) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p[u])) - Rz;
-        le_image_v(v, ex, ey, ez, delta);
-        if (ex * ex + ey * ey + ez * ez < deep) { act[u] = false; continue; }
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < items; base += LINK_CHUNK) {
+    const int end = min(items, base + LINK_CHUNK);
+    // screen: item t = (node t / 18, direction 1 + t % 18)
+    for (int t0 = base; t0 < end; t0 += blockDim.x) {
+      const int t = t0 + (int)threadIdx.x;
+      bool keep = false;
+      if (t < end) {
+        const uint32_t w = s_node[t / 18];
+        const int p = 1 + t % 18;
+        const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
+        const int ryn = y + D3Q19::cy(p);
+        keep = true;
+        if (ryn >= 0 && ryn < v.ny) {
+          TC ex = (TC)(x + D3Q19::cx(p)) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p)) - Rz;
+          le_image_v(v, ex, ey, ez, delta);
+          keep = !(ex * ex + ey * ey + ez * ez < deep);
+        }
       }
-      r[u] = link_target_nr(v, pr, x, y, z, p[u], rxa[u], rya[u], rza[u], cross[u]);
-      sidx[u] = x + (long long)v.nx * (y + (long long)v.ny * z);
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      int wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(&s_items_n, __popc(bal));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep) s_items[wbase + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)t;
     }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const int q = D3Q19::opp(p[u]);
-      ow[u] = act[u] ? v.owner[r[u]] : i;
-      nq[u] = act[u] ? S::load(f, (long long)q * v.ncell + r[u], wq<TC>(q) * rho0, (TC)v.inv_scale) : (TC)0;
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      if (!act[u] || ow[u] == i) continue;
-      const int q = D3Q19::opp(p[u]);
+    __syncthreads();
+    const int ns = s_items_n;
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      const int t = (int)s_items[k];
+      const uint32_t w = s_node[t / 18];
+      const int p = 1 + t % 18;
+      const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
+      int rx, ry, rz;
+      bool crossing;
+      const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);
+      const int q = D3Q19::opp(p);
+      // the receiver's owner word and its population q are loaded together
+      // (the population of a solid receiver is read and discarded)
+      const int ow = v.owner[r];
+      const TC nq = S::load(f, (long long)q * v.ncell + r, wq<TC>(q) * rho0, (TC)v.inv_scale);
+      if (ow == i) continue;
       const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
-      TC dx = (TC)rxa[u] + (TC)0.5 * cqx - Rx, dy = (TC)rya[u] + (TC)0.5 * cqy - Ry,
-         dz = (TC)rza[u] + (TC)0.5 * cqz - Rz;
-      const int k = le_image_v(v, dx, dy, dz, delta);
-      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
+      TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
+      const int kimg = le_image_v(v, dx, dy, dz, delta);
+      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)kimg * ule;
       const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
       const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
       const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
@@ -334,11 +338,13 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       // fluid receiver: momentum exchange and the bounce-back value for the
       // next pull; another particle's node: fluid at rest
       TC mag;
-      if (ow[u] < 0) {
+      if (ow < 0) {
         const TC wall = (TC)6 * wqq * rho0 * cu;
-        mag = (TC)2 * nq[u] - wall;
-        if (!cross[u])
-          f[(long long)p[u] * v.ncell + sidx[u]] = S::enc(nq[u] - wall, (TC)D3Q19::w(p[u]) * rho0, (TC)v.scale);
+        mag = (TC)2 * nq - wall;
+        if (!crossing) {
+          const long long sidx = x + (long long)v.nx * (y + (long long)v.ny * z);
+          f[(long long)p * v.ncell + sidx] = S::enc(nq - wall, (TC)D3Q19::w(p) * rho0, (TC)v.scale);
+        }
       } else {
         mag = (TC)2 * wqq * rho0;
       }
@@ -349,6 +355,9 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
       acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s_items_n = 0;
+    __syncthreads();
   }
   block_sum<TC, 15>(acc, red);
   if (threadIdx.x == 0) {
@@ -401,10 +410,10 @@ void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s) {
 void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s) {
   if (nparts == 0) return;
   switch (prec) {
-    case 0: k_links<0, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
-    case 1: k_links<1, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
-    case 2: k_links<2, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
-    default: k_links<3, LINK_UNROLL><<<nparts, 256, 0, s>>>(B); break;
+    case 0: k_links<0><<<nparts, 256, 0, s>>>(B); break;
+    case 1: k_links<1><<<nparts, 256, 0, s>>>(B); break;
+    case 2: k_links<2><<<nparts, 256, 0, s>>>(B); break;
+    default: k_links<3><<<nparts, 256, 0, s>>>(B); break;
   }
 }
 
