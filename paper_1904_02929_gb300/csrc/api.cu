@@ -37,7 +37,7 @@ susp_status fail(susp_status st, const std::string& msg) {
   return st;
 }
 
-const int HSLOTS = 16;        // tangential springs per particle (partners with larger index)
+const int HSLOTS = HSLOTS_DEV;   // tangential springs per particle (partners with larger index)
 const double KPI = 3.14159265358979323846;
 
 size_t esize(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }

@@ -389,21 +389,36 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
     const T px = pl[12 * i], py = pl[12 * i + 1], pz = pl[12 * i + 2], pa = pl[12 * i + 9];
     const T dl = (T)delta, sk = (T)(skin + 0.01);
     int rbase = 0;
-    for (int j0 = 0; j0 < v.n; j0 += 32) {
-      const int j = j0 + lane;
-      bool take = false;
-      if (j < v.n && j != i) {
-        T dx = pl[12 * j] - px, dy = pl[12 * j + 1] - py, dz = pl[12 * j + 2] - pz;
-        le_image_v<T>(v, dx, dy, dz, dl);
-        const T lim = pa + pl[12 * j + 9] + sk;
-        take = dx * dx + dy * dy + dz * dz < lim * lim;
+    // 8 candidates per lane and round: their loads are issued together
+    constexpr int CU = 8;
+    for (int j0 = 0; j0 < v.n; j0 += 32 * CU) {
+      T cx[CU], cy[CU], cz[CU], cr[CU];
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int j = j0 + 32 * u + lane;
+        const bool ok = j < v.n;
+        cx[u] = ok ? pl[12 * j] : (T)0;
+        cy[u] = ok ? pl[12 * j + 1] : (T)0;
+        cz[u] = ok ? pl[12 * j + 2] : (T)0;
+        cr[u] = ok ? pl[12 * j + 9] : (T)0;
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, take);
-      if (take) {
-        const int c = rbase + __popc(bal & lt);
-        if (c < PAIR_SLOTS) pj[c] = j;
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int j = j0 + 32 * u + lane;
+        bool take = false;
+        if (j < v.n && j != i) {
+          T dx = cx[u] - px, dy = cy[u] - py, dz = cz[u] - pz;
+          le_image_v<T>(v, dx, dy, dz, dl);
+          const T lim = pa + cr[u] + sk;
+          take = dx * dx + dy * dy + dz * dz < lim * lim;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (take) {
+          const int c = rbase + __popc(bal & lt);
+          if (c < PAIR_SLOTS) pj[c] = j;
+        }
+        rbase += __popc(bal);
       }
-      rbase += __popc(bal);
     }
     // springs of the candidates (lanes over the list)
     const int m = rbase < PAIR_SLOTS ? rbase : PAIR_SLOTS;
@@ -411,13 +426,19 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
     for (int c = lane; c < m; c += 32) {
       const int j = pj[c];
       const int a = i < j ? i : j, b = i < j ? j : i;
-      double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+      // all slots of a's row at once (the table has HSLOTS_DEV slots per particle)
       const int mm = old.cnt[a];
-      for (int s = 0; s < mm; ++s)
-        if (old.part[a * v.K + s] == b) {
-          h0 = old.val[3 * (a * v.K + s)]; h1 = old.val[3 * (a * v.K + s) + 1]; h2 = old.val[3 * (a * v.K + s) + 2];
-          break;
-        }
+      int hit = -1;
+#pragma unroll
+      for (int s = 0; s < HSLOTS_DEV; ++s) {
+        const int pb = old.part[a * HSLOTS_DEV + s];
+        if (s < mm && pb == b && hit < 0) hit = s;
+      }
+      double h0 = 0.0, h1 = 0.0, h2 = 0.0;
+      if (hit >= 0) {
+        const double* hv = old.val + 3 * (a * HSLOTS_DEV + hit);
+        h0 = hv[0]; h1 = hv[1]; h2 = hv[2];
+      }
       ph[3 * c] = h0; ph[3 * c + 1] = h1; ph[3 * c + 2] = h2;
     }
     base = rbase;

@@ -147,6 +147,10 @@ struct PullAll<P, 19, BND> {
                                              int, int, typename Store<P>::C, typename Store<P>::C (&)[19]) {}
 };
 
+template <int P>
+__device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* __restrict__ fout, int idx,
+                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6]);
+
 // One lattice node: pull (Eq. 3; bounce-back values sit in the solid
 // sources' slots) with the Lees-Edwards planes, BGK collision (Eq. 4, 5),
 // store, viscous-stress accumulation.  BND: the node lies on a Lees-Edwards
@@ -175,6 +179,18 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   TC n[19];
   n[0] = S::load(fin, (uint32_t)idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
   PullAll<P, 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
+  lb_collide<P>(v, fout, idx, n, acc);
+}
+
+// BGK collision (Eq. 4, 5) of one fluid node from its pulled populations n,
+// optional body force, store, viscous-stress accumulation.
+template <int P>
+__device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* __restrict__ fout, int idx,
+                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6]) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  const uint32_t nc = (uint32_t)v.ncell;
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   // moments from the opposite pairs (q, q+1), q odd: sums s and differences d
   TC sp[9], dp[9];
 #pragma unroll
@@ -244,15 +260,113 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   acc[5] += vf * (pyz - jy * jz * inv);
 }
 
+// ---------------------------------------------------------------------------
+// Staged pulls (FP32 storage).  Each lane copies, one row ahead, the source
+// populations of its node and its owner word from global into shared memory
+// with cp.async, and computes the current row from the previous stage while
+// the next row's copies are in flight.  A lane only ever reads the slots it
+// filled, so no barrier is needed.  Pulls across a Lees-Edwards plane keep
+// their direct path.  (For 16-bit storage the extra registers of the staging
+// cost more occupancy than the overlap gains; those types pull directly.)
+// ---------------------------------------------------------------------------
+constexpr int STAGE_WORDS = 20;   // 19 populations + owner word
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Issue the copies of node (y, idx) into the stage words at sbase (word q at
+// sbase + 128 q bytes, owner word at word 19).
+template <int P, bool BND>
+__device__ __forceinline__ void stage_issue(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                            uint32_t sbase, int y, int idx, int dxm, int dxp, int dzm, int dzp) {
+  using T = typename Store<P>::T;
+  const uint32_t nc = (uint32_t)v.ncell;
+  const int nx = v.nx;
+  const char* fb = reinterpret_cast<const char*>(fin);
+#pragma unroll
+  for (int p = 0; p < 19; ++p) {
+    const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+    if (BND && cpy != 0) {
+      const int sy = y - cpy;
+      if (sy < 0 || sy >= v.ny) continue;   // crossing pull: read directly by le_pull
+    }
+    const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
+    const uint32_t e = (uint32_t)p * nc + (uint32_t)(idx + off);
+    const size_t byte = ((size_t)e * sizeof(T)) & ~(size_t)3;
+    cp_async4(sbase + 128u * (uint32_t)p, fb + byte);
+  }
+  cp_async4(sbase + 128u * 19u, v.owner + idx);
+}
+
+template <int P, int p, bool BND>
+struct StagedAll {
+  __device__ __forceinline__ static void run(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                             const typename Store<P>::C* __restrict__ plb,
+                                             const Proto* __restrict__ pr, int x, int y, int z, int idx,
+                                             int dxm, int dxp, int dzm, int dzp, typename Store<P>::C rho0,
+                                             const uint32_t* sw, typename Store<P>::C (&n)[19]) {
+    using TC = typename Store<P>::C;
+    constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+    const int sy = y - cpy;
+    if (BND && cpy != 0 && (sy < 0 || sy >= v.ny)) {
+      n[p] = le_pull<P, p>(v, fin, plb, pr, x, y, z, idx);
+    } else {
+      const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * v.nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
+      const uint32_t e = (uint32_t)p * (uint32_t)v.ncell + (uint32_t)(idx + off);
+      n[p] = Store<P>::from_word(sw[32 * p], e, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
+    }
+    StagedAll<P, p + 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, sw, n);
+  }
+};
+template <int P, bool BND>
+struct StagedAll<P, 19, BND> {
+  __device__ __forceinline__ static void run(const View&, const typename Store<P>::T* __restrict__,
+                                             const typename Store<P>::C* __restrict__, const Proto* __restrict__,
+                                             int, int, int, int, int, int, int, int, typename Store<P>::C,
+                                             const uint32_t*, typename Store<P>::C (&)[19]) {}
+};
+
+// One lattice node from its staged words (sw: word 0 of this lane).
+template <int P, bool BND>
+__device__ __forceinline__ void lb_node_staged(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                               typename Store<P>::T* __restrict__ fout, int x, int y, int z,
+                                               int dzm, int dzp, typename Store<P>::C (&acc)[6],
+                                               const uint32_t* sw) {
+  using TC = typename Store<P>::C;
+  using S = Store<P>;
+  const int nx = v.nx;
+  const int idx = x + nx * (y + v.ny * z);
+  const uint32_t nc = (uint32_t)v.ncell;
+  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  if ((int)sw[32 * 19] >= 0) {
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
+    return;
+  }
+  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
+  TC n[19];
+  StagedAll<P, 0, BND>::run(v, fin, reinterpret_cast<const TC*>(v.plb), v.proto, x, y, z, idx, dxm, dxp, dzm, dzp,
+                            rho0, sw, n);
+  lb_collide<P>(v, fout, idx, n, acc);
+}
+
 // Persistent grid over the 32 (x) by 8 (y) tiles of every box (z slowest
-// within a box); each block takes a contiguous range of tiles, sums its nodes'
-// viscous stress per box and adds it to the box's accumulator when its range
-// leaves the box.
+// within a box); each block takes a contiguous range of tiles (warp w takes
+// row w of each tile), sums its nodes' viscous stress per box and adds it to
+// the box's accumulator when its range leaves the box.
 template <int P>
 __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   using TC = typename Store<P>::C;
   using T = typename Store<P>::T;
   __shared__ TC red[32 * 6];
+  __shared__ uint32_t stage[P == 1 ? 8 : 1][2][STAGE_WORDS][32];   // [warp][stage][word][lane]
   const int total = B.tile_off[B.nbox];
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
@@ -268,18 +382,63 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
     const int tiles_per_plane = ntx * nty;
     const int nxny = v.nx * v.ny;
     TC acc[6] = {0, 0, 0, 0, 0, 0};
-    for (; t < te; ++t) {
-      const int lt = t - base;
-      const int z = lt / tiles_per_plane;
-      const int r = lt - z * tiles_per_plane;
-      const int ty = r / ntx, tx = r - ty * ntx;
-      const int x = tx * 32 + lx, y = ty * 8 + ly;
-      const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
-      if (x < v.nx && y < v.ny) {
-        // a warp covers one x row, so this branch is warp-uniform
-        if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc);
-        else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc);
+    if constexpr (P != 1) {
+      for (; t < te; ++t) {
+        const int lt = t - base;
+        const int z = lt / tiles_per_plane;
+        const int r = lt - z * tiles_per_plane;
+        const int ty = r / ntx, tx = r - ty * ntx;
+        const int x = tx * 32 + lx, y = ty * 8 + ly;
+        const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
+        if (x < v.nx && y < v.ny) {
+          // a warp covers one x row, so this branch is warp-uniform
+          if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc);
+          else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc);
+        }
       }
+    } else {
+      const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(&stage[ly][0][0][lx]);
+      const uint32_t sstride = STAGE_WORDS * 32 * 4;
+      // copies of this warp's row of tile tt into stage s (nothing for rows
+      // outside the box; one copy group per call in every case)
+      auto issue = [&](int tt, int s) {
+        const int lt = tt - base;
+        const int z = lt / tiles_per_plane;
+        const int r = lt - z * tiles_per_plane;
+        const int ty = r / ntx, tx = r - ty * ntx;
+        const int x = tx * 32 + lx, y = ty * 8 + ly;
+        if (x < v.nx && y < v.ny) {
+          const int idx = x + v.nx * (y + v.ny * z);
+          const int dxm = x == 0 ? v.nx - 1 : -1, dxp = x == v.nx - 1 ? 1 - v.nx : 1;
+          const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
+          const uint32_t sb = sb0 + sstride * (uint32_t)s;
+          if (y == 0 || y == v.ny - 1) stage_issue<P, true>(v, fin, sb, y, idx, dxm, dxp, dzm, dzp);
+          else stage_issue<P, false>(v, fin, sb, y, idx, dxm, dxp, dzm, dzp);
+        }
+        cp_async_commit();
+      };
+      const int nrows = te - t;
+      issue(t, 0);
+      for (int k = 0; k < nrows; ++k) {
+        if (k + 1 < nrows) {
+          issue(t + k + 1, (k + 1) & 1);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        const int lt = t + k - base;
+        const int z = lt / tiles_per_plane;
+        const int r = lt - z * tiles_per_plane;
+        const int ty = r / ntx, tx = r - ty * ntx;
+        const int x = tx * 32 + lx, y = ty * 8 + ly;
+        const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
+        if (x < v.nx && y < v.ny) {
+          const uint32_t* sw = &stage[ly][k & 1][0][lx];
+          if (y == 0 || y == v.ny - 1) lb_node_staged<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
+          else lb_node_staged<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
+        }
+      }
+      t = te;
     }
     block_sum<TC, 6>(acc, red);
     if (threadIdx.x == 0)

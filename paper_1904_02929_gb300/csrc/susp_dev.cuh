@@ -44,6 +44,8 @@ template <> struct Store<1> {
   using T = float; using C = float;
   template <typename I> __device__ static C load(const T* f, I i, C, C) { return __ldg(f + i); }
   __device__ static T enc(C v, C, C) { return v; }
+  // value of element e from the aligned 32-bit word that holds it
+  __device__ static C from_word(uint32_t w, uint32_t, C, C) { return __uint_as_float(w); }
 };
 template <> struct Store<2> {
   using T = __half; using C = float;
@@ -139,6 +141,8 @@ struct View {
 // ERR_LINKS: a particle has more surface nodes than the link kernel stages.
 // Candidate partners per particle and lattice step (two per lane of a warp).
 constexpr int PAIR_SLOTS = 64;
+// Tangential springs per particle in the step tables (partners with larger index).
+constexpr int HSLOTS_DEV = 16;
 // Boxes with at most this many particles find candidates by scanning all
 // particles instead of through the cell list.
 constexpr int BRUTE_PAIRS_MAX = 4096;
