@@ -358,20 +358,23 @@ __device__ __forceinline__ void lb_node_staged(const View& v, const typename Sto
 }
 
 // Persistent grid over the 32 (x) by 8 (y) tiles of every box (z slowest
-// within a box); each block takes a contiguous range of tiles (warp w takes
-// row w of each tile), sums its nodes' viscous stress per box and adds it to
-// the box's accumulator when its range leaves the box.
+// within a box); each block takes a contiguous range of tiles, sums its nodes'
+// viscous stress per box and adds it to the box's accumulator when its range
+// leaves the box.  Within a block the warps claim the 32-node rows of the
+// range one at a time from a shared counter, so a warp that draws the costly
+// Lees-Edwards plane rows does not hold the others at the block's barrier.
 template <int P>
 __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   using TC = typename Store<P>::C;
   using T = typename Store<P>::T;
   __shared__ TC red[32 * 6];
   __shared__ uint32_t stage[P == 1 ? 8 : 1][2][STAGE_WORDS][32];   // [warp][stage][word][lane]
+  __shared__ int s_next;
   const int total = B.tile_off[B.nbox];
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
   if (t0 >= t1) return;
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int lx = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int b = box_of(B.tile_off, B.nbox, t0);
   for (int t = t0; t < t1; ++b) {
     const View& v = B.views[b];
@@ -381,14 +384,29 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
     const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
     const int tiles_per_plane = ntx * nty;
     const int nxny = v.nx * v.ny;
+    const int rows = 8 * (te - t);   // rows of this block's range in this box
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    auto claim = [&]() {
+      int r = 0;
+      if (lx == 0) r = atomicAdd(&s_next, 1);
+      return __shfl_sync(0xffffffffu, r, 0);
+    };
+    // row k of the range: tile t + k / 8, row k % 8 of the tile
+    auto decode = [&](int k, int& x, int& y, int& z) {
+      const int lt = t + (k >> 3) - base;
+      z = lt / tiles_per_plane;
+      const int r = lt - z * tiles_per_plane;
+      const int ty = r / ntx, tx = r - ty * ntx;
+      x = tx * 32 + lx;
+      y = ty * 8 + (k & 7);
+    };
     TC acc[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (P != 1) {
-      for (; t < te; ++t) {
-        const int lt = t - base;
-        const int z = lt / tiles_per_plane;
-        const int r = lt - z * tiles_per_plane;
-        const int ty = r / ntx, tx = r - ty * ntx;
-        const int x = tx * 32 + lx, y = ty * 8 + ly;
+      for (int k = claim(); k < rows; k = claim()) {
+        int x, y, z;
+        decode(k, x, y, z);
         const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
         if (x < v.nx && y < v.ny) {
           // a warp covers one x row, so this branch is warp-uniform
@@ -397,16 +415,13 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
         }
       }
     } else {
-      const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(&stage[ly][0][0][lx]);
+      const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(&stage[wid][0][0][lx]);
       const uint32_t sstride = STAGE_WORDS * 32 * 4;
-      // copies of this warp's row of tile tt into stage s (nothing for rows
-      // outside the box; one copy group per call in every case)
-      auto issue = [&](int tt, int s) {
-        const int lt = tt - base;
-        const int z = lt / tiles_per_plane;
-        const int r = lt - z * tiles_per_plane;
-        const int ty = r / ntx, tx = r - ty * ntx;
-        const int x = tx * 32 + lx, y = ty * 8 + ly;
+      // copies of row k into stage s (nothing for rows outside the box; one
+      // copy group per call in every case)
+      auto issue = [&](int k, int s) {
+        int x, y, z;
+        decode(k, x, y, z);
         if (x < v.nx && y < v.ny) {
           const int idx = x + v.nx * (y + v.ny * z);
           const int dxm = x == 0 ? v.nx - 1 : -1, dxp = x == v.nx - 1 ? 1 - v.nx : 1;
@@ -417,29 +432,28 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
         }
         cp_async_commit();
       };
-      const int nrows = te - t;
-      issue(t, 0);
-      for (int k = 0; k < nrows; ++k) {
-        if (k + 1 < nrows) {
-          issue(t + k + 1, (k + 1) & 1);
+      int cur = claim();
+      if (cur < rows) issue(cur, 0);
+      for (int it = 0; cur < rows; ++it) {
+        const int nxt = claim();
+        if (nxt < rows) {
+          issue(nxt, (it + 1) & 1);
           cp_async_wait<1>();
         } else {
           cp_async_wait<0>();
         }
-        const int lt = t + k - base;
-        const int z = lt / tiles_per_plane;
-        const int r = lt - z * tiles_per_plane;
-        const int ty = r / ntx, tx = r - ty * ntx;
-        const int x = tx * 32 + lx, y = ty * 8 + ly;
+        int x, y, z;
+        decode(cur, x, y, z);
         const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
         if (x < v.nx && y < v.ny) {
-          const uint32_t* sw = &stage[ly][k & 1][0][lx];
+          const uint32_t* sw = &stage[wid][it & 1][0][lx];
           if (y == 0 || y == v.ny - 1) lb_node_staged<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
           else lb_node_staged<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
         }
+        cur = nxt;
       }
-      t = te;
     }
+    t = te;
     block_sum<TC, 6>(acc, red);
     if (threadIdx.x == 0)
 #pragma unroll
