@@ -588,12 +588,17 @@ __device__ inline void write_plb(const View& v, int i) {
 // integrates the particle into the other buffer, so one grid-wide barrier per
 // sub-step suffices; boxes with fewer sub-steps idle in the later rounds.  The
 // final state ends in the canonical buffer (R, U, W).
+// Warps (particles in flight) per block of the cooperative particle kernel.
+#ifndef DEM_WARPS
+#define DEM_WARPS 4
+#endif
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_dem_step(Batch B) {
+__global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int wib = threadIdx.x >> 5;
-  const int gwarp = blockIdx.x * 4 + wib, nwarps = gridDim.x * 4;
+  const int gwarp = blockIdx.x * DEM_WARPS + wib, nwarps = gridDim.x * DEM_WARPS;
   const int ntot = B.part_off[B.nbox];
   // candidate partners of every moving particle at the step start
   for (int g = gwarp; g < ntot; g += nwarps) {
@@ -665,11 +670,11 @@ int dem_grid_blocks(int plb_double, int n) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (plb_double) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<double>, 128, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<float>, 128, 0);
+  if (plb_double) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<double>, 32 * DEM_WARPS, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<float>, 32 * DEM_WARPS, 0);
   if (per < 1) per = 1;
   if (sms < 1) sms = 1;
-  const int want = (n + 3) / 4;
+  const int want = (n + DEM_WARPS - 1) / DEM_WARPS;
   const int cap = sms * per;
   return want < cap ? (want > 0 ? want : 1) : cap;
 }
@@ -690,6 +695,6 @@ cudaError_t launch_dem_step(const Batch& B, int nparts, int ncells, int plb_doub
   Batch bb = B;
   void* args[] = {&bb};
   if (plb_double)
-    return cudaLaunchCooperativeKernel((const void*)k_dem_step<double>, dim3(grid), dim3(128), args, 0, s);
-  return cudaLaunchCooperativeKernel((const void*)k_dem_step<float>, dim3(grid), dim3(128), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)k_dem_step<double>, dim3(grid), dim3(32 * DEM_WARPS), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_dem_step<float>, dim3(grid), dim3(32 * DEM_WARPS), args, 0, s);
 }
