@@ -32,17 +32,21 @@
 
 namespace susp_dev {
 
+// Bounding box of one Lees-Edwards image of a particle: first node, extents,
+// node count, and the image centre (x brought into [0, nx)).
+template <typename TC>
 struct ImgBox {
   int x0, y0, z0, ex, ey, ez, cnt;
+  TC cx, cy, cz;
 };
 
 template <typename TC>
 __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delta, TC reach,
-                                     ImgBox (&b)[3]) {
+                                     ImgBox<TC> (&b)[3]) {
   int total = 0;
 #pragma unroll
   for (int k = -1; k <= 1; ++k) {
-    ImgBox& B = b[k + 1];
+    ImgBox<TC>& B = b[k + 1];
     // image centre, x brought back into [0, nx): Rx + k delta can lie up to one
     // period outside (0 <= delta < nx), and the cell visit wraps x only once
     TC cx = Rx + (TC)k * delta;
@@ -55,6 +59,7 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
     const int z0 = (int)ceil(cz - reach), z1 = (int)floor(cz + reach);
     B.x0 = x0; B.y0 = y0; B.z0 = z0;
     B.ex = x1 - x0 + 1; B.ey = y1 - y0 + 1; B.ez = z1 - z0 + 1;
+    B.cx = cx; B.cy = cy; B.cz = cz;
     B.cnt = (y0 > y1) ? 0 : B.ex * B.ey * B.ez;
     total += B.cnt;
   }
@@ -63,24 +68,29 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
 
 // Visit the cells of a particle's image boxes: half-warps take (y, z) rows and
 // their 16 lanes run along x (coalesced).  Box corners lie less than one period
-// outside the lattice (reach < L / 2, centres in [0, L)), so one wrap suffices.  fn(x, y, z, c, dx, dy, dz, k) gets
-// the cell index and the minimum-image displacement from the particle centre.
+// outside the lattice (reach < L / 2, centres in [0, L)), so one wrap suffices.
+// fn(x, y, z, c, dx, dy, dz, k) gets the cell index and the displacement from
+// the particle's image k: every node of an image's box lies within reach of
+// that image's centre (reach < L / 2, the boxes of different images do not
+// overlap), so that image is the node's minimum image and the displacement is
+// the unwrapped coordinate minus the image centre.
 template <typename TC, typename F>
-__device__ __forceinline__ void for_box_cells(const View& v, const ImgBox (&b)[3], TC Rx, TC Ry, TC Rz,
+__device__ __forceinline__ void for_box_cells(const View& v, const ImgBox<TC> (&b)[3], TC Rx, TC Ry, TC Rz,
                                               TC delta, F&& fn) {
   const int lane = threadIdx.x & 15, half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
 #pragma unroll
   for (int kb = 0; kb < 3; ++kb) {
-    const ImgBox B = b[kb];
+    const ImgBox<TC> B = b[kb];
     if (B.cnt == 0) continue;
     const int rows = B.ey * B.ez;
     for (int row = half; row < rows; row += nhalf) {
       const int lz = row / B.ey, ly = row - lz * B.ey;
-      const int y = B.y0 + ly, z = wrap1(B.z0 + lz, v.nz);
+      const int y = B.y0 + ly, zu = B.z0 + lz, z = wrap1(zu, v.nz);
+      const TC dy = (TC)y - B.cy, dz = (TC)zu - B.cz;
       for (int lx = lane; lx < B.ex; lx += 16) {
-        const int x = wrap1(B.x0 + lx, v.nx);
-        TC dx = (TC)x - Rx, dy = (TC)y - Ry, dz = (TC)z - Rz;
-        const int k = le_image_v(v, dx, dy, dz, delta);
+        const int xu = B.x0 + lx, x = wrap1(xu, v.nx);
+        const TC dx = (TC)xu - B.cx;
+        const int k = kb - 1;
         const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
         fn(x, y, z, c, dx, dy, dz, k);
       }
@@ -105,7 +115,7 @@ __global__ void k_claim(Batch B) {
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto);
-  ImgBox b[3];
+  ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
     if (dx * dx + dy * dy + dz * dz < am * am) {
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto), ule = pule<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  ImgBox b[3];
+  ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k) {
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  ImgBox b[3];
+  ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   const TC inner = am > (TC)1 ? am - (TC)1 : (TC)0;
@@ -244,6 +254,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   __shared__ TC red[32 * 15];
   __shared__ int s_nodes, s_items_n;
   __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
+  __shared__ uint2 s_disp[LINK_NODES_MAX];      // their displacement from the image centre (3 halves)
   __shared__ uint32_t s_items[LINK_CHUNK];      // screened (node, direction) items of one chunk
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
@@ -258,7 +269,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   const Proto* pr = v.proto;
   const TC delta = pdelta<TC>(pr), ule = pule<TC>(pr);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  ImgBox b[3];
+  ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   // A link's receiver lies within sqrt(2) of its solid node, or -- across a
   // Lees-Edwards plane, where the receiver is the node whose nearest source is
@@ -270,8 +281,15 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
     if (!(d2 < am * am) || d2 < inner * inner) return;
     if (v.owner[s] != i) return;
     const int k = atomicAdd(&s_nodes, 1);
-    if (k < LINK_NODES_MAX) s_node[k] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
-    else overflow = true;
+    if (k < LINK_NODES_MAX) {
+      s_node[k] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
+      const uint32_t hx = __half_as_ushort(__float2half_rn((float)sdx));
+      const uint32_t hy = __half_as_ushort(__float2half_rn((float)sdy));
+      const uint32_t hz = __half_as_ushort(__float2half_rn((float)sdz));
+      s_disp[k] = make_uint2(hx | (hy << 16), hz);
+    } else {
+      overflow = true;
+    }
   });
   if (overflow) atomicOr(v.err, ERR_LINKS);
   __syncthreads();
@@ -280,12 +298,13 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) acc[k] = 0;
   const int items = nn * 18;
-  // a receiver deeper than a_map - 0.05 inside this particle's own mapped
+  // a receiver deeper than a_map - 0.1 inside this particle's own mapped
   // sphere is one of its solid nodes (the node map holds every node closer
-  // than a_map): no link, and no need to look it up.  Items are screened in
+  // than a_map; the margin covers the half-precision displacements of the
+  // screen): no link, and no need to look it up.  Items are screened in
   // chunks; the survivors are compacted into shared memory so that full
   // warps then process only candidate links (one memory round trip each).
-  const TC deep = am > (TC)0.05 ? (am - (TC)0.05) * (am - (TC)0.05) : (TC)0;
+  const float deep = am > (TC)0.1 ? (float)((am - (TC)0.1) * (am - (TC)0.1)) : 0.0f;
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < items; base += LINK_CHUNK) {
     const int end = min(items, base + LINK_CHUNK);
@@ -294,14 +313,17 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       const int t = t0 + (int)threadIdx.x;
       bool keep = false;
       if (t < end) {
-        const uint32_t w = s_node[t / 18];
+        const int nd = t / 18;
         const int p = 1 + t % 18;
-        const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
+        const int y = (int)((s_node[nd] >> 11) & 2047u);
         const int ryn = y + D3Q19::cy(p);
         keep = true;
         if (ryn >= 0 && ryn < v.ny) {
-          TC ex = (TC)(x + D3Q19::cx(p)) - Rx, ey = (TC)ryn - Ry, ez = (TC)(z + D3Q19::cz(p)) - Rz;
-          le_image_v(v, ex, ey, ez, delta);
+          // receiver displacement = node displacement + c_p (same image)
+          const uint2 dd = s_disp[nd];
+          const float ex = __half2float(__ushort_as_half((unsigned short)(dd.x & 0xffffu))) + (float)D3Q19::cx(p);
+          const float ey = __half2float(__ushort_as_half((unsigned short)(dd.x >> 16))) + (float)D3Q19::cy(p);
+          const float ez = __half2float(__ushort_as_half((unsigned short)(dd.y & 0xffffu))) + (float)D3Q19::cz(p);
           keep = !(ex * ex + ey * ey + ez * ez < deep);
         }
       }
