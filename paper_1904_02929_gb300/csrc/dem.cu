@@ -278,18 +278,41 @@ __device__ inline void write_plb(const View& v, int i, const double* R, const do
   pp[9] = (TC)v.rad[i];
 }
 
+// Per-step constants of one particle, loaded once per lattice step when a
+// warp holds a single particle for the whole step: the protocol offset and
+// image velocity, and for its integration the held link and covering force
+// and torque and the inverse mass and inertia.
+template <typename T>
+struct StepConst {
+  T delta, ule;
+  double Fh[3], Fcov[3], Th[3], Tcov[3], im, iI;
+};
+
+template <typename T>
+__device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
+  const Proto* pr = v.proto;
+  c.delta = (T)pr->delta;
+  c.ule = (T)pr->ule;
+  for (int a = 0; a < 3; ++a) {
+    c.Fh[a] = v.Fh[3 * i + a]; c.Fcov[a] = v.Fcov[3 * i + a];
+    c.Th[a] = v.Th[3 * i + a]; c.Tcov[a] = v.Tcov[3 * i + a];
+  }
+  c.im = v.inv_m[i];
+  c.iI = v.inv_I[i];
+}
+
 // Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
 // the write state, with the pair force and torque (F, T); at the last sub-step
 // the Lees-Edwards wrap of the centre, the speed check and the compute-type copy.
 // Velocities are updated in precision T; positions always in FP64.
 template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
-                                     double dt, bool last, bool plb_double) {
+                                     double dt, bool last, bool plb_double, const StepConst<T>* sc) {
   double R[3], U[3], W[3];
-  const T im = (T)v.inv_m[i], iI = (T)v.inv_I[i], dtt = (T)dt;
+  const T im = (T)(sc ? sc->im : v.inv_m[i]), iI = (T)(sc ? sc->iI : v.inv_I[i]), dtt = (T)dt;
   for (int c = 0; c < 3; ++c) {
-    const T F = (T)v.Fh[3 * i + c] + (T)v.Fcov[3 * i + c] + Fp[c];
-    const T Tq = (T)v.Th[3 * i + c] + (T)v.Tcov[3 * i + c] + Tp[c];
+    const T F = (T)(sc ? sc->Fh[c] : v.Fh[3 * i + c]) + (T)(sc ? sc->Fcov[c] : v.Fcov[3 * i + c]) + Fp[c];
+    const T Tq = (T)(sc ? sc->Th[c] : v.Th[3 * i + c]) + (T)(sc ? sc->Tcov[c] : v.Tcov[3 * i + c]) + Tp[c];
     U[c] = (double)((T)S.U[3 * i + c] + dtt * F * im);
     W[c] = (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
   }
@@ -477,11 +500,11 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
 // spring table of the next step.
 template <typename T>
 __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample, bool last,
-                         const SpringTable& next) {
+                         const SpringTable& next, const StepConst<T>* sc) {
   const int lane = threadIdx.x & 31;
   const Proto* pr = v.proto;
-  const T delta = (T)pr->delta;
-  const T ule = (T)pr->ule;
+  const T delta = sc ? sc->delta : (T)pr->delta;
+  const T ule = sc ? sc->ule : (T)pr->ule;
   T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   T cv[9], rv[9];
   for (int c = 0; c < 9; ++c) { cv[c] = (T)0; rv[c] = (T)0; }
@@ -565,7 +588,7 @@ __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt,
   }
   __syncwarp();
   if (lane == 0) {
-    integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8);
+    integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8, sc);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(v.step_acc + 15 + c, (double)cv[c]);
@@ -601,6 +624,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
   const int gwarp = blockIdx.x * DEM_WARPS + wib, nwarps = gridDim.x * DEM_WARPS;
   const int ntot = B.part_off[B.nbox];
   // candidate partners of every moving particle at the step start
+  int my_np = 0;   // candidate count of this warp's last particle (all lanes)
   for (int g = gwarp; g < ntot; g += nwarps) {
     const int bx = box_of(B.part_off, B.nbox, g);
     const View& v = B.views[bx];
@@ -608,6 +632,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
     const int i = g - B.part_off[bx];
     const int np = collect_pairs<T>(v, i, spring_table(v, v.proto->t));
     if ((threadIdx.x & 31) == 0) v.pcnt[i] = np;
+    my_np = np;
   }
   bool any_odd = false;
   for (int b = 0; b < B.nbox; ++b) {
@@ -631,6 +656,40 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
     }
     grid.sync();
   }
+  if (ntot <= nwarps) {
+    // at most one particle per warp: its per-step constants stay in registers
+    const int g = gwarp;
+    bool has = false;
+    int bx = 0, i = 0, nsub = 0;
+    if (g < ntot) {
+      bx = box_of(B.part_off, B.nbox, g);
+      i = g - B.part_off[bx];
+      has = B.views[bx].move != 0;
+    }
+    const View& v = B.views[bx];
+    __shared__ StepConst<T> s_sc[DEM_WARPS];
+    StepConst<T>& sc = s_sc[wib];
+    SpringTable nxt{};
+    State toA{}, toB{};
+    if (has) {
+      nsub = v.nsub;
+      if ((threadIdx.x & 31) == 0) load_step_const<T>(v, i, sc);
+      __syncwarp();
+      nxt = spring_table(v, v.proto->t + 1);
+      toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W};
+      toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2};
+    }
+    const T dt = has ? (T)(1.0 / nsub) : (T)0;
+    for (int sub = 0; sub < B.max_nsub; ++sub) {
+      if (has && sub < nsub) {
+        // sub-step s reads A when (nsub - s) is even, so the last write lands in A
+        const State& S = ((nsub - sub) & 1) ? toA : toB;
+        pairs_of<T>(v, i, my_np, S, dt, sub == 0, sub == nsub - 1, nxt, &sc);
+      }
+      if (sub + 1 < B.max_nsub) grid.sync();
+    }
+    return;
+  }
   for (int sub = 0; sub < B.max_nsub; ++sub) {
     for (int g = gwarp; g < ntot; g += nwarps) {
       const int bx = box_of(B.part_off, B.nbox, g);
@@ -643,7 +702,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T>(v, i, v.pcnt[i], S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1,
-                  spring_table(v, v.proto->t + 1));
+                  spring_table(v, v.proto->t + 1), nullptr);
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }
