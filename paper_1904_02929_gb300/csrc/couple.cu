@@ -74,9 +74,13 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
 // that image's centre (reach < L / 2, the boxes of different images do not
 // overlap), so that image is the node's minimum image and the displacement is
 // the unwrapped coordinate minus the image centre.
+// Rows (y, z) whose distance from the image's x axis is row_r or more hold no
+// node closer than row_r and are skipped.  fn also gets d2 = dx^2 + (dy^2 +
+// dz^2), summed in that order so that the row test and every node test agree.
 template <typename TC, typename F>
 __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox<TC> (&b)[3], TC Rx, TC Ry, TC Rz,
-                                              TC delta, F&& fn) {
+                                              TC delta, TC row_r, F&& fn) {
+  const TC row_r2 = row_r * row_r;
   const int lane = threadIdx.x & 15, half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
 #pragma unroll
   for (int kb = 0; kb < 3; ++kb) {
@@ -87,12 +91,14 @@ __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox<TC> (&
       const int lz = row / B.ey, ly = row - lz * B.ey;
       const int y = B.y0 + ly, zu = B.z0 + lz, z = wrap1(zu, v.nz);
       const TC dy = (TC)y - B.cy, dz = (TC)zu - B.cz;
+      const TC rho2 = dy * dy + dz * dz;
+      if (!(rho2 < row_r2)) continue;
       for (int lx = lane; lx < B.ex; lx += 16) {
         const int xu = B.x0 + lx, x = wrap1(xu, v.nx);
         const TC dx = (TC)xu - B.cx;
         const int k = kb - 1;
         const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
-        fn(x, y, z, c, dx, dy, dz, k);
+        fn(x, y, z, c, dx, dy, dz, k, dx * dx + rho2);
       }
     }
   }
@@ -117,8 +123,8 @@ __global__ void k_claim(Batch B) {
   const TC delta = pdelta<TC>(v.proto);
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
-    if (dx * dx + dy * dy + dz * dz < am * am) {
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am, [&](int, int, int, long long c, TC, TC, TC, int, TC d2) {
+    if (d2 < am * am) {
       const int old = atomicCAS(v.owner + c, -1, i);
       if (old != -1 && old != i) atomicOr(v.err, ERR_OVERLAP);
     }
@@ -143,9 +149,11 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k) {
-    // only nodes outside the mapped sphere can leave it
-    if (dx * dx + dy * dy + dz * dz < am * am) return;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am + (TC)1,
+                    [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k, TC d2) {
+    // only nodes outside the mapped sphere can leave it, and only those within
+    // one lattice unit (a particle moves less than 0.5 per step)
+    if (d2 < am * am) return;
     if (v.owner[c] != i) return;
     // solid node leaves the mapped sphere: fluid at rho0 and the boundary velocity
     const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
@@ -189,8 +197,7 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   const TC inner = am > (TC)1 ? am - (TC)1 : (TC)0;
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int) {
-    const TC d2 = dx * dx + dy * dy + dz * dz;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int, TC d2) {
     // nodes deeper than a_map - 1 were inside before the move (speed < 0.5)
     if (!(d2 < am * am) || d2 < inner * inner) return;
     const int own = v.owner[c];
@@ -245,7 +252,7 @@ __device__ __forceinline__ long long link_target_nr(const View& v, const Proto* 
 // nodes near the mapped surface into shared memory, then its threads take
 // (node, direction) work items, so every lane does the same work.
 constexpr int LINK_NODES_MAX = 2048;
-constexpr int LINK_CHUNK = 4608;     // items screened per round (18 per thread of a 256-thread block)
+constexpr int LINK_CHUNK = 4608;     // items of one round: up to 18 per node, one node per thread of 256
 
 template <int P>
 __global__ void __launch_bounds__(256) k_links(Batch B) {
@@ -254,8 +261,8 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   __shared__ TC red[32 * 15];
   __shared__ int s_nodes, s_items_n;
   __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
-  __shared__ uint2 s_disp[LINK_NODES_MAX];      // their displacement from the image centre (3 halves)
-  __shared__ uint32_t s_items[LINK_CHUNK];      // screened (node, direction) items of one chunk
+  __shared__ uint32_t s_mask[LINK_NODES_MAX];   // their candidate link directions (bits 1-18)
+  __shared__ uint32_t s_items[LINK_CHUNK];      // (node << 5 | direction) items of one round
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
@@ -275,18 +282,31 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   // Lees-Edwards plane, where the receiver is the node whose nearest source is
   // s -- within sqrt(1.5^2 + 1) = 1.80; deeper solid nodes cannot have links.
   const TC inner = am > (TC)2 ? am - (TC)2 : (TC)0;
+  // a receiver deeper than a_map - 0.05 inside this particle's own mapped
+  // sphere is one of its solid nodes (the node map holds every node closer
+  // than a_map): that direction is no link and needs no look-up
+  const TC deep = am > (TC)0.05 ? (am - (TC)0.05) * (am - (TC)0.05) : (TC)0;
   bool overflow = false;
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, [&](int x, int y, int z, long long s, TC sdx, TC sdy, TC sdz, int) {
-    const TC d2 = sdx * sdx + sdy * sdy + sdz * sdz;
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am,
+                    [&](int x, int y, int z, long long s, TC sdx, TC sdy, TC sdz, int, TC d2) {
     if (!(d2 < am * am) || d2 < inner * inner) return;
     if (v.owner[s] != i) return;
+    uint32_t m = 0;
+#pragma unroll
+    for (int p = 1; p < 19; ++p) {
+      const int ryn = y + D3Q19::cy(p);
+      bool keep = true;   // a pull across a Lees-Edwards plane is always examined
+      if (ryn >= 0 && ryn < v.ny) {
+        const TC ex = sdx + (TC)D3Q19::cx(p), ey = sdy + (TC)D3Q19::cy(p), ez = sdz + (TC)D3Q19::cz(p);
+        keep = !(ex * ex + ey * ey + ez * ez < deep);
+      }
+      if (keep) m |= 1u << p;
+    }
+    if (!m) return;
     const int k = atomicAdd(&s_nodes, 1);
     if (k < LINK_NODES_MAX) {
       s_node[k] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
-      const uint32_t hx = __half_as_ushort(__float2half_rn((float)sdx));
-      const uint32_t hy = __half_as_ushort(__float2half_rn((float)sdy));
-      const uint32_t hz = __half_as_ushort(__float2half_rn((float)sdz));
-      s_disp[k] = make_uint2(hx | (hy << 16), hz);
+      s_mask[k] = m;
     } else {
       overflow = true;
     }
@@ -297,48 +317,38 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   TC acc[15];
 #pragma unroll
   for (int k = 0; k < 15; ++k) acc[k] = 0;
-  const int items = nn * 18;
-  // a receiver deeper than a_map - 0.1 inside this particle's own mapped
-  // sphere is one of its solid nodes (the node map holds every node closer
-  // than a_map; the margin covers the half-precision displacements of the
-  // screen): no link, and no need to look it up.  Items are screened in
-  // chunks; the survivors are compacted into shared memory so that full
-  // warps then process only candidate links (one memory round trip each).
-  const float deep = am > (TC)0.1 ? (float)((am - (TC)0.1) * (am - (TC)0.1)) : 0.0f;
+  // rounds of blockDim nodes: their candidate directions are expanded into
+  // (node, direction) items in shared memory (at most 18 per node), so that
+  // full warps then process the items, one memory round trip each
   const int lane = threadIdx.x & 31;
-  for (int base = 0; base < items; base += LINK_CHUNK) {
-    const int end = min(items, base + LINK_CHUNK);
-    // screen: item t = (node t / 18, direction 1 + t % 18)
-    for (int t0 = base; t0 < end; t0 += blockDim.x) {
-      const int t = t0 + (int)threadIdx.x;
-      bool keep = false;
-      if (t < end) {
-        const int nd = t / 18;
-        const int p = 1 + t % 18;
-        const int y = (int)((s_node[nd] >> 11) & 2047u);
-        const int ryn = y + D3Q19::cy(p);
-        keep = true;
-        if (ryn >= 0 && ryn < v.ny) {
-          // receiver displacement = node displacement + c_p (same image)
-          const uint2 dd = s_disp[nd];
-          const float ex = __half2float(__ushort_as_half((unsigned short)(dd.x & 0xffffu))) + (float)D3Q19::cx(p);
-          const float ey = __half2float(__ushort_as_half((unsigned short)(dd.x >> 16))) + (float)D3Q19::cy(p);
-          const float ez = __half2float(__ushort_as_half((unsigned short)(dd.y & 0xffffu))) + (float)D3Q19::cz(p);
-          keep = !(ex * ex + ey * ey + ez * ez < deep);
-        }
+  for (int nb = 0; nb < nn; nb += blockDim.x) {
+    {
+      const int k = nb + (int)threadIdx.x;
+      const uint32_t m = k < nn ? s_mask[k] : 0u;
+      const int cnt = __popc(m);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int up = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += up;
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
       int wbase = 0;
-      if (lane == 0 && bal) wbase = atomicAdd(&s_items_n, __popc(bal));
-      wbase = __shfl_sync(0xffffffffu, wbase, 0);
-      if (keep) s_items[wbase + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)t;
+      if (lane == 31 && incl) wbase = atomicAdd(&s_items_n, incl);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      int pos = wbase + incl - cnt;
+      uint32_t mm = m;
+      while (mm) {
+        const int p = __ffs(mm) - 1;
+        mm &= mm - 1;
+        s_items[pos++] = ((uint32_t)k << 5) | (uint32_t)p;
+      }
     }
     __syncthreads();
     const int ns = s_items_n;
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      const int t = (int)s_items[k];
-      const uint32_t w = s_node[t / 18];
-      const int p = 1 + t % 18;
+      const uint32_t it = s_items[k];
+      const uint32_t w = s_node[it >> 5];
+      const int p = (int)(it & 31u);
       const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
       int rx, ry, rz;
       bool crossing;
