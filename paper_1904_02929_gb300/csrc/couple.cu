@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am + (TC)1,
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am + (TC)0.6,
                     [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k, TC d2) {
-    // only nodes outside the mapped sphere can leave it, and only those within
-    // one lattice unit (a particle moves less than 0.5 per step)
-    if (d2 < am * am) return;
+    // only nodes outside the mapped sphere can leave it, and only those that
+    // were inside before the move: closer than a_map + 0.5 (a particle moves
+    // less than 0.5 per step; 0.6 leaves a margin)
+    if (d2 < am * am || !(d2 < (am + (TC)0.6) * (am + (TC)0.6))) return;
     if (v.owner[c] != i) return;
     // solid node leaves the mapped sphere: fluid at rho0 and the boundary velocity
     const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
@@ -196,9 +197,9 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  const TC inner = am > (TC)1 ? am - (TC)1 : (TC)0;
+  const TC inner = am > (TC)0.6 ? am - (TC)0.6 : (TC)0;
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int, TC d2) {
-    // nodes deeper than a_map - 1 were inside before the move (speed < 0.5)
+    // nodes deeper than a_map - 0.6 were inside before the move (speed < 0.5)
     if (!(d2 < am * am) || d2 < inner * inner) return;
     const int own = v.owner[c];
     if (own == i) return;

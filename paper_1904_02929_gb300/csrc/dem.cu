@@ -138,7 +138,7 @@ struct PairOut {
 // FP64 (positions are FP64 on every path), the rest in precision T; returns
 // false when the pair is out of range.
 template <typename T>
-__device__ inline bool pair_geometry(const View& v, const double* __restrict__ Rs, int a, int b, T delta,
+__device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int b, T delta,
                                      T d[3], int& k, T& h) {
   d[0] = (T)(Rs[3 * b] - Rs[3 * a]);
   d[1] = (T)(Rs[3 * b + 1] - Rs[3 * a + 1]);
@@ -161,7 +161,7 @@ __device__ inline bool pair_geometry(const View& v, const double* __restrict__ R
 // minimum-image displacement d, gap h and the pair's tangential spring as it
 // stood after the previous sub-step (zero for a new contact).
 template <typename T>
-__device__ void pair_interact(const View& v, const double* __restrict__ Us, const double* __restrict__ Ws,
+__device__ void pair_interact(const View& v, const double* Us, const double* Ws,
                               int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
                               PairOut<T>& o) {
   const T ra = (T)v.rad[a], rb = (T)v.rad[b];
@@ -261,7 +261,9 @@ __device__ inline T warp_sum(T x) {
   return x;
 }
 
-// State buffers of one sub-step.
+// State buffers of one sub-step.  Other warps write the read buffers during
+// the launch (in earlier sub-steps), so they are never read through the
+// non-coherent read-only path.
 struct State {
   const double *R, *U, *W;   // read: positions and velocities at the sub-step start
   double *Rn, *Un, *Wn;      // write: after the sub-step
