@@ -178,6 +178,7 @@ def batched_leg(ws, steps: int, warmup: int):
     for w, g in zip(ws, boxes):
         batch.attach(g, S.make_shear(**w.shear))
     batch.step(warmup)
+    tuned = batch.tune()                            # collide-stream launch shape for this batch
     for g in boxes:
         g.stress_reset()
     batch.profile(True)
@@ -231,12 +232,19 @@ def batched_leg(ws, steps: int, warmup: int):
     so = o.stress(O.TOTAL)[0][0, 1]
     mb = nodes * steps / (ms_b / 1e3) / 1e6
     mp = nodes * steps / (ms_p / 1e3) / 1e6
+    k1 = k1_ms / max(k1_n, 1)
+    alg = 2 * 19 * 2 * nodes                        # BF16 populations of every lattice cell
+    peak, kind = peak_hbm()
     return {
         "boxes": len(ws), "lattice_nodes": nodes, "particles": parts, "steps": steps,
         "warmup": warmup, "storage": "bf16", "compute": "f32 (positions, offsets, stress sums f64)",
         "value": mb, "unit": "MLUPS", "ms_per_step": ms_b / steps,
         "particle_steps_per_s": parts * steps / (ms_b / 1e3),
-        "k_collide_stream_avg_ms": k1_ms / max(k1_n, 1),
+        "k_collide_stream_avg_ms": k1,
+        "roofline": {"bound": "hbm", "kernel": "k_collide_stream<bf16>", "achieved": alg / (k1 / 1e3) / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
+                     "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+        "launch_shape": tuned,
         "stage_us": {k: round(1e3 * v / max(k1_n, 1), 1) for k, v in stages.items()},
         "gpu_launches_per_step": launches_b, "workspace_bytes": mem_b,
         "l2": "not flushed: the boxes hold > 1.9 GB of populations, far above L2",
@@ -263,7 +271,7 @@ def monolayer_leg(steps: int, warmup: int):
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp16", **w.params)
     sh = S.make_shear(**w.shear)
     g.step(warmup, sh)
-    nfluid = int((g.owner() < 0).sum())
+    tuned = g.tune()
     S.susp_profile(g.h, True)
     g.step(1, sh)
     torch.cuda.synchronize()
@@ -282,7 +290,7 @@ def monolayer_leg(steps: int, warmup: int):
     info = g.info()
     g.close()
     k1 = stages["collide_stream"] / n
-    alg = 2 * 19 * 2 * nfluid
+    alg = 2 * 19 * 2 * w.ncell                      # FP16 populations of every lattice cell
     peak, kind = peak_hbm()
     return {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "particles": w.n, "storage": "fp16",
             "steps": steps, "value": w.ncell * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
@@ -292,6 +300,7 @@ def monolayer_leg(steps: int, warmup: int):
             "roofline": {"bound": "hbm", "kernel": "k_collide_stream<fp16>", "achieved": alg / (k1 / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
                          "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+            "launch_shape": tuned,
             "l2": "not flushed: 560 MB of populations per buffer, above L2"}
 
 
@@ -403,6 +412,7 @@ def main():
     info = g.info()
     sh = S.make_shear(**w.shear)
     g.step(args.warmup, sh)
+    tuned = g.tune()                        # collide-stream launch shape (untimed)
     torch.cuda.synchronize()
     nfluid = int((g.owner() < 0).sum())
 
@@ -443,6 +453,7 @@ def main():
     barrier()
     t0 = time.perf_counter()
     e = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **w.params)
+    e.tune()
     for k in range(K):
         e.step(1, sh)
         R, _, _ = e.particles()
@@ -461,7 +472,7 @@ def main():
 
     if rank == 0:
         peak, peak_kind = peak_hbm()
-        alg_bytes = 2 * 19 * 4 * nfluid                  # FP32 populations of fluid nodes
+        alg_bytes = 2 * 19 * 4 * w.ncell                 # FP32 populations of every lattice cell
         k1_avg_s = (k1_ms / max(k1_n, 1)) / 1e3
         achieved = alg_bytes / k1_avg_s / 1e9
         traffic = k1_traffic(w.name)
@@ -473,6 +484,7 @@ def main():
                        "phi3": 0.50, "storage": "fp32", "shear_rate": w.shear["rate"],
                        "dem_substeps": info.dem_substeps, "fluid_nodes": nfluid,
                        "l2": "flushed between timed steps (256 MB write)",
+                       "launch_shape": tuned,
                        "parallelism": f"replicas{world}"},
             "particle_steps_per_s": psteps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -217,6 +217,23 @@ susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double tau, double d
  * as plain launches.  Disabling drops the captured graph.  Synchronises. */
 susp_status susp_set_graphs(susp *h, int enable);
 
+/* Launch-shape tuner (no counterpart in the paper; the batched step takes
+ * its tile shapes from it).  Times the collide-stream on this machine for each
+ * tile height of 4, 8 and 16 rows of 32 nodes and each count of resident
+ * blocks per SM that the occupancy allows (three launches per shape after a
+ * warm-up, CUDA events on the handle's stream), keeps the fastest, and
+ * reports it: *tile_rows, *blocks_per_sm, and *us, the average launch time
+ * of that shape in microseconds (any of the three may be NULL).  Call it
+ * between steps: the trial launches only rewrite the population buffer that
+ * the next step overwrites, and the current step's viscous-stress sums are
+ * cleared after them, so the following steps give the untuned results up to
+ * the summation order of the viscous-stress block sums (populations and
+ * particles are bitwise the same).  The choice holds for later steps and
+ * across susp_save / susp_load.  Synchronises; drops the captured graph.  A
+ * box attached to a batch returns SUSP_ESTATE (tune the batch).  Errors:
+ * SUSP_EINVAL, SUSP_ESTATE, SUSP_ECUDA. */
+susp_status susp_tune(susp *h, int *tile_rows, int *blocks_per_sm, double *us);
+
 /* Release the handle (not the caller's workspace). */
 void susp_destroy(susp *h);
 
@@ -251,6 +268,10 @@ susp_status susp_batch_detach(susp_batch *b, susp *h);
 int susp_batch_size(const susp_batch *b);
 /* Advance every attached box by nsteps steps under its own protocol (asynchronous). */
 susp_status susp_batch_step(susp_batch *b, int nsteps);
+/* As susp_tune, over every attached box at once (one shape for the batch's
+ * persistent collide-stream grid); the choice holds across attach and
+ * detach.  SUSP_ESTATE when no box is attached. */
+susp_status susp_batch_tune(susp_batch *b, int *tile_rows, int *blocks_per_sm, double *us);
 /* As susp_profile / susp_profile_read, for the batch's collide-stream launch. */
 susp_status susp_batch_profile(susp_batch *b, int enable);
 susp_status susp_batch_profile_read(susp_batch *b, double *ms_total, int *launches);

@@ -18,8 +18,8 @@ using namespace susp_dev;
 // launchers defined in the other translation units
 void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s);
 void launch_collide_stream(int prec, const Batch& B, int grid, cudaStream_t s);
-int lb_blocks(int nx, int ny, int nz);
-int lb_grid_blocks(int prec, int nx, int ny, int nz);
+int lb_blocks(int nx, int ny, int nz, int tile_lg);
+void lb_occupancy(int prec, int* per_sm, int* sms);
 void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s);
 void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s);
 void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s);
@@ -245,6 +245,8 @@ struct Engine {
   int nbox = 0, nparts = 0, ncells = 0, nplane = 0, ntiles = 0;
   bool any_move = false;     // some box has moving particles
   int lb_grid = 1, dem_grid = 1;
+  int tile_lg = 3;           // collide-stream tile height 2^tile_lg (the tuner's choice)
+  int bps = 0;               // its resident blocks per SM (0: as many as fit)
   cudaStream_t stream = nullptr;
   bool use_graphs = true;
   GraphSlot graphs[2];       // [timed]
@@ -272,7 +274,7 @@ static void eng_tables(Engine& e, const std::vector<const View*>& vs, std::vecto
   int msub = 1;
   for (int b = 0; b < nb; ++b) {
     const View& v = *vs[b];
-    tile[b + 1] = tile[b] + lb_blocks(v.nx, v.ny, v.nz);
+    tile[b + 1] = tile[b] + lb_blocks(v.nx, v.ny, v.nz, e.tile_lg);
     part[b + 1] = part[b] + v.n;
     plane[b + 1] = plane[b] + 2 * v.nx * v.nz;
     cell[b + 1] = cell[b] + (v.brute ? 0 : v.ncells);
@@ -282,7 +284,11 @@ static void eng_tables(Engine& e, const std::vector<const View*>& vs, std::vecto
   e.ntiles = tile[nb]; e.nparts = part[nb]; e.nplane = plane[nb]; e.ncells = cell[nb];
   e.B.nbox = nb;
   e.B.max_nsub = msub;
-  e.lb_grid = std::max(1, std::min(lb_grid_blocks(e.prec, 0, 0, 0), e.ntiles));
+  e.B.tile_lg = e.tile_lg;
+  int per = 1, sms = 1;
+  lb_occupancy(e.prec, &per, &sms);
+  const int bps = (e.bps >= 1 && e.bps <= per) ? e.bps : per;
+  e.lb_grid = std::max(1, std::min(sms * bps, e.ntiles));
   e.dem_grid = dem_grid_blocks(e.prec == 0, e.nparts);
 }
 
@@ -447,6 +453,68 @@ static void eng_release(Engine& e) {
   eng_drop_graphs(e);
   for (auto& x : e.ev) cudaEventDestroy(x);
   e.ev.clear();
+}
+
+// Clear the viscous-stress sums of the current step of every box.
+__global__ void k_zero_visc(Batch B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B.nbox)
+    for (int k = 0; k < 6; ++k) B.views[b].step_acc[k] = 0.0;
+}
+
+// Launch-shape tuner: times the collide-stream over the set's own boxes for
+// tile heights of 4, 8 and 16 rows and each count of resident blocks per SM
+// the occupancy allows, and keeps the fastest.  At a step boundary the
+// collide-stream is a pure function of the buffer it reads and overwrites
+// the other one, which the next step rewrites, so the trial launches leave
+// the state alone but for the viscous-stress sums, cleared afterwards (they
+// are zero at a step boundary).  tabs_dev: the device copy of the prefix
+// tables, rewritten for each trial shape.  Synchronises.
+static susp_status eng_tune(Engine& e, const std::vector<const View*>& vs, char* tabs_dev, int* tile_rows,
+                            int* blocks_per_sm, double* us) {
+  cudaStream_t s = e.stream;
+  susp_status st = cuda_check(cudaStreamSynchronize(s), "sync");
+  if (st) return st;
+  eng_drop_graphs(e);
+  int per = 1, sms = 1;
+  lb_occupancy(e.prec, &per, &sms);
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  st = cuda_check(cudaEventCreate(&ea), "cudaEventCreate");
+  if (!st) st = cuda_check(cudaEventCreate(&eb), "cudaEventCreate");
+  const int reps = 3;
+  double best = 1e300;
+  int best_lg = e.tile_lg, best_bps = e.bps;
+  std::vector<int> tabs;
+  for (int lg = 2; lg <= 4 && !st; ++lg)
+    for (int bps = 1; bps <= per && !st; ++bps) {
+      e.tile_lg = lg;
+      e.bps = bps;
+      eng_tables(e, vs, tabs);
+      cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
+      launch_plane_moments(e.prec, e.B, e.nplane, s);
+      launch_collide_stream(e.prec, e.B, e.lb_grid, s);   // warm-up
+      cudaEventRecord(ea, s);
+      for (int r = 0; r < reps; ++r) launch_collide_stream(e.prec, e.B, e.lb_grid, s);
+      cudaEventRecord(eb, s);
+      st = cuda_check(cudaEventSynchronize(eb), "tuning launch");
+      float ms = 0.0f;
+      if (!st) st = cuda_check(cudaEventElapsedTime(&ms, ea, eb), "cudaEventElapsedTime");
+      if (!st && ms / reps < best) { best = ms / reps; best_lg = lg; best_bps = bps; }
+    }
+  if (ea) cudaEventDestroy(ea);
+  if (eb) cudaEventDestroy(eb);
+  e.tile_lg = best_lg;
+  e.bps = best_bps;
+  eng_tables(e, vs, tabs);
+  cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
+  k_zero_visc<<<(e.nbox + 127) / 128, 128, 0, s>>>(e.B);
+  susp_status st2 = cuda_check(cudaStreamSynchronize(s), "tuner");
+  if (st) return st;
+  if (st2) return st2;
+  if (tile_rows) *tile_rows = 1 << e.tile_lg;
+  if (blocks_per_sm) *blocks_per_sm = std::max(1, std::min(e.bps, per));
+  if (us) *us = 1e3 * best;
+  return SUSP_OK;
 }
 
 // ------------------------------------------------------------ handles
@@ -977,6 +1045,7 @@ susp_status susp_load(susp* h, const void* host_buf, size_t bytes) {
   std::vector<int> tabs;
   Engine tmp;
   tmp.prec = h->prec;
+  tmp.tile_lg = e.tile_lg;
   eng_tables(tmp, std::vector<const View*>{&h->v}, tabs);
   st = cuda_check(cudaMemcpy(h->ws + h->L.views, &h->v, sizeof(View), cudaMemcpyHostToDevice), "load view");
   if (st) return st;
@@ -1016,6 +1085,12 @@ susp_status susp_set_graphs(susp* h, int enable) {
   eng_drop_graphs(h->eng);
   h->eng.use_graphs = enable != 0;
   return SUSP_OK;
+}
+
+susp_status susp_tune(susp* h, int* tile_rows, int* blocks_per_sm, double* us) {
+  if (!h) return fail(SUSP_EINVAL, "NULL handle");
+  if (h->batch) return fail(SUSP_ESTATE, "box is attached to a batch: tune the batch");
+  return eng_tune(h->eng, std::vector<const View*>{&h->v}, h->ws + h->L.tabs, tile_rows, blocks_per_sm, us);
 }
 
 void susp_destroy(susp* h) {
@@ -1105,6 +1180,14 @@ susp_status susp_batch_step(susp_batch* b, int nsteps) {
   if (!b || nsteps < 0) return fail(SUSP_EINVAL, "bad argument to susp_batch_step");
   if (b->boxes.empty()) return SUSP_OK;
   return eng_step(b->eng, nsteps);
+}
+
+susp_status susp_batch_tune(susp_batch* b, int* tile_rows, int* blocks_per_sm, double* us) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  if (b->boxes.empty()) return fail(SUSP_ESTATE, "no box attached");
+  std::vector<const View*> vs;
+  for (susp* h : b->boxes) vs.push_back(&h->v);
+  return eng_tune(b->eng, vs, b->ws + al(sizeof(View) * (size_t)b->max_boxes), tile_rows, blocks_per_sm, us);
 }
 
 susp_status susp_batch_profile(susp_batch* b, int enable) {

@@ -357,7 +357,7 @@ __device__ __forceinline__ void lb_node_staged(const View& v, const typename Sto
   lb_collide<P>(v, fout, idx, n, acc);
 }
 
-// Persistent grid over the 32 (x) by 8 (y) tiles of every box (z slowest
+// Persistent grid over the 32 (x) by 2^tile_lg (y) tiles of every box (z slowest
 // within a box); each block takes a contiguous range of tiles, sums its nodes'
 // viscous stress per box and adds it to the box's accumulator when its range
 // leaves the box.  Within a block the warps claim the 32-node rows of the
@@ -381,10 +381,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
     const int base = B.tile_off[b], te = min(t1, B.tile_off[b + 1]);
     const T* __restrict__ fin = static_cast<const T*>(fin_of(v));
     T* __restrict__ fout = static_cast<T*>(fout_of(v));
-    const int ntx = (v.nx + 31) >> 5, nty = (v.ny + 7) >> 3;
+    const int lg = B.tile_lg, th = 1 << lg;
+    const int ntx = (v.nx + 31) >> 5, nty = (v.ny + th - 1) >> lg;
     const int tiles_per_plane = ntx * nty;
     const int nxny = v.nx * v.ny;
-    const int rows = 8 * (te - t);   // rows of this block's range in this box
+    const int rows = (te - t) << lg;   // rows of this block's range in this box
     __syncthreads();
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
@@ -393,14 +394,14 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
       if (lx == 0) r = atomicAdd(&s_next, 1);
       return __shfl_sync(0xffffffffu, r, 0);
     };
-    // row k of the range: tile t + k / 8, row k % 8 of the tile
+    // row k of the range: tile t + k / th, row k % th of the tile
     auto decode = [&](int k, int& x, int& y, int& z) {
-      const int lt = t + (k >> 3) - base;
+      const int lt = t + (k >> lg) - base;
       z = lt / tiles_per_plane;
       const int r = lt - z * tiles_per_plane;
       const int ty = r / ntx, tx = r - ty * ntx;
       x = tx * 32 + lx;
-      y = ty * 8 + (k & 7);
+      y = (ty << lg) + (k & (th - 1));
     };
     TC acc[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (P != 1) {
@@ -522,11 +523,14 @@ __global__ void k_plane_moments(View v, const typename Store<P>::T* __restrict__
 using namespace susp_dev;
 
 // Tiles of the collide-stream grid (upper bound of its block count).
-int lb_blocks(int nx, int ny, int nz) { return ((nx + 31) / 32) * ((ny + 7) / 8) * nz; }
+// Collide-stream tiles of one box (32 x 2^tile_lg nodes).
+int lb_blocks(int nx, int ny, int nz, int tile_lg) {
+  const int th = 1 << tile_lg;
+  return ((nx + 31) / 32) * ((ny + th - 1) / th) * nz;
+}
 
-// Persistent grid size: resident blocks of k_collide_stream<P> times SMs,
-// capped by the tile count.
-int lb_grid_blocks(int prec, int nx, int ny, int nz) {
+// Resident blocks of k_collide_stream<P> per SM (*per) and the SM count.
+void lb_occupancy(int prec, int* per_sm, int* sms_out) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -539,8 +543,8 @@ int lb_grid_blocks(int prec, int nx, int ny, int nz) {
   }
   if (e != cudaSuccess || per < 1) per = 1;
   if (sms < 1) sms = 1;
-  (void)nx; (void)ny; (void)nz;
-  return sms * per;
+  *per_sm = per;
+  *sms_out = sms;
 }
 
 void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s) {

@@ -154,12 +154,13 @@ enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 }
 // work index (collide-stream tile, particle, plane node, cell) to its box.
 struct Batch {
   const View* __restrict__ views;   // [nbox], device
-  const int* __restrict__ tile_off;   // [nbox + 1] collide-stream tiles (32 x 8 nodes)
+  const int* __restrict__ tile_off;   // [nbox + 1] collide-stream tiles (32 x 2^tile_lg nodes)
   const int* __restrict__ part_off;   // [nbox + 1] particles
   const int* __restrict__ plane_off;  // [nbox + 1] Lees-Edwards plane nodes (2 nx nz)
   const int* __restrict__ cell_off;   // [nbox + 1] cell-list cells
   int nbox;
   int max_nsub;
+  int tile_lg;                        // collide-stream tile height: 2^tile_lg rows
 };
 
 // Box owning global work index g (off is an ascending prefix table).

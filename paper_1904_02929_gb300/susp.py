@@ -108,6 +108,9 @@ def library() -> C.CDLL:
                                               C.c_void_p]
         L.susp_set_graphs.restype = C.c_int
         L.susp_set_graphs.argtypes = [C.c_void_p, C.c_int]
+        for name in ("susp_tune", "susp_batch_tune"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]
         L.susp_destroy.restype = None
         L.susp_destroy.argtypes = [C.c_void_p]
         L.susp_batch_workspace_bytes.restype = C.c_size_t
@@ -277,6 +280,21 @@ def susp_set_graphs(h, enable: bool) -> None:
     _check(library().susp_set_graphs(h, int(bool(enable))), "susp_set_graphs")
 
 
+def _tune(fn, handle, where):
+    rows, bps, us = C.c_int(0), C.c_int(0), C.c_double(0.0)
+    _check(fn(handle, C.byref(rows), C.byref(bps), C.byref(us)), where)
+    return {"tile_rows": int(rows.value), "blocks_per_sm": int(bps.value), "us": float(us.value)}
+
+
+def susp_tune(h) -> dict:
+    """Collide-stream launch shape chosen by timing (tile rows, blocks per SM, us)."""
+    return _tune(library().susp_tune, h, "susp_tune")
+
+
+def susp_batch_tune(b) -> dict:
+    return _tune(library().susp_batch_tune, b, "susp_batch_tune")
+
+
 def susp_destroy(h) -> None:
     library().susp_destroy(h)
 
@@ -433,6 +451,9 @@ class Suspension:
     def set_graphs(self, enable: bool):
         susp_set_graphs(self.h, enable)
 
+    def tune(self) -> dict:
+        return susp_tune(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             susp_destroy(self.h)
@@ -482,6 +503,9 @@ class Batch:
     def errors(self):
         """Device status of each member, in ``self.members`` order."""
         return susp_batch_errors(self.b, len(self.members))
+
+    def tune(self) -> dict:
+        return susp_batch_tune(self.b)
 
     def profile(self, enable: bool):
         susp_batch_profile(self.b, enable)
