@@ -500,9 +500,17 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
 // Sums are reduced across the warp; lane 0 integrates.  At the box's last
 // sub-step the particle's touching pairs with larger partners go to the
 // spring table of the next step.
+// A lane's candidates (slots lane and lane + 32) and their springs, kept in
+// registers across the sub-steps when a warp holds one particle for the step.
+struct PairRegs {
+  int j[PAIR_SLOTS / 32];
+  double h[PAIR_SLOTS / 32][3];
+};
+
 template <typename T>
-__device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample, bool last,
-                         const SpringTable& next, const StepConst<T>* sc) {
+__device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample,
+                                         bool last, const SpringTable& next, const StepConst<T>* sc,
+                                         PairRegs* rg) {
   const int lane = threadIdx.x & 31;
   const Proto* pr = v.proto;
   const T delta = sc ? sc->delta : (T)pr->delta;
@@ -520,17 +528,22 @@ __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt,
   for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
     const int c = lane + 32 * slot;
     if (c >= npairs) continue;
-    const int j = pj[c];
+    const int j = rg ? rg->j[slot] : pj[c];
     const int a = i < j ? i : j, b = i < j ? j : i;
     T d[3], h;
     int k;
     bool touching = false;
     if (pair_geometry<T>(v, S.R, a, b, delta, d, k, h)) {
-      const T spring[3] = {(T)ph[3 * c], (T)ph[3 * c + 1], (T)ph[3 * c + 2]};
+      T spring[3];
+      for (int x = 0; x < 3; ++x) spring[x] = (T)(rg ? rg->h[slot][x] : ph[3 * c + x]);
       PairOut<T> o;
       pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, o);
       touching = o.touching != 0;
-      for (int x = 0; x < 3; ++x) ph[3 * c + x] = touching ? (double)o.ht[x] : 0.0;
+      for (int x = 0; x < 3; ++x) {
+        const double hv = touching ? (double)o.ht[x] : 0.0;
+        if (rg) rg->h[slot][x] = hv;
+        else ph[3 * c + x] = hv;
+      }
       if (i == a) {
         for (int x = 0; x < 3; ++x) { F[x] += o.Fa[x]; Tq[x] += o.Ta[x]; }
         keep[slot] = touching;
@@ -558,6 +571,8 @@ __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt,
       } else {
         for (int x = 0; x < 3; ++x) { F[x] -= o.Fa[x]; Tq[x] += o.Tb[x]; }
       }
+    } else if (rg) {
+      rg->h[slot][0] = 0.0; rg->h[slot][1] = 0.0; rg->h[slot][2] = 0.0;
     } else {
       ph[3 * c] = 0.0; ph[3 * c + 1] = 0.0; ph[3 * c + 2] = 0.0;
     }
@@ -577,8 +592,8 @@ __device__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt,
         const int m = base + __popc(bal & ((1u << lane) - 1u));
         const int c = lane + 32 * slot;
         if (m < v.K) {
-          next.part[i * v.K + m] = pj[c];
-          for (int x = 0; x < 3; ++x) next.val[3 * (i * v.K + m) + x] = ph[3 * c + x];
+          next.part[i * v.K + m] = rg ? rg->j[slot] : pj[c];
+          for (int x = 0; x < 3; ++x) next.val[3 * (i * v.K + m) + x] = rg ? rg->h[slot][x] : ph[3 * c + x];
         }
       }
       base += __popc(bal);
@@ -682,11 +697,23 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2};
     }
     const T dt = has ? (T)(1.0 / nsub) : (T)0;
+    PairRegs rg;
+#pragma unroll
+    for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
+      const int c = (threadIdx.x & 31) + 32 * slot;
+      rg.j[slot] = 0;
+      rg.h[slot][0] = rg.h[slot][1] = rg.h[slot][2] = 0.0;
+      if (has && c < my_np) {
+        const double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+        rg.j[slot] = v.pj[(long long)i * PAIR_SLOTS + c];
+        rg.h[slot][0] = ph[3 * c]; rg.h[slot][1] = ph[3 * c + 1]; rg.h[slot][2] = ph[3 * c + 2];
+      }
+    }
     for (int sub = 0; sub < B.max_nsub; ++sub) {
       if (has && sub < nsub) {
         // sub-step s reads A when (nsub - s) is even, so the last write lands in A
         const State& S = ((nsub - sub) & 1) ? toA : toB;
-        pairs_of<T>(v, i, my_np, S, dt, sub == 0, sub == nsub - 1, nxt, &sc);
+        pairs_of<T>(v, i, my_np, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg);
       }
       if (sub + 1 < B.max_nsub) grid.sync();
     }
@@ -704,7 +731,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T>(v, i, v.pcnt[i], S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1,
-                  spring_table(v, v.proto->t + 1), nullptr);
+                  spring_table(v, v.proto->t + 1), nullptr, nullptr);
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }
