@@ -134,12 +134,30 @@ struct PairOut {
   int touching;
 };
 
+// Per-box pair-force constants in the compute type, converted once instead of
+// at every pair (FP64 arithmetic and conversions are slow on this GPU).
+template <typename T>
+struct PairConst {
+  T kn, kt, eta_n, mu, F0, debye, debye10, lub_cut, lub_delta, eta0, hrange;
+  bool rep, lub;
+};
+
+template <typename T>
+__device__ inline void load_pair_const(const View& v, PairConst<T>& c) {
+  c.kn = (T)v.kn; c.kt = (T)v.kt; c.eta_n = (T)v.eta_n; c.mu = (T)v.mu;
+  c.F0 = (T)v.F0; c.debye = (T)v.debye; c.debye10 = (T)(10.0 * v.debye);
+  c.lub_cut = (T)v.lub_cut; c.lub_delta = (T)v.lub_delta; c.eta0 = (T)v.eta0;
+  c.hrange = (T)v.hrange;
+  c.rep = v.F0 > 0.0;
+  c.lub = v.lub_cut > 0.0;
+}
+
 // Minimum-image displacement R_b - R_a: the centre difference is taken in
 // FP64 (positions are FP64 on every path), the rest in precision T; returns
 // false when the pair is out of range.
 template <typename T>
 __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int b, T delta,
-                                     T d[3], int& k, T& h) {
+                                     const PairConst<T>& pc, T d[3], int& k, T& h) {
   d[0] = (T)(Rs[3 * b] - Rs[3 * a]);
   d[1] = (T)(Rs[3 * b + 1] - Rs[3 * a + 1]);
   d[2] = (T)(Rs[3 * b + 2] - Rs[3 * a + 2]);
@@ -151,10 +169,10 @@ __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int
   d[2] -= fnz * floor(d[2] * sel<T>(v.inv_nz_d, v.inv_nz_f) + (T)0.5);
   const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   const T rsum = (T)(v.rad[a] + v.rad[b]);
-  const T lim = rsum + (T)v.hrange + (T)1e-6;
+  const T lim = rsum + pc.hrange + (T)1e-6;
   if (!(d2 < lim * lim)) return false;   // cheap rejection before the square root
   h = sqrt(d2) - rsum;
-  return (h < (T)v.hrange) || (h < (T)0);
+  return (h < pc.hrange) || (h < (T)0);
 }
 
 // Full interaction of the canonical pair (a, b) in precision T, given the
@@ -163,7 +181,7 @@ __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int
 template <typename T>
 __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
                               int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
-                              PairOut<T>& o) {
+                              const PairConst<T>& pc, PairOut<T>& o) {
   const T ra = (T)v.rad[a], rb = (T)v.rad[b];
   const T dist = sqrt(dot3(d, d));
   const T uab[3] = {(T)(Us[3 * a] - Us[3 * b]) - (T)k * ule, (T)(Us[3 * a + 1] - Us[3 * b + 1]),
@@ -187,13 +205,13 @@ __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
     const T vv[3] = {uab[0] + rot[0], uab[1] + rot[1], uab[2] + rot[2]};
     const T vn = dot3(vv, n);
     const T vt[3] = {vv[0] - vn * n[0], vv[1] - vn * n[1], vv[2] - vn * n[2]};
-    const T kn = (T)v.kn, kt = (T)v.kt;
-    const T fn = kn * overlap + (T)v.eta_n * vn;
+    const T kn = pc.kn, kt = pc.kt;
+    const T fn = kn * overlap + pc.eta_n * vn;
     const T hn = dot3(ht, n);
     for (int c = 0; c < 3; ++c) ht[c] = ht[c] - hn * n[c] + vt[c] * dt;
     T ft[3] = {-kt * ht[0], -kt * ht[1], -kt * ht[2]};
     const T ftm = sqrt(dot3(ft, ft));
-    const T cap = (T)v.mu * fabs(fn);
+    const T cap = pc.mu * fabs(fn);
     if (ftm >= cap && ftm > (T)0) {
       for (int c = 0; c < 3; ++c) {
         ft[c] = cap * ft[c] / ftm;
@@ -213,23 +231,23 @@ __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
     o.touching = 1;
   }
   // ---- double-layer repulsion
-  if (v.F0 > 0.0 && h < (T)(10.0 * v.debye)) {
-    const T fr = (T)v.F0 * exp(-(h > (T)0 ? h : (T)0) / (T)v.debye);
+  if (pc.rep && h < pc.debye10) {
+    const T fr = pc.F0 * exp(-(h > (T)0 ? h : (T)0) / pc.debye);
     for (int c = 0; c < 3; ++c) {
       o.Fr[c] = -fr * n[c];
       o.Fa[c] += o.Fr[c];
     }
   }
   // ---- lubrication correction
-  if (v.lub_cut > 0.0 && h < (T)v.lub_cut) {
+  if (pc.lub && h < pc.lub_cut) {
     const T hh = h < (T)0 ? (T)0 : h;
     const T sc = (T)2 / (ra + rb);
-    const T xi = sc * hh, xc = sc * (T)v.lub_cut, dl = sc * (T)v.lub_delta;
+    const T xi = sc * hh, xc = sc * pc.lub_cut, dl = sc * pc.lub_delta;
     const T inv = (T)1 / (xi + dl) - (T)1 / (xc + dl);
     const T lg = log((xc + dl) / (xi + dl));
     const T be = rb / ra, bj = ra / rb;
     const T pi = (T)3.14159265358979323846;
-    const T e0 = (T)v.eta0;
+    const T e0 = pc.eta0;
     const T op = (T)1 + be, oq = (T)1 + bj;
     const T XA = e0 * (T)6 * pi * ra * ((T)2 * be * be / (op * op * op)) * inv;
     const T YA = e0 * (T)6 * pi * ra * ((T)4 * be * ((T)2 + be + (T)2 * be * be) / ((T)15 * op * op * op)) * lg;
@@ -282,12 +300,16 @@ __device__ inline void write_plb(const View& v, int i, const double* R, const do
 
 // Per-step constants of one particle, loaded once per lattice step when a
 // warp holds a single particle for the whole step: the protocol offset and
-// image velocity, and for its integration the held link and covering force
-// and torque and the inverse mass and inertia.
+// image velocity, the pair-force constants, and for its integration the held
+// link plus covering force and torque and the inverse mass and inertia, in
+// the compute type (the same conversions the per-sub-step path makes).
 template <typename T>
 struct StepConst {
   T delta, ule;
-  double Fh[3], Fcov[3], Th[3], Tcov[3], im, iI;
+  T F0[3], T0[3];   // (T) F^h + (T) F^cov and (T) T^h + (T) T^cov
+  T im, iI;
+  double dt;        // 1 / n_sub
+  PairConst<T> pc;
 };
 
 template <typename T>
@@ -296,11 +318,13 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   c.delta = (T)pr->delta;
   c.ule = (T)pr->ule;
   for (int a = 0; a < 3; ++a) {
-    c.Fh[a] = v.Fh[3 * i + a]; c.Fcov[a] = v.Fcov[3 * i + a];
-    c.Th[a] = v.Th[3 * i + a]; c.Tcov[a] = v.Tcov[3 * i + a];
+    c.F0[a] = (T)v.Fh[3 * i + a] + (T)v.Fcov[3 * i + a];
+    c.T0[a] = (T)v.Th[3 * i + a] + (T)v.Tcov[3 * i + a];
   }
-  c.im = v.inv_m[i];
-  c.iI = v.inv_I[i];
+  c.im = (T)v.inv_m[i];
+  c.iI = (T)v.inv_I[i];
+  c.dt = 1.0 / v.nsub;
+  load_pair_const<T>(v, c.pc);
 }
 
 // Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
@@ -311,10 +335,10 @@ template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
                                      double dt, bool last, bool plb_double, const StepConst<T>* sc) {
   double R[3], U[3], W[3];
-  const T im = (T)(sc ? sc->im : v.inv_m[i]), iI = (T)(sc ? sc->iI : v.inv_I[i]), dtt = (T)dt;
+  const T im = sc ? sc->im : (T)v.inv_m[i], iI = sc ? sc->iI : (T)v.inv_I[i], dtt = (T)dt;
   for (int c = 0; c < 3; ++c) {
-    const T F = (T)(sc ? sc->Fh[c] : v.Fh[3 * i + c]) + (T)(sc ? sc->Fcov[c] : v.Fcov[3 * i + c]) + Fp[c];
-    const T Tq = (T)(sc ? sc->Th[c] : v.Th[3 * i + c]) + (T)(sc ? sc->Tcov[c] : v.Tcov[3 * i + c]) + Tp[c];
+    const T F = (sc ? sc->F0[c] : (T)v.Fh[3 * i + c] + (T)v.Fcov[3 * i + c]) + Fp[c];
+    const T Tq = (sc ? sc->T0[c] : (T)v.Th[3 * i + c] + (T)v.Tcov[3 * i + c]) + Tp[c];
     U[c] = (double)((T)S.U[3 * i + c] + dtt * F * im);
     W[c] = (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
   }
@@ -502,19 +526,23 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
 // spring table of the next step.
 // A lane's candidates (slots lane and lane + 32) and their springs, kept in
 // registers across the sub-steps when a warp holds one particle for the step.
+template <typename T>
 struct PairRegs {
   int j[PAIR_SLOTS / 32];
-  double h[PAIR_SLOTS / 32][3];
+  T h[PAIR_SLOTS / 32][3];   // (springs are exact in T: each is a T result)
 };
 
 template <typename T>
 __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample,
                                          bool last, const SpringTable& next, const StepConst<T>* sc,
-                                         PairRegs* rg) {
+                                         PairRegs<T>* rg) {
   const int lane = threadIdx.x & 31;
   const Proto* pr = v.proto;
   const T delta = sc ? sc->delta : (T)pr->delta;
   const T ule = sc ? sc->ule : (T)pr->ule;
+  PairConst<T> pcl;
+  if (!sc) load_pair_const<T>(v, pcl);
+  const PairConst<T>& pc = sc ? sc->pc : pcl;
   T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
   T cv[9], rv[9];
   for (int c = 0; c < 9; ++c) { cv[c] = (T)0; rv[c] = (T)0; }
@@ -533,16 +561,15 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
     T d[3], h;
     int k;
     bool touching = false;
-    if (pair_geometry<T>(v, S.R, a, b, delta, d, k, h)) {
+    if (pair_geometry<T>(v, S.R, a, b, delta, pc, d, k, h)) {
       T spring[3];
-      for (int x = 0; x < 3; ++x) spring[x] = (T)(rg ? rg->h[slot][x] : ph[3 * c + x]);
+      for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : (T)ph[3 * c + x];
       PairOut<T> o;
-      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, o);
+      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, pc, o);
       touching = o.touching != 0;
       for (int x = 0; x < 3; ++x) {
-        const double hv = touching ? (double)o.ht[x] : 0.0;
-        if (rg) rg->h[slot][x] = hv;
-        else ph[3 * c + x] = hv;
+        if (rg) rg->h[slot][x] = touching ? o.ht[x] : (T)0;
+        else ph[3 * c + x] = touching ? (double)o.ht[x] : 0.0;
       }
       if (i == a) {
         for (int x = 0; x < 3; ++x) { F[x] += o.Fa[x]; Tq[x] += o.Ta[x]; }
@@ -552,16 +579,34 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
           if (touching) {
             for (int x = 0; x < 3; ++x)
               for (int y = 0; y < 3; ++y) cv[3 * x + y] += (T)0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
-            double th = atan2((double)r[1], (double)r[0]);
-            const double tx = -sin(th), ty = cos(th);
-            if (th < 0.0) th += pi;
-            if (th >= pi) th -= pi;
-            int bin = (int)floor(th / dth);
+            // contact angle theta in [0, pi) and the tangential direction
+            // (-sin theta, cos theta) of the unfolded angle (Eq. 26, 27)
+            int bin;
+            double ftan;
+            if constexpr (sizeof(T) == 8) {
+              double th = atan2((double)r[1], (double)r[0]);
+              const double tx = -sin(th), ty = cos(th);
+              if (th < 0.0) th += pi;
+              if (th >= pi) th -= pi;
+              bin = (int)floor(th / dth);
+              ftan = (double)o.Fc[0] * tx + (double)o.Fc[1] * ty;
+            } else {
+              // FP32 angles: the same bins but at the edges; the direction
+              // straight from r (no trigonometry)
+              const float pf = 3.14159265358979323846f;
+              float th = atan2f((float)r[1], (float)r[0]);
+              const float rr = sqrtf((float)r[0] * (float)r[0] + (float)r[1] * (float)r[1]);
+              const float tx = rr > 0.0f ? -(float)r[1] / rr : 0.0f, ty = rr > 0.0f ? (float)r[0] / rr : 1.0f;
+              if (th < 0.0f) th += pf;
+              if (th >= pf) th -= pf;
+              bin = (int)floorf(th * ((float)v.nbins / pf));
+              ftan = (double)((float)o.Fc[0] * tx + (float)o.Fc[1] * ty);
+            }
             if (bin >= v.nbins) bin = v.nbins - 1;
             if (bin < 0) bin = 0;
             atomicAdd(v.hist + 3 * bin, 1.0);
             atomicAdd(v.hist + 3 * bin + 1, (double)o.fn);
-            atomicAdd(v.hist + 3 * bin + 2, (double)o.Fc[0] * tx + (double)o.Fc[1] * ty);
+            atomicAdd(v.hist + 3 * bin + 2, ftan);
             ++ncont;
           }
           if (v.F0 > 0.0)
@@ -572,7 +617,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
         for (int x = 0; x < 3; ++x) { F[x] -= o.Fa[x]; Tq[x] += o.Tb[x]; }
       }
     } else if (rg) {
-      rg->h[slot][0] = 0.0; rg->h[slot][1] = 0.0; rg->h[slot][2] = 0.0;
+      rg->h[slot][0] = (T)0; rg->h[slot][1] = (T)0; rg->h[slot][2] = (T)0;
     } else {
       ph[3 * c] = 0.0; ph[3 * c + 1] = 0.0; ph[3 * c + 2] = 0.0;
     }
@@ -593,7 +638,8 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
         const int c = lane + 32 * slot;
         if (m < v.K) {
           next.part[i * v.K + m] = rg ? rg->j[slot] : pj[c];
-          for (int x = 0; x < 3; ++x) next.val[3 * (i * v.K + m) + x] = rg ? rg->h[slot][x] : ph[3 * c + x];
+          for (int x = 0; x < 3; ++x)
+            next.val[3 * (i * v.K + m) + x] = rg ? (double)rg->h[slot][x] : ph[3 * c + x];
         }
       }
       base += __popc(bal);
@@ -605,7 +651,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
   }
   __syncwarp();
   if (lane == 0) {
-    integrate_one<T>(v, i, S, F, Tq, 1.0 / v.nsub, last, sizeof(T) == 8, sc);
+    integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : 1.0 / v.nsub, last, sizeof(T) == 8, sc);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(v.step_acc + 15 + c, (double)cv[c]);
@@ -697,16 +743,16 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2};
     }
     const T dt = has ? (T)(1.0 / nsub) : (T)0;
-    PairRegs rg;
+    PairRegs<T> rg;
 #pragma unroll
     for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
       const int c = (threadIdx.x & 31) + 32 * slot;
       rg.j[slot] = 0;
-      rg.h[slot][0] = rg.h[slot][1] = rg.h[slot][2] = 0.0;
+      rg.h[slot][0] = rg.h[slot][1] = rg.h[slot][2] = (T)0;
       if (has && c < my_np) {
         const double* ph = v.ph + 3LL * i * PAIR_SLOTS;
         rg.j[slot] = v.pj[(long long)i * PAIR_SLOTS + c];
-        rg.h[slot][0] = ph[3 * c]; rg.h[slot][1] = ph[3 * c + 1]; rg.h[slot][2] = ph[3 * c + 2];
+        rg.h[slot][0] = (T)ph[3 * c]; rg.h[slot][1] = (T)ph[3 * c + 1]; rg.h[slot][2] = (T)ph[3 * c + 2];
       }
     }
     for (int sub = 0; sub < B.max_nsub; ++sub) {
