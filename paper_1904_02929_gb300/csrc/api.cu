@@ -100,7 +100,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.fb = take(19 * nc * esize(prec));
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
-  L.vacc = take(34 * 8);
+  L.vacc = take(ACC_REP * ACC_STRIDE * 8);
   L.views = take(sizeof(View));
   L.tabs = take(4 * 2 * sizeof(int));   // the one-box batch tables
   L.R = take(24 * nn); L.U = take(24 * nn); L.W = take(24 * nn);
@@ -180,10 +180,21 @@ __global__ void __launch_bounds__(64) k_finalize(Batch B) {
   const View& v = B.views[blockIdx.x];
   __shared__ double tot[34];
   // 0-5 viscous, 6-14 stresslet, 15-23 contact virial, 24 contact count,
-  // 25-33 repulsive virial
-  if (threadIdx.x < 34) tot[threadIdx.x] = v.step_acc[threadIdx.x];
+  // 25-33 repulsive virial; the replicas added in a fixed order, then cleared
+  if (threadIdx.x < 34) {
+    double* a = v.step_acc + threadIdx.x;
+    double part[ACC_REP];
+#pragma unroll
+    for (int r = 0; r < ACC_REP; ++r) part[r] = a[r * ACC_STRIDE];   // loads issued together
+    double x = 0.0;
+#pragma unroll
+    for (int r = 0; r < ACC_REP; ++r) {
+      x += part[r];
+      a[r * ACC_STRIDE] = 0.0;
+    }
+    tot[threadIdx.x] = x;
+  }
   __syncthreads();
-  if (threadIdx.x < 34) v.step_acc[threadIdx.x] = 0.0;
   if (threadIdx.x < 36) {
     // compensated time sums, one entry per thread; the viscous partials are
     // xx yy zz xy xz yz, expanded to the full 3 x 3
@@ -459,7 +470,8 @@ static void eng_release(Engine& e) {
 __global__ void k_zero_visc(Batch B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < B.nbox)
-    for (int k = 0; k < 6; ++k) B.views[b].step_acc[k] = 0.0;
+    for (int r = 0; r < ACC_REP; ++r)
+      for (int k = 0; k < 6; ++k) B.views[b].step_acc[r * ACC_STRIDE + k] = 0.0;
 }
 
 // Launch-shape tuner: times the collide-stream over the set's own boxes for
@@ -564,7 +576,8 @@ static susp_status device_status(susp* h) {
 // Rebuild the boundary links of this box from its current populations (the
 // stresslet sum they feed to the next finalisation starts again from zero).
 static void refresh_links(susp* h) {
-  cudaMemsetAsync(h->v.step_acc + 6, 0, 9 * sizeof(double), stream_of(h));
+  for (int r = 0; r < ACC_REP; ++r)
+    cudaMemsetAsync(h->v.step_acc + r * ACC_STRIDE + 6, 0, 9 * sizeof(double), stream_of(h));
   launch_links(h->prec, h->eng.B, h->v.n, stream_of(h));
 }
 

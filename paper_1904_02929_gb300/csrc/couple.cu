@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
       v.Fh[3 * i + a] = (double)acc[a];
       v.Th[3 * i + a] = (double)acc[3 + a];
     }
-    for (int a = 0; a < 9; ++a) atomicAdd(v.step_acc + 6 + a, (double)acc[6 + a]);
+    for (int a = 0; a < 9; ++a) atomicAdd(acc_rep(v, i) + 6 + a, (double)acc[6 + a]);
   }
 }
 

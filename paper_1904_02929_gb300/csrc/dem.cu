@@ -654,10 +654,10 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
     integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : 1.0 / v.nsub, last, sizeof(T) == 8, sc);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
-        atomicAdd(v.step_acc + 15 + c, (double)cv[c]);
-        if (v.F0 > 0.0) atomicAdd(v.step_acc + 25 + c, (double)rv[c]);
+        atomicAdd(acc_rep(v, i) + 15 + c, (double)cv[c]);
+        if (v.F0 > 0.0) atomicAdd(acc_rep(v, i) + 25 + c, (double)rv[c]);
       }
-      if (ncont) atomicAdd(v.step_acc + 24, (double)ncont);
+      if (ncont) atomicAdd(acc_rep(v, i) + 24, (double)ncont);
     }
   }
   __syncwarp();

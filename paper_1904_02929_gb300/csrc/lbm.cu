@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
     block_sum<TC, 6>(acc, red);
     if (threadIdx.x == 0)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) atomicAdd(v.step_acc + k, (double)acc[k]);
+      for (int k = 0; k < 6; ++k) atomicAdd(acc_rep(v, blockIdx.x) + k, (double)acc[k]);
   }
 }
 

@@ -88,6 +88,13 @@ __device__ inline double proto_increment(const Proto& s, long long t) {
   return (double)s.ny * s.gamma0 * (cos(a) - cos(b));
 }
 
+// Per-box step sums are accumulated with FP64 atomics in L2.  Hundreds of
+// blocks or warps adding to the same 34 addresses serialise on them, so each
+// adder takes one of ACC_REP replicas (on separate cache lines), chosen by its
+// block or particle index; the finalisation adds the replicas.
+constexpr int ACC_REP = 16;
+constexpr int ACC_STRIDE = 48;   // doubles per replica (34 used)
+
 // ------------------------------------------------------------ state view
 struct View {
   // lattice
@@ -103,8 +110,9 @@ struct View {
   float inv_nx_f, inv_ny_f, inv_nz_f;
   void* fa;                     // population buffers; step t reads fa when t is even
   void* fb;
-  double* step_acc;             // [34] sums of the current step: 0-5 viscous (xx yy zz xy xz yz),
-                                //  6-14 stresslet, 15-23 contact virial, 24 contacts, 25-33 repulsive
+  double* step_acc;             // [ACC_REP][ACC_STRIDE] replicas of the 34 sums of the current step:
+                                //  0-5 viscous (xx yy zz xy xz yz), 6-14 stresslet, 15-23 contact
+                                //  virial, 24 contacts, 25-33 repulsive
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
   // particles
@@ -148,6 +156,11 @@ constexpr int HSLOTS_DEV = 16;
 constexpr int BRUTE_PAIRS_MAX = 4096;
 
 enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
+
+// Replica r (taken modulo ACC_REP) of a box's step sums.
+__device__ __forceinline__ double* acc_rep(const View& v, int r) {
+  return v.step_acc + (r & (ACC_REP - 1)) * ACC_STRIDE;
+}
 
 // A set of boxes stepped together (one box for the single-box API).  Work of
 // every kernel is numbered across the boxes; the prefix tables map a global
