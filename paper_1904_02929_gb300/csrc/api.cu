@@ -687,6 +687,18 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
     double c = 2.0 * (v.eta_n + zeta) / mmin;
     v.nsub = std::max(1, (int)ceil(std::max(om, c)));
   }
+  v.dt_sub = 1.0 / v.nsub;
+  {
+    PairConst<double>& d = v.pc_d;
+    d.kn = v.kn; d.kt = v.kt; d.eta_n = v.eta_n; d.mu = v.mu; d.F0 = v.F0; d.debye = v.debye;
+    d.debye10 = 10.0 * v.debye; d.lub_cut = v.lub_cut; d.lub_delta = v.lub_delta; d.eta0 = v.eta0;
+    d.hrange = v.hrange; d.rep = v.F0 > 0.0; d.lub = v.lub_cut > 0.0;
+    PairConst<float>& f = v.pc_f;
+    f.kn = (float)d.kn; f.kt = (float)d.kt; f.eta_n = (float)d.eta_n; f.mu = (float)d.mu;
+    f.F0 = (float)d.F0; f.debye = (float)d.debye; f.debye10 = (float)d.debye10;
+    f.lub_cut = (float)d.lub_cut; f.lub_delta = (float)d.lub_delta; f.eta0 = (float)d.eta0;
+    f.hrange = (float)d.hrange; f.rep = d.rep; f.lub = d.lub;
+  }
   v.sums = (double*)(w + L.sums); v.hist = (double*)(w + L.hist);
   v.counters = (unsigned long long*)(w + L.counters);
   v.proto = (Proto*)(w + L.proto); v.err = (int*)(w + L.err);

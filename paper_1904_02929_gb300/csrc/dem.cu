@@ -134,22 +134,10 @@ struct PairOut {
   int touching;
 };
 
-// Per-box pair-force constants in the compute type, converted once instead of
-// at every pair (FP64 arithmetic and conversions are slow on this GPU).
 template <typename T>
-struct PairConst {
-  T kn, kt, eta_n, mu, F0, debye, debye10, lub_cut, lub_delta, eta0, hrange;
-  bool rep, lub;
-};
-
-template <typename T>
-__device__ inline void load_pair_const(const View& v, PairConst<T>& c) {
-  c.kn = (T)v.kn; c.kt = (T)v.kt; c.eta_n = (T)v.eta_n; c.mu = (T)v.mu;
-  c.F0 = (T)v.F0; c.debye = (T)v.debye; c.debye10 = (T)(10.0 * v.debye);
-  c.lub_cut = (T)v.lub_cut; c.lub_delta = (T)v.lub_delta; c.eta0 = (T)v.eta0;
-  c.hrange = (T)v.hrange;
-  c.rep = v.F0 > 0.0;
-  c.lub = v.lub_cut > 0.0;
+__device__ __forceinline__ void load_pair_const(const View& v, PairConst<T>& c) {
+  if constexpr (sizeof(T) == 8) c = v.pc_d;
+  else c = v.pc_f;
 }
 
 // Minimum-image displacement R_b - R_a: the centre difference is taken in
@@ -323,7 +311,7 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   }
   c.im = (T)v.inv_m[i];
   c.iI = (T)v.inv_I[i];
-  c.dt = 1.0 / v.nsub;
+  c.dt = v.dt_sub;
   load_pair_const<T>(v, c.pc);
 }
 
@@ -651,7 +639,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
   }
   __syncwarp();
   if (lane == 0) {
-    integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : 1.0 / v.nsub, last, sizeof(T) == 8, sc);
+    integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8, sc);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(acc_rep(v, i) + 15 + c, (double)cv[c]);
@@ -742,7 +730,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W};
       toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2};
     }
-    const T dt = has ? (T)(1.0 / nsub) : (T)0;
+    const T dt = has ? (T)v.dt_sub : (T)0;
     PairRegs<T> rg;
 #pragma unroll
     for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
@@ -776,7 +764,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W};
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
-      pairs_of<T>(v, i, v.pcnt[i], S, (T)(1.0 / nsub), sub == 0, sub == nsub - 1,
+      pairs_of<T>(v, i, v.pcnt[i], S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
                   spring_table(v, v.proto->t + 1), nullptr, nullptr);
     }
     if (sub + 1 < B.max_nsub) grid.sync();

@@ -95,6 +95,14 @@ __device__ inline double proto_increment(const Proto& s, long long t) {
 constexpr int ACC_REP = 16;
 constexpr int ACC_STRIDE = 48;   // doubles per replica (34 used)
 
+// Pair-force constants of a box in one compute type (built on the host in
+// both types, so that no kernel converts them per pair).
+template <typename T>
+struct PairConst {
+  T kn, kt, eta_n, mu, F0, debye, debye10, lub_cut, lub_delta, eta0, hrange;
+  bool rep, lub;   // double-layer force on (F0 > 0), lubrication on (cut-off > 0)
+};
+
 // ------------------------------------------------------------ state view
 struct View {
   // lattice
@@ -138,6 +146,9 @@ struct View {
   // physics
   double mu, kn, kt, eta_n, F0, debye, lub_delta, lub_cut, eta0, hrange;
   int nsub, quasi2d, move, nbins;
+  double dt_sub;                // 1 / nsub
+  PairConst<double> pc_d;       // the pair constants above in each compute type
+  PairConst<float> pc_f;
   // accumulators
   double* sums;                 // [4][9] Kahan sums (visc, slet, contact, repulsive) + [4][9] comps
   double* hist;                 // [3 nbins]
