@@ -131,11 +131,35 @@ __global__ void k_claim(Batch B) {
   });
 }
 
+// Band nodes of one particle collected by the scan of its bounding boxes, so
+// that their owner words are then loaded in one round by all threads instead
+// of one dependent load per scan step.  A node that finds the list full is
+// handled where the scan met it.
+constexpr int BAND_CAP = 1024;
+template <typename TC>
+struct BandList {
+  uint32_t c[BAND_CAP];   // node index (19 ncell < 2^32)
+  TC d[BAND_CAP][3];      // displacement from the particle's image centre
+  signed char k[BAND_CAP];
+  int n;
+};
+
+template <typename TC>
+__device__ __forceinline__ bool band_push(BandList<TC>& L, long long c, TC dx, TC dy, TC dz, int k) {
+  const int slot = atomicAdd(&L.n, 1);
+  if (slot >= BAND_CAP) return false;
+  L.c[slot] = (uint32_t)c;
+  L.d[slot][0] = dx; L.d[slot][1] = dy; L.d[slot][2] = dz;
+  L.k[slot] = (signed char)k;
+  return true;
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
+  __shared__ BandList<TC> L;
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
@@ -146,17 +170,15 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto), ule = pule<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  if (threadIdx.x == 0) L.n = 0;
+  __syncthreads();
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am + (TC)0.6,
-                    [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k, TC d2) {
-    // only nodes outside the mapped sphere can leave it, and only those that
-    // were inside before the move: closer than a_map + 0.5 (a particle moves
-    // less than 0.5 per step; 0.6 leaves a margin)
-    if (d2 < am * am || !(d2 < (am + (TC)0.6) * (am + (TC)0.6))) return;
+  // solid node of this particle that left the mapped sphere: fluid at rho0
+  // and the boundary velocity; the particle loses that momentum
+  auto release = [&](long long c, TC dx, TC dy, TC dz, int k) {
     if (v.owner[c] != i) return;
-    // solid node leaves the mapped sphere: fluid at rho0 and the boundary velocity
     const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)k * ule;
     const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
     const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
@@ -169,7 +191,19 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
     v.owner[c] = -1;
     acc[0] -= jx; acc[1] -= jy; acc[2] -= jz;
     acc[3] -= dy * jz - dz * jy; acc[4] -= dz * jx - dx * jz; acc[5] -= dx * jy - dy * jx;
+  };
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am + (TC)0.6,
+                    [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k, TC d2) {
+    // only nodes outside the mapped sphere can leave it, and only those that
+    // were inside before the move: closer than a_map + 0.5 (a particle moves
+    // less than 0.5 per step; 0.6 leaves a margin)
+    if (d2 < am * am || !(d2 < (am + (TC)0.6) * (am + (TC)0.6))) return;
+    if (!band_push(L, c, dx, dy, dz, k)) release(c, dx, dy, dz, k);
   });
+  __syncthreads();
+  const int n = min(L.n, BAND_CAP);
+  for (int e = threadIdx.x; e < n; e += blockDim.x)
+    release((long long)L.c[e], L.d[e][0], L.d[e][1], L.d[e][2], (int)L.k[e]);
   block_sum<TC, 6>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -184,6 +218,7 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
+  __shared__ BandList<TC> L;
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
@@ -194,13 +229,15 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   const TC am = sel<TC>(v.amap[i], (float)v.amap[i]);
   const TC delta = pdelta<TC>(v.proto);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
+  if (threadIdx.x == 0) L.n = 0;
+  __syncthreads();
   ImgBox<TC> b[3];
   particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   const TC inner = am > (TC)0.6 ? am - (TC)0.6 : (TC)0;
-  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int, TC d2) {
-    // nodes deeper than a_map - 0.6 were inside before the move (speed < 0.5)
-    if (!(d2 < am * am) || d2 < inner * inner) return;
+  // fluid node that entered the mapped sphere: solid, its momentum goes to
+  // the particle (a node held by another particle is an overlap)
+  auto claim = [&](long long c, TC dx, TC dy, TC dz) {
     const int own = v.owner[c];
     if (own == i) return;
     const int old = own == -1 ? atomicCAS(v.owner + c, -1, i) : own;
@@ -213,7 +250,15 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
     }
     acc[0] += jx; acc[1] += jy; acc[2] += jz;
     acc[3] += dy * jz - dz * jy; acc[4] += dz * jx - dx * jz; acc[5] += dx * jy - dy * jx;
+  };
+  for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am, [&](int, int, int, long long c, TC dx, TC dy, TC dz, int k, TC d2) {
+    // nodes deeper than a_map - 0.6 were inside before the move (speed < 0.5)
+    if (!(d2 < am * am) || d2 < inner * inner) return;
+    if (!band_push(L, c, dx, dy, dz, k)) claim(c, dx, dy, dz);
   });
+  __syncthreads();
+  const int n = min(L.n, BAND_CAP);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) claim((long long)L.c[e], L.d[e][0], L.d[e][1], L.d[e][2]);
   block_sum<TC, 6>(acc, red);
   if (threadIdx.x == 0) {
     for (int a = 0; a < 3; ++a) {
@@ -290,8 +335,10 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   bool overflow = false;
   for_box_cells<TC>(v, b, Rx, Ry, Rz, delta, am,
                     [&](int x, int y, int z, long long s, TC sdx, TC sdy, TC sdz, int, TC d2) {
+    // every node closer than a_map is this particle's (the node-map kernels
+    // claim exactly those, with the same d2; a node another particle holds
+    // there has raised the overlap flag), so no owner look-up here
     if (!(d2 < am * am) || d2 < inner * inner) return;
-    if (v.owner[s] != i) return;
     uint32_t m = 0;
 #pragma unroll
     for (int p = 1; p < 19; ++p) {
@@ -346,47 +393,63 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
     }
     __syncthreads();
     const int ns = s_items_n;
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      const uint32_t it = s_items[k];
-      const uint32_t w = s_node[it >> 5];
-      const int p = (int)(it & 31u);
-      const int x = (int)(w & 2047u), y = (int)((w >> 11) & 2047u), z = (int)(w >> 22);
-      int rx, ry, rz;
-      bool crossing;
-      const long long r = link_target_nr(v, pr, x, y, z, p, rx, ry, rz, crossing);
-      const int q = D3Q19::opp(p);
-      // the receiver's owner word and its population q are loaded together
-      // (the population of a solid receiver is read and discarded)
-      const int ow = v.owner[r];
-      const TC nq = S::load(f, (long long)q * v.ncell + r, wq<TC>(q) * rho0, (TC)v.inv_scale);
-      if (ow == i) continue;
-      const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
-      TC dx = (TC)rx + (TC)0.5 * cqx - Rx, dy = (TC)ry + (TC)0.5 * cqy - Ry, dz = (TC)rz + (TC)0.5 * cqz - Rz;
-      const int kimg = le_image_v(v, dx, dy, dz, delta);
-      const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)kimg * ule;
-      const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
-      const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
-      const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
-      const TC wqq = wq<TC>(q);
-      // fluid receiver: momentum exchange and the bounce-back value for the
-      // next pull; another particle's node: fluid at rest
-      TC mag;
-      if (ow < 0) {
-        const TC wall = (TC)6 * wqq * rho0 * cu;
-        mag = (TC)2 * nq - wall;
-        if (!crossing) {
-          const long long sidx = x + (long long)v.nx * (y + (long long)v.ny * z);
-          f[(long long)p * v.ncell + sidx] = S::enc(nq - wall, (TC)D3Q19::w(p) * rho0, (TC)v.scale);
-        }
-      } else {
-        mag = (TC)2 * wqq * rho0;
+    // two items per thread and pass: both receivers' loads are in flight together
+    for (int k0 = threadIdx.x; k0 < ns; k0 += 2 * blockDim.x) {
+      int x[2], y[2], z[2], p[2], rx[2], ry[2], rz[2], ow[2];
+      long long r[2];
+      bool crossing[2], live[2];
+      TC nq[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = k0 + u * (int)blockDim.x;
+        live[u] = k < ns;
+        const uint32_t it = live[u] ? s_items[k] : s_items[k0];
+        const uint32_t w = s_node[it >> 5];
+        p[u] = (int)(it & 31u);
+        x[u] = (int)(w & 2047u); y[u] = (int)((w >> 11) & 2047u); z[u] = (int)(w >> 22);
+        r[u] = link_target_nr(v, pr, x[u], y[u], z[u], p[u], rx[u], ry[u], rz[u], crossing[u]);
       }
-      const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
-      acc[0] += fx; acc[1] += fy; acc[2] += fz;
-      acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
-      acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
-      acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
-      acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        // the receiver's owner word and its population q are loaded together
+        // (the population of a solid receiver is read and discarded)
+        const int q = D3Q19::opp(p[u]);
+        ow[u] = v.owner[r[u]];
+        nq[u] = S::load(f, (long long)q * v.ncell + r[u], wq<TC>(q) * rho0, (TC)v.inv_scale);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!live[u] || ow[u] == i) continue;
+        const int q = D3Q19::opp(p[u]);
+        const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+        TC dx = (TC)rx[u] + (TC)0.5 * cqx - Rx, dy = (TC)ry[u] + (TC)0.5 * cqy - Ry,
+           dz = (TC)rz[u] + (TC)0.5 * cqz - Rz;
+        const int kimg = le_image_v(v, dx, dy, dz, delta);
+        const TC ubx = pp[3] + (pp[7] * dz - pp[8] * dy) + (TC)kimg * ule;
+        const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
+        const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
+        const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
+        const TC wqq = wq<TC>(q);
+        // fluid receiver: momentum exchange and the bounce-back value for the
+        // next pull; another particle's node: fluid at rest
+        TC mag;
+        if (ow[u] < 0) {
+          const TC wall = (TC)6 * wqq * rho0 * cu;
+          mag = (TC)2 * nq[u] - wall;
+          if (!crossing[u]) {
+            const long long sidx = x[u] + (long long)v.nx * (y[u] + (long long)v.ny * z[u]);
+            f[(long long)p[u] * v.ncell + sidx] = S::enc(nq[u] - wall, (TC)D3Q19::w(p[u]) * rho0, (TC)v.scale);
+          }
+        } else {
+          mag = (TC)2 * wqq * rho0;
+        }
+        const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
+        acc[0] += fx; acc[1] += fy; acc[2] += fz;
+        acc[3] += dy * fz - dz * fy; acc[4] += dz * fx - dx * fz; acc[5] += dx * fy - dy * fx;
+        acc[6] += dx * fx; acc[7] += dx * fy; acc[8] += dx * fz;
+        acc[9] += dy * fx; acc[10] += dy * fy; acc[11] += dy * fz;
+        acc[12] += dz * fx; acc[13] += dz * fy; acc[14] += dz * fz;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) s_items_n = 0;
