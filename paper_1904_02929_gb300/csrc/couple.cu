@@ -492,14 +492,16 @@ void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s) {
   }
 }
 
-// Node-map update after the particles moved: uncover, then cover.
+// Node-map update after the particles moved: uncover, then cover (one block
+// of 128 threads per particle: the scans are short, and smaller blocks let
+// every particle's block be resident at once on the 96^3 box).
 void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s) {
   if (nparts == 0) return;
   switch (prec) {
-    case 0: k_uncover<0><<<nparts, 256, 0, s>>>(B); k_cover<0><<<nparts, 256, 0, s>>>(B); break;
-    case 1: k_uncover<1><<<nparts, 256, 0, s>>>(B); k_cover<1><<<nparts, 256, 0, s>>>(B); break;
-    case 2: k_uncover<2><<<nparts, 256, 0, s>>>(B); k_cover<2><<<nparts, 256, 0, s>>>(B); break;
-    default: k_uncover<3><<<nparts, 256, 0, s>>>(B); k_cover<3><<<nparts, 256, 0, s>>>(B); break;
+    case 0: k_uncover<0><<<nparts, 128, 0, s>>>(B); k_cover<0><<<nparts, 128, 0, s>>>(B); break;
+    case 1: k_uncover<1><<<nparts, 128, 0, s>>>(B); k_cover<1><<<nparts, 128, 0, s>>>(B); break;
+    case 2: k_uncover<2><<<nparts, 128, 0, s>>>(B); k_cover<2><<<nparts, 128, 0, s>>>(B); break;
+    default: k_uncover<3><<<nparts, 128, 0, s>>>(B); k_cover<3><<<nparts, 128, 0, s>>>(B); break;
   }
 }
 
