@@ -72,6 +72,26 @@ def k1_traffic(workload_name: str):
         return None
 
 
+STAGE_KERNELS = {
+    "plane_moments": ("k_plane_moments_b", "hbm (two planes, tiny)"),
+    "collide_stream": ("k_collide_stream", "hbm"),
+    "particles": ("k_dem_step (all particle sub-steps, one cooperative launch)",
+                  "latency: one warp per particle, a grid barrier per sub-step, ~0.5 MB of DRAM traffic"),
+    "finalize": ("k_finalize", "latency"),
+    "node_map": ("k_uncover + k_cover", "latency: bounding-box scans per particle"),
+    "links": ("k_links", "latency: surface-shell gather per particle"),
+}
+
+
+def dominant_stage(stages: dict) -> dict:
+    """The stage that took the most time in the timed steps, its kernel(s)
+    and what bounds it."""
+    tot = sum(stages.values()) or 1.0
+    name = max(stages, key=stages.get)
+    kern, bound = STAGE_KERNELS[name]
+    return {"stage": name, "kernel": kern, "share": stages[name] / tot, "bound": bound}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -435,7 +455,8 @@ def main():
     barrier()
     clk = clocks.stop() if clocks else None
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-    k1_ms, k1_n = S.susp_profile_read(g.h)   # reads the timed region's launches only
+    stages, k1_n = S.susp_profile_stages(g.h)   # the timed region's steps only
+    k1_ms = stages["collide_stream"]
     S.susp_profile(g.h, False)
     st = S.susp_stress(g.h, S.TOTAL, g.nbins)   # raises on any device error flag
     t_max = ms
@@ -487,6 +508,8 @@ def main():
                        "launch_shape": tuned,
                        "parallelism": f"replicas{world}"},
             "particle_steps_per_s": psteps,
+            "stage_us": {k: round(1e3 * v / max(k1_n, 1), 1) for k, v in stages.items()},
+            "dominant_kernel": dominant_stage(stages),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_collide_stream<fp32>", "peak_source": peak_kind,
