@@ -156,7 +156,8 @@ __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int
   d[0] -= fnx * floor(d[0] * sel<T>(v.inv_nx_d, v.inv_nx_f) + (T)0.5);
   d[2] -= fnz * floor(d[2] * sel<T>(v.inv_nz_d, v.inv_nz_f) + (T)0.5);
   const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  const T rsum = (T)(v.rad[a] + v.rad[b]);
+  const T* pl = reinterpret_cast<const T*>(v.plb);
+  const T rsum = pl[12 * a + 9] + pl[12 * b + 9];   // radii from the compute-type copy
   const T lim = rsum + pc.hrange + (T)1e-6;
   if (!(d2 < lim * lim)) return false;   // cheap rejection before the square root
   h = sqrt(d2) - rsum;
@@ -170,7 +171,8 @@ template <typename T>
 __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
                               int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
                               const PairConst<T>& pc, PairOut<T>& o) {
-  const T ra = (T)v.rad[a], rb = (T)v.rad[b];
+  const T* pl = reinterpret_cast<const T*>(v.plb);
+  const T ra = pl[12 * a + 9], rb = pl[12 * b + 9];
   const T dist = sqrt(dot3(d, d));
   const T uab[3] = {(T)(Us[3 * a] - Us[3 * b]) - (T)k * ule, (T)(Us[3 * a + 1] - Us[3 * b + 1]),
                     (T)(Us[3 * a + 2] - Us[3 * b + 2])};
@@ -291,11 +293,22 @@ __device__ inline void write_plb(const View& v, int i, const double* R, const do
 // image velocity, the pair-force constants, and for its integration the held
 // link plus covering force and torque and the inverse mass and inertia, in
 // the compute type (the same conversions the per-sub-step path makes).
+// The integration constants of particle i for one step, in the compute type:
+// (T) F^h + (T) F^cov, (T) T^h + (T) T^cov, 1 / m, 1 / I.
+template <typename T>
+__device__ inline void integ_const(const View& v, int i, T (&k)[8]) {
+  for (int a = 0; a < 3; ++a) {
+    k[a] = (T)v.Fh[3 * i + a] + (T)v.Fcov[3 * i + a];
+    k[3 + a] = (T)v.Th[3 * i + a] + (T)v.Tcov[3 * i + a];
+  }
+  k[6] = (T)v.inv_m[i];
+  k[7] = (T)v.inv_I[i];
+}
+
 template <typename T>
 struct StepConst {
   T delta, ule;
-  T F0[3], T0[3];   // (T) F^h + (T) F^cov and (T) T^h + (T) T^cov
-  T im, iI;
+  T k[8];           // integ_const
   double dt;        // 1 / n_sub
   PairConst<T> pc;
 };
@@ -305,12 +318,7 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   const Proto* pr = v.proto;
   c.delta = (T)pr->delta;
   c.ule = (T)pr->ule;
-  for (int a = 0; a < 3; ++a) {
-    c.F0[a] = (T)v.Fh[3 * i + a] + (T)v.Fcov[3 * i + a];
-    c.T0[a] = (T)v.Th[3 * i + a] + (T)v.Tcov[3 * i + a];
-  }
-  c.im = (T)v.inv_m[i];
-  c.iI = (T)v.inv_I[i];
+  integ_const<T>(v, i, c.k);
   c.dt = v.dt_sub;
   load_pair_const<T>(v, c.pc);
 }
@@ -321,12 +329,12 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
 // Velocities are updated in precision T; positions always in FP64.
 template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
-                                     double dt, bool last, bool plb_double, const StepConst<T>* sc) {
+                                     double dt, bool last, bool plb_double, const T* k) {
   double R[3], U[3], W[3];
-  const T im = sc ? sc->im : (T)v.inv_m[i], iI = sc ? sc->iI : (T)v.inv_I[i], dtt = (T)dt;
+  const T im = k[6], iI = k[7], dtt = (T)dt;
   for (int c = 0; c < 3; ++c) {
-    const T F = (sc ? sc->F0[c] : (T)v.Fh[3 * i + c] + (T)v.Fcov[3 * i + c]) + Fp[c];
-    const T Tq = (sc ? sc->T0[c] : (T)v.Th[3 * i + c] + (T)v.Tcov[3 * i + c]) + Tp[c];
+    const T F = k[c] + Fp[c];
+    const T Tq = k[3 + c] + Tp[c];
     U[c] = (double)((T)S.U[3 * i + c] + dtt * F * im);
     W[c] = (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
   }
@@ -390,7 +398,7 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
   const double delta = v.proto->delta;
   const double skin = v.hrange + 1.0;
   int* pj = v.pj + (long long)i * PAIR_SLOTS;
-  double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+  T* ph = reinterpret_cast<T*>(v.ph) + 3LL * i * PAIR_SLOTS;   // springs in the compute type
   int base = 0;
   auto consider = [&](int j, bool valid) {
     bool take = false;
@@ -414,7 +422,7 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
             h0 = old.val[3 * (a * v.K + s)]; h1 = old.val[3 * (a * v.K + s) + 1]; h2 = old.val[3 * (a * v.K + s) + 2];
             break;
           }
-        ph[3 * c] = h0; ph[3 * c + 1] = h1; ph[3 * c + 2] = h2;
+        ph[3 * c] = (T)h0; ph[3 * c + 1] = (T)h1; ph[3 * c + 2] = (T)h2;
       }
     }
     base += __popc(bal);
@@ -476,7 +484,7 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
         const double* hv = old.val + 3 * (a * HSLOTS_DEV + hit);
         h0 = hv[0]; h1 = hv[1]; h2 = hv[2];
       }
-      ph[3 * c] = h0; ph[3 * c + 1] = h1; ph[3 * c + 2] = h2;
+      ph[3 * c] = (T)h0; ph[3 * c + 1] = (T)h1; ph[3 * c + 2] = (T)h2;
     }
     base = rbase;
   } else {
@@ -538,7 +546,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
   const double pi = 3.14159265358979323846;
   const double dth = pi / v.nbins;
   int* pj = v.pj + (long long)i * PAIR_SLOTS;
-  double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+  T* ph = reinterpret_cast<T*>(v.ph) + 3LL * i * PAIR_SLOTS;
   bool keep[PAIR_SLOTS / 32] = {};   // touching pair with i = a after this sub-step
 #pragma unroll
   for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
@@ -551,13 +559,13 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
     bool touching = false;
     if (pair_geometry<T>(v, S.R, a, b, delta, pc, d, k, h)) {
       T spring[3];
-      for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : (T)ph[3 * c + x];
+      for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : ph[3 * c + x];
       PairOut<T> o;
       pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, pc, o);
       touching = o.touching != 0;
       for (int x = 0; x < 3; ++x) {
         if (rg) rg->h[slot][x] = touching ? o.ht[x] : (T)0;
-        else ph[3 * c + x] = touching ? (double)o.ht[x] : 0.0;
+        else ph[3 * c + x] = touching ? o.ht[x] : (T)0;
       }
       if (i == a) {
         for (int x = 0; x < 3; ++x) { F[x] += o.Fa[x]; Tq[x] += o.Ta[x]; }
@@ -607,7 +615,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
     } else if (rg) {
       rg->h[slot][0] = (T)0; rg->h[slot][1] = (T)0; rg->h[slot][2] = (T)0;
     } else {
-      ph[3 * c] = 0.0; ph[3 * c + 1] = 0.0; ph[3 * c + 2] = 0.0;
+      ph[3 * c] = (T)0; ph[3 * c + 1] = (T)0; ph[3 * c + 2] = (T)0;
     }
   }
   for (int c = 0; c < 3; ++c) { F[c] = warp_sum(F[c]); Tq[c] = warp_sum(Tq[c]); }
@@ -627,7 +635,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
         if (m < v.K) {
           next.part[i * v.K + m] = rg ? rg->j[slot] : pj[c];
           for (int x = 0; x < 3; ++x)
-            next.val[3 * (i * v.K + m) + x] = rg ? (double)rg->h[slot][x] : ph[3 * c + x];
+            next.val[3 * (i * v.K + m) + x] = (double)(rg ? rg->h[slot][x] : ph[3 * c + x]);
         }
       }
       base += __popc(bal);
@@ -639,7 +647,8 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
   }
   __syncwarp();
   if (lane == 0) {
-    integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8, sc);
+    integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8,
+                     sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(acc_rep(v, i) + 15 + c, (double)cv[c]);
@@ -682,7 +691,13 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
     if (!v.move) continue;
     const int i = g - B.part_off[bx];
     const int np = collect_pairs<T>(v, i, spring_table(v, v.proto->t));
-    if ((threadIdx.x & 31) == 0) v.pcnt[i] = np;
+    if ((threadIdx.x & 31) == 0) {
+      v.pcnt[i] = np;
+      T k[8];
+      integ_const<T>(v, i, k);
+      T* dst = reinterpret_cast<T*>(v.pconst) + 8 * i;
+      for (int c = 0; c < 8; ++c) dst[c] = k[c];
+    }
     my_np = np;
   }
   bool any_odd = false;
@@ -738,9 +753,9 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       rg.j[slot] = 0;
       rg.h[slot][0] = rg.h[slot][1] = rg.h[slot][2] = (T)0;
       if (has && c < my_np) {
-        const double* ph = v.ph + 3LL * i * PAIR_SLOTS;
+        const T* ph = reinterpret_cast<const T*>(v.ph) + 3LL * i * PAIR_SLOTS;
         rg.j[slot] = v.pj[(long long)i * PAIR_SLOTS + c];
-        rg.h[slot][0] = (T)ph[3 * c]; rg.h[slot][1] = (T)ph[3 * c + 1]; rg.h[slot][2] = (T)ph[3 * c + 2];
+        rg.h[slot][0] = ph[3 * c]; rg.h[slot][1] = ph[3 * c + 1]; rg.h[slot][2] = ph[3 * c + 2];
       }
     }
     for (int sub = 0; sub < B.max_nsub; ++sub) {

@@ -139,6 +139,8 @@ struct View {
   int* pj;
   double* ph;                   // [n][PAIR_SLOTS][3]
   int* pcnt;                    // [n]
+  void* pconst;                 // [n][8] per-step constants in the compute type: F^h + F^cov,
+                                //  T^h + T^cov, 1 / m, 1 / I (written at the step start)
   // tangential-spring table: per particle a, partners b > a
   int K;
   int *hcnt0, *hpart0, *hcnt1, *hpart1;
