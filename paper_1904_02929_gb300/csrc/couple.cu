@@ -339,15 +339,25 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
     // claim exactly those, with the same d2; a node another particle holds
     // there has raised the overlap flag), so no owner look-up here
     if (!(d2 < am * am) || d2 < inner * inner) return;
+    // |s + c_p - R|^2 = d2 + 2 (s - R).c_p + |c_p|^2, with the partial sums
+    // shared between directions
+    const TC d1 = d2 + (TC)1, dd = d2 + (TC)2;
+    const TC tx = (TC)2 * sdx, ty = (TC)2 * sdy, tz = (TC)2 * sdz;
+    const TC xp = dd + tx, xm = dd - tx, yp = dd + ty, ym = dd - ty;
     uint32_t m = 0;
 #pragma unroll
     for (int p = 1; p < 19; ++p) {
-      const int ryn = y + D3Q19::cy(p);
-      bool keep = true;   // a pull across a Lees-Edwards plane is always examined
-      if (ryn >= 0 && ryn < v.ny) {
-        const TC ex = sdx + (TC)D3Q19::cx(p), ey = sdy + (TC)D3Q19::cy(p), ez = sdz + (TC)D3Q19::cz(p);
-        keep = !(ex * ex + ey * ey + ez * ez < deep);
-      }
+      const int cx = D3Q19::cx(p), cy = D3Q19::cy(p), cz = D3Q19::cz(p);
+      const int ryn = y + cy;
+      TC e2;
+      if (cx * cx + cy * cy + cz * cz == 1)
+        e2 = d1 + (cx ? (cx > 0 ? tx : -tx) : (cy ? (cy > 0 ? ty : -ty) : (cz > 0 ? tz : -tz)));
+      else if (cx)
+        e2 = (cx > 0 ? xp : xm) + (cy ? (cy > 0 ? ty : -ty) : (cz > 0 ? tz : -tz));
+      else
+        e2 = (cy > 0 ? yp : ym) + (cz > 0 ? tz : -tz);
+      // a pull across a Lees-Edwards plane is always examined
+      const bool keep = (ryn < 0 || ryn >= v.ny) || !(e2 < deep);
       if (keep) m |= 1u << p;
     }
     if (!m) return;

@@ -15,7 +15,9 @@ chunks; between chunks it
     steps run in the same launches).
 
 New boxes are created on a stream of their own while the batch's chunk runs
-on the GPU, so the set-up of arriving requests overlaps the running work.  A
+on the GPU, so the set-up of arriving requests overlaps the running work.
+After the first chunk the batch's collide-stream launch shape is tuned once
+(``susp_batch_tune``) and kept for every later membership.  A
 box's results do not depend on the company it keeps: per-node and
 per-particle arithmetic is the same alone and in a batch.
 """
@@ -76,7 +78,7 @@ class Server:
     """Continuous-batching server on the current CUDA device."""
 
     def __init__(self, hbm_budget: int, max_boxes: int = 64, chunk: int = 25,
-                 precision: str = "bf16"):
+                 precision: str = "bf16", tune: bool = True):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget)
@@ -94,6 +96,8 @@ class Server:
         self.node_steps = 0
         self.chunks = 0
         self.waits_on_memory = 0
+        self.tune = tune
+        self.launch_shape = None      # collide-stream shape from the tuner (first full chunk)
 
     # ---------------------------------------------------------------- intake
     def submit(self, req: Request) -> None:
@@ -169,6 +173,10 @@ class Server:
             for r in joining:
                 self.batch.attach(r.box, S.make_shear(**r.shear))
                 self.active.append(r)
+            if self.tune and self.launch_shape is None and self.active and n:
+                # once, between two chunks: the choice then holds for every
+                # membership (results do not depend on it)
+                self.launch_shape = self.batch.tune()
             if not self.active and not self.queue and pending:
                 time.sleep(max(0.0, pending[0].arrival - now()))
         self.wall = now()
@@ -195,6 +203,7 @@ class Server:
             "hbm_budget_bytes": self.budget,
             "peak_resident_bytes": self.peak_used,
             "admissions_deferred_on_memory": self.waits_on_memory,
+            "launch_shape": self.launch_shape,
         }
 
     def close(self) -> None:

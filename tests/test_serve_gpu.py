@@ -59,6 +59,7 @@ def test_continuous_batching_results_equal_alone(precision, tol):
     assert len(done) == 9 and rep["completed"] == 8
     assert rep["peak_resident_bytes"] <= budget
     assert rep["admissions_deferred_on_memory"] > 0
+    assert rep["launch_shape"]["tile_rows"] in (4, 8, 16)   # tuned once, mid-run
     # the failure (step 17 of 40) is reported at the first chunk boundary
     # after it happened: the request leaves with steps still to run
     assert bad.error == S.SUSP_EOVERLAP and 0 < bad.remaining <= 40 - 17
