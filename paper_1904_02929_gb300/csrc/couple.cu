@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
   if (threadIdx.x == 0) L.n = 0;
   __syncthreads();
   ImgBox<TC> b[3];
-  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)0.6, b);   // the band's outer radius
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   // solid node of this particle that left the mapped sphere: fluid at rho0
   // and the boundary velocity; the particle loses that momentum
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   if (threadIdx.x == 0) L.n = 0;
   __syncthreads();
   ImgBox<TC> b[3];
-  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am, b);   // nodes inside the mapped sphere only
   TC acc[6] = {0, 0, 0, 0, 0, 0};
   const TC inner = am > (TC)0.6 ? am - (TC)0.6 : (TC)0;
   // fluid node that entered the mapped sphere: solid, its momentum goes to
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   const TC delta = pdelta<TC>(pr), ule = pule<TC>(pr);
   const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
   ImgBox<TC> b[3];
-  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am + (TC)1, b);
+  particle_boxes<TC>(v, Rx, Ry, Rz, delta, am, b);   // solid nodes lie inside a_map
   // A link's receiver lies within sqrt(2) of its solid node, or -- across a
   // Lees-Edwards plane, where the receiver is the node whose nearest source is
   // s -- within sqrt(1.5^2 + 1) = 1.80; deeper solid nodes cannot have links.
