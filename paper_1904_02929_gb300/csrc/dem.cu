@@ -316,8 +316,8 @@ struct StepConst {
 template <typename T>
 __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   const Proto* pr = v.proto;
-  c.delta = (T)pr->delta;
-  c.ule = (T)pr->ule;
+  c.delta = sel<T>(pr->delta, pr->delta_f);
+  c.ule = sel<T>(pr->ule, pr->ule_f);
   integ_const<T>(v, i, c.k);
   c.dt = v.dt_sub;
   load_pair_const<T>(v, c.pc);
@@ -528,14 +528,29 @@ struct PairRegs {
   T h[PAIR_SLOTS / 32][3];   // (springs are exact in T: each is a T result)
 };
 
-template <typename T>
-__device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const State& S, T dt, int sample,
-                                         bool last, const SpringTable& next, const StepConst<T>* sc,
-                                         PairRegs<T>* rg) {
-  const int lane = threadIdx.x & 31;
+// Sum over the LANES lanes of a lane group (a warp or a half-warp).
+template <int LANES, typename T>
+__device__ __forceinline__ T group_sum(T x) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// One sub-step of particle i, computed by a group of LANES lanes (the whole
+// warp, or one half when a warp takes two particles; every lane of the warp
+// calls this together).  valid = false: the group has no particle this time
+// and only takes part in the shuffles.
+template <typename T, int LANES>
+__device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool valid, const State& S, T dt,
+                                         int sample, bool last, const SpringTable& next,
+                                         const StepConst<T>* sc, PairRegs<T>* rg) {
+  constexpr int NS = PAIR_SLOTS / LANES;   // candidate slots per lane
+  const int lane = threadIdx.x & (LANES - 1);
+  const int grp_shift = (threadIdx.x & 31) & ~(LANES - 1);   // first lane of the group
+  if (!valid) npairs = 0;
   const Proto* pr = v.proto;
-  const T delta = sc ? sc->delta : (T)pr->delta;
-  const T ule = sc ? sc->ule : (T)pr->ule;
+  const T delta = sc ? sc->delta : sel<T>(pr->delta, pr->delta_f);
+  const T ule = sc ? sc->ule : sel<T>(pr->ule, pr->ule_f);
   PairConst<T> pcl;
   if (!sc) load_pair_const<T>(v, pcl);
   const PairConst<T>& pc = sc ? sc->pc : pcl;
@@ -547,10 +562,10 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
   const double dth = pi / v.nbins;
   int* pj = v.pj + (long long)i * PAIR_SLOTS;
   T* ph = reinterpret_cast<T*>(v.ph) + 3LL * i * PAIR_SLOTS;
-  bool keep[PAIR_SLOTS / 32] = {};   // touching pair with i = a after this sub-step
+  bool keep[NS] = {};   // touching pair with i = a after this sub-step
 #pragma unroll
-  for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
-    const int c = lane + 32 * slot;
+  for (int slot = 0; slot < NS; ++slot) {
+    const int c = lane + LANES * slot;
     if (c >= npairs) continue;
     const int j = rg ? rg->j[slot] : pj[c];
     const int a = i < j ? i : j, b = i < j ? j : i;
@@ -618,20 +633,21 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
       ph[3 * c] = (T)0; ph[3 * c + 1] = (T)0; ph[3 * c + 2] = (T)0;
     }
   }
-  for (int c = 0; c < 3; ++c) { F[c] = warp_sum(F[c]); Tq[c] = warp_sum(Tq[c]); }
+  for (int c = 0; c < 3; ++c) { F[c] = group_sum<LANES>(F[c]); Tq[c] = group_sum<LANES>(Tq[c]); }
   if (sample) {
-    for (int c = 0; c < 9; ++c) { cv[c] = warp_sum(cv[c]); rv[c] = warp_sum(rv[c]); }
-    for (int o = 16; o > 0; o >>= 1) ncont += __shfl_xor_sync(0xffffffffu, ncont, o);
+    for (int c = 0; c < 9; ++c) { cv[c] = group_sum<LANES>(cv[c]); rv[c] = group_sum<LANES>(rv[c]); }
+    ncont = group_sum<LANES>(ncont);
   }
   if (last) {
     // touching pairs (i, b > i) in candidate order -> next step's table
     int base = 0;
 #pragma unroll
-    for (int slot = 0; slot < PAIR_SLOTS / 32; ++slot) {
-      const unsigned bal = __ballot_sync(0xffffffffu, keep[slot]);
+    for (int slot = 0; slot < NS; ++slot) {
+      const unsigned all = __ballot_sync(0xffffffffu, keep[slot]);
+      const unsigned bal = LANES == 32 ? all : (all >> grp_shift) & ((1u << (LANES & 31)) - 1u);
       if (keep[slot]) {
         const int m = base + __popc(bal & ((1u << lane) - 1u));
-        const int c = lane + 32 * slot;
+        const int c = lane + LANES * slot;
         if (m < v.K) {
           next.part[i * v.K + m] = rg ? rg->j[slot] : pj[c];
           for (int x = 0; x < 3; ++x)
@@ -640,13 +656,13 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, const
       }
       base += __popc(bal);
     }
-    if (lane == 0) {
+    if (lane == 0 && valid) {
       next.cnt[i] = base < v.K ? base : v.K;
       if (base > v.K) atomicOr(v.err, ERR_PAIRS);
     }
   }
   __syncwarp();
-  if (lane == 0) {
+  if (lane == 0 && valid) {
     integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8,
                      sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i);
     if (sample) {
@@ -762,25 +778,35 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       if (has && sub < nsub) {
         // sub-step s reads A when (nsub - s) is even, so the last write lands in A
         const State& S = ((nsub - sub) & 1) ? toA : toB;
-        pairs_of<T>(v, i, my_np, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg);
+        pairs_of<T, 32>(v, i, my_np, true, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg);
       }
       if (sub + 1 < B.max_nsub) grid.sync();
     }
     return;
   }
+  // Many particles per warp: two at a time, one per half-warp (16 lanes and
+  // four candidate slots each), so that two latency chains run per warp.  The
+  // halves take other particles than the candidate search did: one grid
+  // barrier first.
+  if (!any_odd) grid.sync();
   for (int sub = 0; sub < B.max_nsub; ++sub) {
-    for (int g = gwarp; g < ntot; g += nwarps) {
-      const int bx = box_of(B.part_off, B.nbox, g);
+    for (int gp = gwarp; 2 * gp < ntot; gp += nwarps) {
+      const int g = 2 * gp + ((threadIdx.x >> 4) & 1);
+      int bx = 0, i = 0;
+      bool valid = g < ntot;
+      if (valid) {
+        bx = box_of(B.part_off, B.nbox, g);
+        i = g - B.part_off[bx];
+      }
       const View& v = B.views[bx];
       const int nsub = v.nsub;
-      if (!v.move || sub >= nsub) continue;
-      const int i = g - B.part_off[bx];
+      valid = valid && v.move && sub < nsub;
       // sub-step s reads A when (nsub - s) is even, so the last write lands in A
       const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W};
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
-      pairs_of<T>(v, i, v.pcnt[i], S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
-                  spring_table(v, v.proto->t + 1), nullptr, nullptr);
+      pairs_of<T, 16>(v, i, valid ? v.pcnt[i] : 0, valid, S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
+                      spring_table(v, v.proto->t + 1), nullptr, nullptr);
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }

@@ -153,3 +153,31 @@ def test_batch_state_errors():
     batch.close()
     a.step(2, S.make_shear(kind=0, rate=1e-3))
     assert a.time()[0] == 2
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_many_particles_per_warp(precision, tol):
+    """Four 96^3 boxes at phi_3 = 0.50 (3528 particles, more than the
+    particle kernel's resident warps): the batch takes the path that steps two
+    particles per warp, the boxes alone the one-particle-per-warp path.  Only
+    the order of the per-particle force sums differs."""
+    ws = [I.config_dst(seed=1002 + k, phi3=0.50, precision=precision) for k in range(4)]
+    assert sum(w.n for w in ws) > 3000
+
+    def make(w):
+        return S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision=precision, **w.params)
+
+    alone = [make(w) for w in ws]
+    mixed = [make(w) for w in ws]
+    batch = S.Batch(len(ws))
+    for w, g in zip(ws, mixed):
+        batch.attach(g, S.make_shear(**w.shear))
+    batch.step(8)
+    for w, g in zip(ws, alone):
+        g.step(8, S.make_shear(**w.shear))
+    assert all(e == 0 for e in batch.errors())
+    for a, m in zip(alone, mixed):
+        _assert_same(m, a, tol)
+    batch.close()
+    for g in alone + mixed:
+        g.close()
