@@ -152,6 +152,32 @@ def test_dense_contacts_lubrication_repulsion_fp64():
     assert hg[:, 0].sum() > 0, "the run should have contacts"
 
 
+def test_cell_list_and_two_particles_per_warp_fp64():
+    """More than 4096 particles in one box: candidates come from the
+    counting-sort cell list, and (FP64 keeps the particle kernel at two
+    resident blocks per SM) each warp steps two particles per sub-step.
+    Monodisperse a = 2.5 at phi_3 ~ 0.33 in 96^3, sheared."""
+    box = (96, 96, 96)
+    n = 4500
+    r = np.full(n, 2.5)
+    pos = I.place_spheres(box, r, seed=51, min_gap=0.05)
+    vel = np.random.default_rng(52).normal(0, 2e-3, (n, 3))
+    kw = dict(tau=1.0, kn=1e3, kt_ratio=0.5, mu=1.0, F0=0.2, debye=0.05, lub_delta=0.025,
+              lub_cut=0.5, a_map_ratio=0.95, nbins=36)
+    g, o = _both(*box, r, pos, vel=vel, **kw)
+    _step(g, o, 6, kind=0, rate=1e-3)
+    assert o.error() == 0
+    Rg, _, _ = g.particles()
+    Ro, _, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+    for kind in (S.CONTACT, S.TOTAL):
+        sg, _ = g.stress(kind)
+        so, _ = o.stress(kind)
+        assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
+
+
 def test_quasi2d_oscillatory_fp64():
     """Monolayer at the paper's resolution (radii 5 / 7, L_z = 4 a_max, Sec. 4.1)."""
     box = (64, 64, 28)
