@@ -19,6 +19,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -97,7 +98,9 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.p = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to $SUSP_CLOCKS_DIR (default: the temp directory)
+        out_dir = os.environ.get("SUSP_CLOCKS_DIR") or tempfile.gettempdir()
+        self.out = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
