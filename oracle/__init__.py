@@ -90,6 +90,8 @@ def lib():
         L.orc_stress.restype = C.c_int
         L.orc_stress.argtypes = [C.c_void_p, C.c_int, _D, _D, C.c_int]
         L.orc_stress_reset.argtypes = [C.c_void_p]
+        L.orc_moduli.restype = C.c_int
+        L.orc_moduli.argtypes = [C.c_void_p, C.c_double, _D, _D]
         L.orc_lattice.argtypes = [C.POINTER(C.c_int), _D, C.POINTER(C.c_int)]
         L.orc_equilibrium.argtypes = [C.c_double, _D, _D]
         L.orc_contact.restype = C.c_int
@@ -286,3 +288,9 @@ class Oracle:
 
     def stress_reset(self):
         lib().orc_stress_reset(self.h)
+
+    def moduli(self, gamma0):
+        """(G', G'') of Eq. 17, 18 over the steps since the last reset."""
+        gp, gpp = np.zeros(1), np.zeros(1)
+        assert lib().orc_moduli(self.h, float(gamma0), _ptr(gp), _ptr(gpp)) == 0
+        return float(gp[0]), float(gpp[0])

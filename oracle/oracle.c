@@ -90,6 +90,9 @@ struct orc_sim {
   double delta, delta_c;
   /* stress sums */
   double s_visc[9], s_slet[9], s_cont[9], s_rep[9];
+  /* Eq. 17, 18: sums over the steps of the step's shear stress sigma_xy
+   * (total, times V) weighted by cos and sin of omega (t + 1/2) + Theta */
+  double s_gc, s_gs;
   double *hist;
   long nsamples, ncontacts;
   int err;
@@ -728,8 +731,15 @@ static void particles_step(orc_sim *s, double delta, double ule, double delta_ne
 
 /* ---------------- one full step ------------------------------------------ */
 
+/* Total shear stress sigma_xy of the sums so far, times V (the stresslet
+ * symmetrised; the contact and double-layer virials enter with a minus). */
+static double sigma_xy_sum(const orc_sim *s) {
+  return s->s_visc[1] + 0.5 * (s->s_slet[1] + s->s_slet[3]) - s->s_cont[1] - s->s_rep[1];
+}
+
 int orc_step(orc_sim *s, int nsteps, const orc_shear *sh) {
   for (int it = 0; it < nsteps; ++it) {
+    const double sxy_before = sigma_xy_sum(s);
     double delta = s->delta;
     double ule = orc_le_increment(sh, s->t, s->ny);
     double dn = s->delta, dc = s->delta_c;
@@ -747,16 +757,41 @@ int orc_step(orc_sim *s, int nsteps, const orc_shear *sh) {
     node_map_update(s, dn, ule_next);
     double *tmp = s->fA; s->fA = s->fB; s->fB = tmp;
     s->delta = dn; s->delta_c = dc;
+    /* the step t -> t+1 shears by gamma(t+1) - gamma(t): its stress belongs
+     * to the midpoint t + 1/2 of the protocol's phase */
+    {
+      const double sxy = sigma_xy_sum(s) - sxy_before;
+      const double om = sh->kind == 1 ? sh->omega : 0.0, th = sh->kind == 1 ? sh->theta : 0.0;
+      const double ph = om * ((double)s->t + 0.5) + th;
+      s->s_gc += sxy * cos(ph);
+      s->s_gs += sxy * sin(ph);
+    }
     s->t += 1;
     s->nsamples += 1;
   }
   return s->err;
 }
 
+/* Storage and loss moduli, Eq. 17 and 18, over the steps since the last
+ * reset (a whole number of periods): the integral over one period divided by
+ * 2 pi / omega is twice the time average, so G' = -2 <sigma_xy cos> / gamma0
+ * and G'' = 2 <sigma_xy sin> / gamma0, the average over the window's steps. */
+int orc_moduli(const orc_sim *s, double gamma0, double *Gp, double *Gpp) {
+  *Gp = *Gpp = 0.0;
+  if (!(gamma0 > 0.0)) return -1;
+  if (s->nsamples == 0) return 0;
+  const double V = (double)s->nx * s->ny * s->nz;
+  const double norm = 1.0 / (V * (double)s->nsamples);
+  *Gp = -2.0 * norm * s->s_gc / gamma0;
+  *Gpp = 2.0 * norm * s->s_gs / gamma0;
+  return 0;
+}
+
 /* ---------------- stress (Eq. 12, 14, 15, 26, 27) ------------------------ */
 
 void orc_stress_reset(orc_sim *s) {
   for (int k = 0; k < 9; ++k) { s->s_visc[k] = s->s_slet[k] = s->s_cont[k] = s->s_rep[k] = 0.0; }
+  s->s_gc = s->s_gs = 0.0;
   for (int b = 0; b < 3 * s->nbins; ++b) s->hist[b] = 0.0;
   s->nsamples = 0;
   s->ncontacts = 0;

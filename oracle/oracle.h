@@ -80,6 +80,10 @@ void orc_get_hydro(const orc_sim *s, double *F, double *T); /* link sums of the 
 void orc_get_pending(const orc_sim *s, double *F, double *T);
 int orc_stress(const orc_sim *s, int kind, double out[9], double *hist, int nbins);
 void orc_stress_reset(orc_sim *s);
+/* Storage and loss moduli (Eq. 17, 18) of the total shear stress over the
+ * steps since the last reset, for strain amplitude gamma0 (the window should
+ * hold whole periods of the oscillatory protocol).  -1 if gamma0 <= 0. */
+int orc_moduli(const orc_sim *s, double gamma0, double *Gp, double *Gpp);
 
 /* ---- component routines (used by the step; exposed for the pins) ---- */
 void orc_lattice(int c[19][3], double w[19], int opp[19]);

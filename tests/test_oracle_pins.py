@@ -437,3 +437,25 @@ def test_histogram_of_a_single_contact():
     n = np.array([math.cos(th), math.sin(th), 0.0])
     expect = -np.outer(r * n, kn * 0.1 * n) / 40 ** 3
     np.testing.assert_allclose(sig, expect, rtol=1e-8, atol=1e-18)
+
+
+# ------------------------------------------------------- moduli (Eq. 17, 18)
+@pytest.mark.parametrize("theta", [0.0, math.pi / 2, 0.7])
+def test_moduli_of_a_newtonian_fluid(theta):
+    """A particle-free Lees-Edwards box is a Newtonian fluid: its volume-mean
+    shear stress is eta0 * gamma_dot(t) at every step (the mean velocity
+    gradient is the plane's velocity jump over L_y), so Eq. 17, 18 give
+    G'' = eta0 omega and G' = 0 over whole periods, for any phase Theta.
+    A phase taken at t instead of t + 1/2, a swapped cos / sin or a lost
+    factor 2 fails this."""
+    P = 2000
+    om, g0, tau = 2 * math.pi / P, 0.05, 1.0
+    o = O.Oracle(4, 8, 4, tau=tau)
+    sh = O.shear(kind=1, gamma0=g0, omega=om, theta=theta)
+    o.step(P, sh)                       # one period to settle
+    o.stress_reset()
+    o.step(2 * P, sh)                   # two periods measured
+    gp, gpp = o.moduli(g0)
+    eta0 = (tau - 0.5) / 3.0
+    assert gpp == pytest.approx(eta0 * om, rel=1e-5)
+    assert abs(gp) < 1e-6 * eta0 * om
