@@ -130,6 +130,17 @@ susp_status susp_step(susp *h, int nsteps, const susp_shear *sh);
  * (count, sum F_nor, sum F_tan) per angular bin.  Synchronises; returns the
  * device error status (SUSP_EOVERLAP, SUSP_EUNSTABLE, SUSP_ENOMEM) if set. */
 susp_status susp_stress(susp *h, susp_stress_kind kind, double out[9], double *hist, int nbins);
+/* Storage and loss moduli of the oscillatory protocol (Eq. 17, 18):
+ *   G' = -(omega/pi) int_0^{2 pi/omega} sigma_xy(t) cos(omega t + Theta) dt / gamma0,
+ *   G'' = (omega/pi) int_0^{2 pi/omega} sigma_xy(t) sin(omega t + Theta) dt / gamma0,
+ * from the total shear stress sigma_xy (as SUSP_STRESS_TOTAL) of every step
+ * since the last susp_stress_reset, each step's stress taken at the
+ * midpoint phase omega (t + 1/2) + Theta (the step shears by
+ * gamma(t+1) - gamma(t)); the window should hold a whole number of periods.
+ * gamma0, omega and Theta are those of the box's current protocol.
+ * Synchronises.  Errors: SUSP_EINVAL (NULL), SUSP_ESTATE (no oscillatory
+ * protocol with gamma0 > 0), a device status, SUSP_ECUDA. */
+susp_status susp_moduli(susp *h, double *Gp, double *Gpp);
 
 /* Zero the stress and histogram accumulators (asynchronous). */
 susp_status susp_stress_reset(susp *h);

@@ -44,6 +44,11 @@ size_t esize(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
 size_t csize(int prec) { return prec == 0 ? 8 : 4; }
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Compensated time sums per box: 36 stress components (viscous, stresslet,
+// contact and double-layer virials, 3 x 3 each) and the two phase-weighted
+// shear-stress sums of Eq. 17, 18; followed by as many compensation terms.
+constexpr int NSUMS = 38;
+
 struct Layout {
   size_t fa, fb, owner, pm, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
@@ -128,7 +133,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.cids = take(4 * nn); L.pcell = take(4 * nn);
   L.hc0 = take(4 * nn); L.hp0 = take(4 * (size_t)nn * HSLOTS); L.hv0 = take(24 * (size_t)nn * HSLOTS);
   L.hc1 = take(4 * nn); L.hp1 = take(4 * (size_t)nn * HSLOTS); L.hv1 = take(24 * (size_t)nn * HSLOTS);
-  L.sums = take(8 * 72);
+  L.sums = take(8 * 2 * NSUMS);
   int nb = p->nbins > 0 ? p->nbins : 36;
   L.hist = take(8 * 3 * nb);
   L.counters = take(8 * 4);
@@ -194,10 +199,18 @@ __global__ void __launch_bounds__(64) k_finalize(Batch B) {
     }
     tot[threadIdx.x] = x;
   }
+  // phase of this step for Eq. 17, 18: the step t -> t+1 shears by
+  // gamma(t+1) - gamma(t), so its stress belongs to omega (t + 1/2) + Theta
+  // (read before thread 0 advances the protocol below)
+  const Proto* pr = v.proto;
+  const double om = pr->kind == 1 ? pr->omega : 0.0, th0 = pr->kind == 1 ? pr->theta : 0.0;
+  const double phase = om * ((double)pr->t + 0.5) + th0;
   __syncthreads();
-  if (threadIdx.x < 36) {
+  if (threadIdx.x < NSUMS) {
     // compensated time sums, one entry per thread; the viscous partials are
-    // xx yy zz xy xz yz, expanded to the full 3 x 3
+    // xx yy zz xy xz yz, expanded to the full 3 x 3; entries 36 and 37: the
+    // step's total shear stress sigma_xy (times V; stresslet symmetrised,
+    // virials with a minus) weighted by cos and sin of the phase
     const int k = threadIdx.x;
     double x;
     if (k < 9) {
@@ -205,9 +218,13 @@ __global__ void __launch_bounds__(64) k_finalize(Batch B) {
       x = tot[vmap[k]];
     } else if (k < 18) x = tot[6 + (k - 9)];
     else if (k < 27) x = v.move ? tot[15 + (k - 18)] : 0.0;
-    else x = v.move ? tot[25 + (k - 27)] : 0.0;
+    else if (k < 36) x = v.move ? tot[25 + (k - 27)] : 0.0;
+    else {
+      const double sxy = tot[3] + 0.5 * (tot[7] + tot[9]) - (v.move ? tot[16] + tot[26] : 0.0);
+      x = sxy * (k == 36 ? cos(phase) : sin(phase));
+    }
     double* S = v.sums;
-    double* Cc = v.sums + 36;
+    double* Cc = v.sums + NSUMS;
     const double y = x - Cc[k];
     const double t = S[k] + y;
     Cc[k] = (t - S[k]) - y;
@@ -785,7 +802,7 @@ susp_status susp_step(susp* h, int nsteps, const susp_shear* sh) {
 susp_status susp_stress_reset(susp* h) {
   if (!h) return fail(SUSP_EINVAL, "NULL handle");
   cudaStream_t s = stream_of(h);
-  cudaMemsetAsync(h->v.sums, 0, 8 * 72, s);
+  cudaMemsetAsync(h->v.sums, 0, 8 * 2 * NSUMS, s);
   cudaMemsetAsync(h->v.hist, 0, 8 * 3 * h->v.nbins, s);
   cudaMemsetAsync(h->v.counters, 0, 8 * 2, s);
   return cuda_check(cudaGetLastError(), "stress reset");
@@ -795,7 +812,7 @@ susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* h
   if (!h || !out) return fail(SUSP_EINVAL, "NULL argument");
   susp_status st = device_status(h);
   if (st) return st;
-  double sums[72];
+  double sums[NSUMS];
   unsigned long long cnt[2];
   std::vector<double> hs(3 * h->v.nbins);
   cudaMemcpy(sums, h->v.sums, sizeof sums, cudaMemcpyDeviceToHost);
@@ -850,6 +867,28 @@ susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* h
     }
     default: return fail(SUSP_EINVAL, "bad stress kind");
   }
+  return SUSP_OK;
+}
+
+susp_status susp_moduli(susp* h, double* Gp, double* Gpp) {
+  if (!h || !Gp || !Gpp) return fail(SUSP_EINVAL, "NULL argument");
+  *Gp = *Gpp = 0.0;
+  if (!h->have_shear || h->shear.kind != 1 || !(h->shear.gamma0 > 0.0))
+    return fail(SUSP_ESTATE, "moduli need an oscillatory protocol with gamma0 > 0");
+  susp_status st = device_status(h);
+  if (st) return st;
+  double sums[NSUMS];
+  unsigned long long cnt[2];
+  cudaMemcpy(sums, h->v.sums, sizeof sums, cudaMemcpyDeviceToHost);
+  cudaMemcpy(cnt, h->v.counters, sizeof cnt, cudaMemcpyDeviceToHost);
+  st = cuda_check(cudaGetLastError(), "read moduli sums");
+  if (st) return st;
+  if (cnt[0] == 0) return SUSP_OK;
+  // the period integral times omega / pi is twice the window's time average
+  const double V = (double)h->v.nx * h->v.ny * h->v.nz;
+  const double norm = 1.0 / (V * (double)cnt[0]);
+  *Gp = -2.0 * norm * sums[36] / h->shear.gamma0;
+  *Gpp = 2.0 * norm * sums[37] / h->shear.gamma0;
   return SUSP_OK;
 }
 

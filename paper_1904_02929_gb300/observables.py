@@ -1,0 +1,51 @@
+"""Derived observables of the paper, computed on the host from what the
+library returns (time-averaged stress tensors, moduli).  No method arithmetic
+of the step lives here.
+
+* ``stress_anisotropy``: Delta lambda = sigma_1 - sigma_3 (largest minus
+  smallest eigenvalue of the stress tensor) and P = -(sigma_1 + sigma_2 +
+  sigma_3) / 3, with their ratio (Sec. 3.3).
+* ``reduced_shear_rate``: gamma_dot* = 6 pi eta0 a_min^2 gamma_dot / F0
+  (Sec. 3.2).
+* ``relative_viscosity``: eta / eta0 = sigma_xy / (eta0 gamma_dot) under a
+  constant rate.
+* ``dimensionless_moduli``: G'* = G' / kn, G''* = G'' / kn and
+  eta* = G''* / (omega tau_c) (Sec. 4.1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def solvent_viscosity(tau: float, rho0: float = 1.0) -> float:
+    """Lattice-Boltzmann shear viscosity eta0 = rho0 (tau - 1/2) / 3."""
+    return rho0 * (tau - 0.5) / 3.0
+
+
+def stress_anisotropy(sigma) -> tuple[float, float, float]:
+    """(Delta lambda, P, Delta lambda / P) of a 3 x 3 stress tensor (its
+    symmetric part; eigenvalues sorted sigma_1 >= sigma_2 >= sigma_3)."""
+    s = np.asarray(sigma, dtype=float).reshape(3, 3)
+    ev = np.linalg.eigvalsh(0.5 * (s + s.T))[::-1]
+    dl = float(ev[0] - ev[2])
+    p = float(-ev.sum() / 3.0)
+    return dl, p, (dl / p if p != 0.0 else math.inf)
+
+
+def reduced_shear_rate(rate: float, eta0: float, a_min: float, F0: float) -> float:
+    """gamma_dot* = 6 pi eta0 a_min^2 gamma_dot / F0."""
+    return 6.0 * math.pi * eta0 * a_min * a_min * rate / F0
+
+
+def relative_viscosity(sigma_xy: float, rate: float, eta0: float) -> float:
+    """Apparent viscosity over the solvent's, eta / eta0 = sigma_xy / (eta0 gamma_dot)."""
+    return sigma_xy / (eta0 * rate)
+
+
+def dimensionless_moduli(Gp: float, Gpp: float, kn: float, omega: float,
+                         tau_c: float) -> tuple[float, float, float]:
+    """(G'*, G''*, eta*) = (G' / kn, G'' / kn, (G'' / kn) / (omega tau_c))."""
+    gps, gpps = Gp / kn, Gpp / kn
+    return gps, gpps, gpps / (omega * tau_c)

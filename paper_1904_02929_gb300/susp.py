@@ -108,6 +108,8 @@ def library() -> C.CDLL:
                                               C.c_void_p]
         L.susp_set_graphs.restype = C.c_int
         L.susp_set_graphs.argtypes = [C.c_void_p, C.c_int]
+        L.susp_moduli.restype = C.c_int
+        L.susp_moduli.argtypes = [C.c_void_p, _D, _D]
         for name in ("susp_tune", "susp_batch_tune"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]
@@ -278,6 +280,13 @@ def susp_fluid_step_noalloc(nx, ny, nz, tau, delta, u_le, f_in_ptr, f_out_ptr, v
 
 def susp_set_graphs(h, enable: bool) -> None:
     _check(library().susp_set_graphs(h, int(bool(enable))), "susp_set_graphs")
+
+
+def susp_moduli(h):
+    """(G', G'') of Eq. 17, 18 over the steps since the last stress reset."""
+    gp, gpp = C.c_double(0.0), C.c_double(0.0)
+    _check(library().susp_moduli(h, C.byref(gp), C.byref(gpp)), "susp_moduli")
+    return float(gp.value), float(gpp.value)
 
 
 def _tune(fn, handle, where):
@@ -453,6 +462,9 @@ class Suspension:
 
     def tune(self) -> dict:
         return susp_tune(self.h)
+
+    def moduli(self):
+        return susp_moduli(self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -459,3 +459,27 @@ def test_moduli_of_a_newtonian_fluid(theta):
     eta0 = (tau - 0.5) / 3.0
     assert gpp == pytest.approx(eta0 * om, rel=1e-5)
     assert abs(gp) < 1e-6 * eta0 * om
+
+
+# ------------------------------------------------- derived observables (host)
+def test_stress_anisotropy_and_scalings():
+    """Delta lambda / P (Sec. 3.3) from the eigenvalues: a diagonal tensor
+    gives its extreme entries, any rotation of it the same numbers; the
+    reduced rate and the dimensionless moduli are the printed ratios."""
+    from paper_1904_02929_gb300 import observables as X
+    d = np.diag([-1.0, -2.5, -4.0])
+    dl, p, r = X.stress_anisotropy(d)
+    assert dl == pytest.approx(3.0) and p == pytest.approx(2.5) and r == pytest.approx(1.2)
+    q, _ = np.linalg.qr(np.random.default_rng(3).normal(size=(3, 3)))
+    dl2, p2, _ = X.stress_anisotropy(q @ d @ q.T)
+    assert dl2 == pytest.approx(dl, rel=1e-12) and p2 == pytest.approx(p, rel=1e-12)
+    # simple shear stress sigma_xy = s, no normal stress: eigenvalues +s, 0, -s
+    s = 0.3
+    dl3, p3, _ = X.stress_anisotropy([[0, s, 0], [s, 0, 0], [0, 0, 0]])
+    assert dl3 == pytest.approx(2 * s) and p3 == pytest.approx(0.0, abs=1e-15)
+    eta0 = X.solvent_viscosity(1.0)
+    assert eta0 == pytest.approx(1.0 / 6.0)
+    assert X.reduced_shear_rate(1e-4, eta0, 4.0, 0.2) == pytest.approx(6 * math.pi * eta0 * 16 * 1e-4 / 0.2)
+    assert X.relative_viscosity(eta0 * 1e-3, 1e-3, eta0) == pytest.approx(1.0)
+    gps, gpps, es = X.dimensionless_moduli(2.0, 3.0, 1e3, 6e-4, 1.0 / 0.6)
+    assert (gps, gpps) == (2e-3, 3e-3) and es == pytest.approx(3e-3 / 1e-3)

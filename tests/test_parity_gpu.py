@@ -178,6 +178,41 @@ def test_cell_list_and_two_particles_per_warp_fp64():
         assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
 
 
+def test_moduli_fp64():
+    """Storage and loss moduli (Eq. 17, 18) through the C ABI against the
+    oracle: moving spheres under oscillatory shear, one period measured after
+    a warm-up period; the Newtonian limit of a particle-free box; no moduli
+    without an oscillatory protocol."""
+    w = I.config_small()
+    P, g0, th = 100, 0.05, 0.4
+    sh = dict(kind=1, gamma0=g0, omega=2 * math.pi / P, theta=th)
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, **_params(w))
+    _step(g, o, P, **sh)
+    g.stress_reset()
+    o.stress_reset()
+    _step(g, o, P, **sh)
+    gg, go = g.moduli(), o.moduli(g0)
+    scale = max(abs(go[0]), abs(go[1]))
+    assert scale > 0
+    assert abs(gg[0] - go[0]) <= 1e-9 * scale and abs(gg[1] - go[1]) <= 1e-9 * scale
+    # particle-free: G'' = eta0 omega, G' = 0
+    f = S.Suspension(4, 8, 4, precision="fp64", tau=1.0)
+    P2 = 2000
+    sh2 = S.make_shear(kind=1, gamma0=g0, omega=2 * math.pi / P2, theta=0.0)
+    f.step(P2, sh2)
+    f.stress_reset()
+    f.step(2 * P2, sh2)
+    gp, gpp = f.moduli()
+    eta0 = 0.5 / 3.0
+    assert gpp == pytest.approx(eta0 * 2 * math.pi / P2, rel=1e-5)
+    assert abs(gp) < 1e-6 * gpp
+    c = S.Suspension(8, 8, 8, precision="fp64", tau=1.0)
+    c.step(2, S.make_shear(kind=0, rate=1e-3))
+    with pytest.raises(S.SuspError) as e:
+        c.moduli()
+    assert e.value.status == S.SUSP_ESTATE
+
+
 def test_quasi2d_oscillatory_fp64():
     """Monolayer at the paper's resolution (radii 5 / 7, L_z = 4 a_max, Sec. 4.1)."""
     box = (64, 64, 28)
