@@ -51,6 +51,7 @@ class OrcParams(C.Structure):
         ("dem_substeps", C.c_int), ("quasi2d", C.c_int),
         ("move_particles", C.c_int), ("nbins", C.c_int),
         ("body_force", C.c_double * 3),
+        ("collision", C.c_int), ("tau_bulk", C.c_double),
     ]
 
 
@@ -179,7 +180,7 @@ class Oracle:
                  rho0=1.0, rho_p=1.0, mu=1.0, kn=100.0, kt_ratio=0.2, eta_n=-1.0, F0=0.0,
                  debye=0.08, lub_delta=0.04, lub_cut=0.5, a_map_ratio=0.95,
                  dem_substeps=0, quasi2d=False, move_particles=True, nbins=36,
-                 body_force=(0.0, 0.0, 0.0)):
+                 body_force=(0.0, 0.0, 0.0), collision="bgk", tau_bulk=0.0):
         self._keep = []
         radius = _vec(radius).ravel()
         n = radius.size
@@ -201,6 +202,8 @@ class Oracle:
         p.a_map_ratio, p.dem_substeps = a_map_ratio, int(dem_substeps)
         p.quasi2d, p.move_particles, p.nbins = int(quasi2d), int(move_particles), int(nbins)
         p.body_force = (C.c_double * 3)(*[float(g) for g in body_force])
+        p.collision = {"bgk": 0, "ladd": 1}[collision] if isinstance(collision, str) else int(collision)
+        p.tau_bulk = float(tau_bulk)
         self.shape = (int(nx), int(ny), int(nz))
         self.nbins = int(nbins)
         self.h = lib().orc_create(C.byref(p))

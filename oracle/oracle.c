@@ -71,6 +71,8 @@ struct orc_sim {
   int nx, ny, nz;
   long ncell;
   double tau, rho0, g[3];
+  int collision;            /* 0 BGK, 1 Ladd */
+  double tau_bulk;
   int n;
   double *rad, *amap, *mass, *inert;
   double *R, *U, *W;        /* [3n] position, velocity, angular velocity */
@@ -177,6 +179,7 @@ orc_sim *orc_create(const orc_params *p) {
   s->nx = p->nx; s->ny = p->ny; s->nz = p->nz;
   s->ncell = (long)p->nx * p->ny * p->nz;
   s->tau = p->tau; s->rho0 = p->rho0;
+  s->collision = p->collision; s->tau_bulk = p->tau_bulk > 0.0 ? p->tau_bulk : p->tau;
   for (int a = 0; a < 3; ++a) s->g[a] = p->body_force[a];
   s->n = p->n;
   int n = p->n > 0 ? p->n : 1;
@@ -501,16 +504,50 @@ static void stream_collide(orc_sim *s, double delta, double ule) {
           }
         }
         if (!(rho > 0.0)) s->err |= ORC_EUNSTABLE;
-        /* viscous stress -(1 - 1/(2 tau)) Pi^neq */
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            double peq = j[a] * j[b] / rho + (a == b ? rho / 3.0 : 0.0);
-            visc[3 * a + b] += vfac * (pi[3 * a + b] - peq);
+        if (s->collision == 1) {
+          /* Ladd's linear operator (Eq. 5 by its eigenvalues): the
+           * non-equilibrium stress relaxes with lambda = -1/tau in its
+           * traceless part and lambda_v = -1/tau_bulk in its trace, every
+           * other (ghost) mode is removed:
+           *   n*_q = n^eq_q + C^q Pi*:(c_q c_q - c_s^2 I) / (2 c_s^4),
+           *   Pi* = (1 + lambda) bar(Pi^neq) + (1 + lambda_v) tr(Pi^neq) I / 3;
+           * viscous stress -(1 + lambda/2) bar(Pi^neq) - (1 + lambda_v/2) tr I / 3 */
+          double lam = -1.0 / s->tau, lamv = -1.0 / s->tau_bulk;
+          double pneq[9], pst[9];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double peq = j[a] * j[b] / rho + (a == b ? rho / 3.0 : 0.0);
+              pneq[3 * a + b] = pi[3 * a + b] - peq;
+            }
+          double tr = pneq[0] + pneq[4] + pneq[8];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double bar = pneq[3 * a + b] - (a == b ? tr / 3.0 : 0.0);
+              double iso = a == b ? tr / 3.0 : 0.0;
+              pst[3 * a + b] = (1.0 + lam) * bar + (1.0 + lamv) * iso;
+              visc[3 * a + b] += -(1.0 + 0.5 * lam) * bar - (1.0 + 0.5 * lamv) * iso;
+            }
+          double trs = pst[0] + pst[4] + pst[8];
+          for (int q = 0; q < Q; ++q) {
+            double fe = feq1(q, rho, j);
+            double ccp = 0.0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) ccp += pst[3 * a + b] * CV[q][a] * CV[q][b];
+            double gc = s->g[0] * CV[q][0] + s->g[1] * CV[q][1] + s->g[2] * CV[q][2];
+            s->fB[q * s->ncell + c] = fe + 4.5 * weight(q) * (ccp - trs / 3.0) + 3.0 * weight(q) * gc;
           }
-        for (int q = 0; q < Q; ++q) {
-          double fe = feq1(q, rho, j);
-          double gc = s->g[0] * CV[q][0] + s->g[1] * CV[q][1] + s->g[2] * CV[q][2];
-          s->fB[q * s->ncell + c] = nq[q] - omega * (nq[q] - fe) + 3.0 * weight(q) * gc;
+        } else {
+          /* BGK: viscous stress -(1 - 1/(2 tau)) Pi^neq */
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double peq = j[a] * j[b] / rho + (a == b ? rho / 3.0 : 0.0);
+              visc[3 * a + b] += vfac * (pi[3 * a + b] - peq);
+            }
+          for (int q = 0; q < Q; ++q) {
+            double fe = feq1(q, rho, j);
+            double gc = s->g[0] * CV[q][0] + s->g[1] * CV[q][1] + s->g[2] * CV[q][2];
+            s->fB[q * s->ncell + c] = nq[q] - omega * (nq[q] - fe) + 3.0 * weight(q) * gc;
+          }
         }
       }
   for (int k = 0; k < 9; ++k) s->s_visc[k] += visc[k];

@@ -48,6 +48,8 @@ typedef struct {
   int move_particles;       /* 0: particles held (forces still computed)              */
   int nbins;                /* angular histogram bins over [0, pi)                    */
   double body_force[3];     /* uniform force density on the fluid                     */
+  int collision;            /* 0 BGK (one eigenvalue -1/tau), 1 Ladd's linear operator */
+  double tau_bulk;          /* Ladd: bulk eigenvalue -1/tau_bulk (shear: -1/tau)      */
 } orc_params;
 
 typedef struct {

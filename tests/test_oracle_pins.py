@@ -483,3 +483,82 @@ def test_stress_anisotropy_and_scalings():
     assert X.relative_viscosity(eta0 * 1e-3, 1e-3, eta0) == pytest.approx(1.0)
     gps, gpps, es = X.dimensionless_moduli(2.0, 3.0, 1e3, 6e-4, 1.0 / 0.6)
     assert (gps, gpps) == (2e-3, 3e-3) and es == pytest.approx(3e-3 / 1e-3)
+
+
+# ----------------------------------------- Ladd's linear collision operator
+def _mode_decay(collision, tau, tau_bulk, shear_wave, L=32, T=320, eps=1e-3):
+    """Decay rate and frequency of one Fourier mode of a periodic 32 x 4 x 4
+    box: a density (sound) wave along x, or a transverse velocity wave
+    u_x(y) (shear); no Lees-Edwards offset (rate 0)."""
+    from scipy.optimize import curve_fit
+    C, W, _ = O.lattice()
+    C, W = np.asarray(C, dtype=float), np.asarray(W)
+    nx, ny, nz = (L, 4, 4) if not shear_wave else (4, L, 4)
+    o = O.Oracle(nx, ny, nz, tau=tau, collision=collision, tau_bulk=tau_bulk)
+    k = 2 * np.pi / L
+    f = np.zeros((19, nz, ny, nx))
+    if shear_wave:
+        y = np.arange(ny)
+        for yy in range(ny):
+            feq = O.equilibrium(1.0, np.array([eps * np.sin(k * yy), 0.0, 0.0]))
+            f[:, :, yy, :] = np.asarray(feq)[:, None, None]
+    else:
+        x = np.arange(nx)
+        rho = 1 + eps * np.cos(k * x)
+        f[:] = W[:, None, None, None] * rho[None, None, None, :]
+    o.set_populations(f.reshape(19, -1))
+    sh = O.shear(kind=0, rate=0.0)
+    amp = []
+    for t in range(T):
+        fp = o.populations().reshape(19, nz, ny, nx)
+        if shear_wave:
+            ux = np.tensordot(C[:, 0], fp, axes=1).mean(axis=(0, 2))
+            amp.append(2.0 / ny * np.sum(ux * np.sin(k * np.arange(ny))))
+        else:
+            r = fp.sum(0).mean(axis=(0, 1))
+            amp.append(2.0 / nx * np.sum((r - 1) * np.cos(k * np.arange(nx))))
+        o.step(1, sh)
+    t, a = np.arange(T, dtype=float), np.array(amp)
+    if shear_wave:
+        g = -np.polyfit(t, np.log(a), 1)[0]
+        return g, 0.0, k
+    fn = lambda t, A, B, G, w: np.exp(-G * t) * (A * np.cos(w * t) + B * np.sin(w * t))
+    p, _ = curve_fit(fn, t, a, p0=[eps, 0.0, 0.005, k / np.sqrt(3.0)])
+    return p[2], p[3], k
+
+
+@pytest.mark.parametrize("collision,tau,tau_bulk", [("bgk", 0.8, 0.8), ("ladd", 0.8, 1.5), ("ladd", 0.7, 0.6)])
+def test_sound_damping_fixes_the_bulk_eigenvalue(collision, tau, tau_bulk):
+    """A standing sound wave oscillates at c_s k and decays at
+    k^2 (4 nu / 3 + nu_v) / 2 with nu = (tau - 1/2) / 3 and the bulk
+    viscosity nu_v = 2 (tau_v - 1/2) / 9 (BGK: tau_v = tau, so nu_v = 2 nu / 3);
+    Ladd's operator moves only the bulk part with tau_bulk."""
+    g, w, k = _mode_decay(collision, tau, tau_bulk, shear_wave=False)
+    nu = (tau - 0.5) / 3.0
+    nuv = 2.0 * ((tau if collision == "bgk" else tau_bulk) - 0.5) / 9.0
+    assert g == pytest.approx(0.5 * k * k * (4.0 * nu / 3.0 + nuv), rel=1e-2)
+    assert w == pytest.approx(k / math.sqrt(3.0), rel=1e-2)
+
+
+@pytest.mark.parametrize("tau_bulk", [0.6, 1.5])
+def test_shear_wave_decay_fixes_the_shear_eigenvalue(tau_bulk):
+    """A transverse wave u_x(y) decays at nu k^2 whatever the bulk eigenvalue."""
+    g, _, k = _mode_decay("ladd", 0.8, tau_bulk, shear_wave=True)
+    assert g == pytest.approx((0.8 - 0.5) / 3.0 * k * k, rel=1e-2)
+
+
+def test_ladd_at_tau_one_is_the_equilibrium_like_bgk():
+    """At tau = tau_bulk = 1 every non-conserved mode is removed by both
+    operators: the populations after a step are n^eq of the pulled moments,
+    the same (to rounding) for a sheared box with held spheres."""
+    from paper_1904_02929_gb300 import inputs as I
+    w = I.config_small(n=6)
+    kw = dict(w.params)
+    kw["move_particles"] = False
+    a = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, collision="bgk", **kw)
+    b = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, collision="ladd", tau_bulk=1.0, **kw)
+    sh = O.shear(kind=0, rate=2e-3)
+    a.step(5, sh)
+    b.step(5, sh)
+    fa, fb = a.populations(), b.populations()
+    assert np.abs(fa - fb).max() < 1e-14
