@@ -85,6 +85,11 @@ typedef struct {
   int nbins;                /* angular histogram bins over [0, pi) (Eq. 19-23); <= 0 selects 36    */
   double body_force[3];     /* uniform force density on the fluid (0 for shear runs)                */
   susp_precision prec;      /* population storage                                                   */
+  int collision;            /* 0: BGK, every non-conserved mode relaxed by 1/tau; 1: Ladd's linear
+                               operator (Eq. 5 by its eigenvalues): the traceless non-equilibrium
+                               stress relaxed by -1/tau, its trace by -1/tau_bulk, ghost modes
+                               removed.  Both coincide at tau = tau_bulk = 1                      */
+  double tau_bulk;          /* Ladd: bulk relaxation time (> 0.5); <= 0 selects tau                */
 } susp_params;
 
 typedef struct {

@@ -66,6 +66,8 @@ bool valid(const susp_params* p, std::string& why) {
   if ((long long)p->nx * p->ny * p->nz >= (1LL << 27)) { why = "lattice larger than 2^27 nodes"; return false; }
   if (p->nx > 2047 || p->ny > 2047 || p->nz > 1023) { why = "lattice dims must be <= 2047 x 2047 x 1023"; return false; }
   if (!(p->tau > 0.5)) { why = "tau must exceed 1/2"; return false; }
+  if (p->collision != 0 && p->collision != 1) { why = "collision must be 0 (BGK) or 1 (Ladd)"; return false; }
+  if (p->collision == 1 && p->tau_bulk > 0.0 && !(p->tau_bulk > 0.5)) { why = "tau_bulk must exceed 1/2"; return false; }
   if (!(p->rho0 > 0.0)) { why = "rho0 must be positive"; return false; }
   if (p->n < 0) { why = "n < 0"; return false; }
   if (p->n > 0 && (!p->radius || !p->pos)) { why = "radius / pos missing"; return false; }
@@ -650,6 +652,12 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.scale = (float)h->scale; v.inv_scale = (float)(1.0 / h->scale);
   v.omega_d = 1.0 / p->tau; v.vf_d = -(1.0 - 0.5 / p->tau);
   v.omega_f = (float)v.omega_d; v.vf_f = (float)v.vf_d; v.rho0_f = (float)p->rho0;
+  {
+    const double taub = p->tau_bulk > 0.0 ? p->tau_bulk : p->tau;
+    v.ladd = p->collision == 1;
+    v.ls_d = 1.0 - 1.0 / p->tau; v.lb_d = 1.0 - 1.0 / taub; v.vfb_d = -(1.0 - 0.5 / taub);
+    v.ls_f = (float)v.ls_d; v.lb_f = (float)v.lb_d; v.vfb_f = (float)v.vfb_d;
+  }
   v.inv_nx_d = 1.0 / p->nx; v.inv_ny_d = 1.0 / p->ny; v.inv_nz_d = 1.0 / p->nz;
   v.inv_nx_f = (float)v.inv_nx_d; v.inv_ny_f = (float)v.inv_ny_d; v.inv_nz_f = (float)v.inv_nz_d;
   v.fa = w + L.fa; v.fb = w + L.fb;

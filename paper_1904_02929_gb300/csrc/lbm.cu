@@ -182,8 +182,9 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   lb_collide<P>(v, fout, idx, n, acc);
 }
 
-// BGK collision (Eq. 4, 5) of one fluid node from its pulled populations n,
-// optional body force, store, viscous-stress accumulation.
+// Collision (Eq. 4, 5: BGK, or Ladd's linear operator when the box asks for
+// it) of one fluid node from its pulled populations n, optional body force,
+// store, viscous-stress accumulation.
 template <int P>
 __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* __restrict__ fout, int idx,
                                            typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6]) {
@@ -220,6 +221,60 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
   const TC base = rho - (TC)1.5 * jj * inv;
   const TC g0 = sel<TC>(v.g[0], v.g_f[0]), g1 = sel<TC>(v.g[1], v.g_f[1]), g2 = sel<TC>(v.g[2], v.g_f[2]);
   const bool hg = v.has_g != 0;
+  if (v.ladd) {
+    // Ladd's linear operator (Eq. 5 by its eigenvalues):
+    //   n*_q = n^eq_q + (9/2) C^q Pi*:(c_q c_q - I/3),
+    //   Pi* = (1 + lambda) bar(Pi^neq) + (1 + lambda_v) tr(Pi^neq) I / 3,
+    // the ghost modes removed; viscous stress -(1 + lambda/2) of the
+    // traceless and -(1 + lambda_v/2) of the isotropic non-equilibrium stress
+    const TC third = rho / (TC)3;
+    const TC nxx = pxx - jx * jx * inv - third, nyy = pyy - jy * jy * inv - third, nzz = pzz - jz * jz * inv - third;
+    const TC nxy = pxy - jx * jy * inv, nxz = pxz - jx * jz * inv, nyz = pyz - jy * jz * inv;
+    const TC ls = sel<TC>(v.ls_d, v.ls_f), lb = sel<TC>(v.lb_d, v.lb_f);
+    const TC t3 = (nxx + nyy + nzz) / (TC)3;
+    const TC sxx = ls * (nxx - t3) + lb * t3, syy = ls * (nyy - t3) + lb * t3, szz = ls * (nzz - t3) + lb * t3;
+    const TC sxy = ls * nxy, sxz = ls * nxz, syz = ls * nyz;
+    const TC st3 = (sxx + syy + szz) / (TC)3;
+    {
+      const TC w0 = (TC)D3Q19::w(0);
+      fout[idx] = S::enc(w0 * base - (TC)4.5 * w0 * st3, w0 * rho0, (TC)v.scale);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int q = 2 * k + 1;
+      const int cxq = D3Q19::cx(q), cyq = D3Q19::cy(q), czq = D3Q19::cz(q);
+      TC jc = 0, ccp = 0;
+      if (cxq) { jc += cxq > 0 ? jx : -jx; ccp += sxx; }
+      if (cyq) { jc += cyq > 0 ? jy : -jy; ccp += syy; }
+      if (czq) { jc += czq > 0 ? jz : -jz; ccp += szz; }
+      if (cxq && cyq) ccp += (TC)2 * (cxq * cyq > 0 ? sxy : -sxy);
+      if (cxq && czq) ccp += (TC)2 * (cxq * czq > 0 ? sxz : -sxz);
+      if (cyq && czq) ccp += (TC)2 * (cyq * czq > 0 ? syz : -syz);
+      const TC w = (TC)D3Q19::w(q);
+      const TC sym = w * (base + (TC)4.5 * jc * jc * inv) + (TC)4.5 * w * (ccp - st3);
+      const TC anti = (TC)3 * w * jc;
+      TC oq = sym + anti, oo = sym - anti;
+      if (hg) {
+        TC gc = 0;
+        if (cxq) gc += cxq > 0 ? g0 : -g0;
+        if (cyq) gc += cyq > 0 ? g1 : -g1;
+        if (czq) gc += czq > 0 ? g2 : -g2;
+        const TC gq = (TC)3 * w * gc;
+        oq += gq;
+        oo -= gq;
+      }
+      fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc(oq, w * rho0, (TC)v.scale);
+      fout[(uint32_t)(q + 1) * nc + (uint32_t)idx] = S::enc(oo, w * rho0, (TC)v.scale);
+    }
+    const TC vf = sel<TC>(v.vf_d, v.vf_f), vfb = sel<TC>(v.vfb_d, v.vfb_f);
+    acc[0] += vf * (nxx - t3) + vfb * t3;
+    acc[1] += vf * (nyy - t3) + vfb * t3;
+    acc[2] += vf * (nzz - t3) + vfb * t3;
+    acc[3] += vf * nxy;
+    acc[4] += vf * nxz;
+    acc[5] += vf * nyz;
+    return;
+  }
   {
     const TC fe = (TC)D3Q19::w(0) * base;
     const TC o = n[0] + omega * (fe - n[0]);

@@ -114,6 +114,9 @@ struct View {
   // per-node constants in both precisions (no FP64 arithmetic on the FP32 paths)
   double omega_d, vf_d;         // 1/tau and -(1 - 1/(2 tau))
   float omega_f, vf_f, rho0_f, g_f[3];
+  int ladd;                     // Ladd's operator instead of BGK
+  double ls_d, lb_d, vfb_d;     // Ladd: 1 + lambda, 1 + lambda_v (lambda = -1/tau, lambda_v = -1/tau_bulk),
+  float ls_f, lb_f, vfb_f;      //  and -(1 + lambda_v / 2) for the bulk viscous stress
   double inv_nx_d, inv_ny_d, inv_nz_d;   // reciprocal box lengths
   float inv_nx_f, inv_ny_f, inv_nz_f;
   void* fa;                     // population buffers; step t reads fa when t is even

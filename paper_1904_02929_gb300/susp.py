@@ -39,6 +39,7 @@ class susp_params(C.Structure):
         ("move_particles", C.c_int), ("nbins", C.c_int),
         ("body_force", C.c_double * 3),
         ("prec", C.c_int),
+        ("collision", C.c_int), ("tau_bulk", C.c_double),
     ]
 
 
@@ -364,7 +365,8 @@ def susp_last_error() -> str:
 def make_params(nx, ny, nz, radius=(), pos=(), vel=None, omega=None, tau=1.0, rho0=1.0,
                 rho_p=1.0, mu=1.0, kn=100.0, kt_ratio=0.2, eta_n=-1.0, F0=0.0, debye=0.08,
                 lub_delta=0.04, lub_cut=0.5, a_map_ratio=0.95, dem_substeps=0, quasi2d=False,
-                move_particles=True, nbins=36, body_force=(0.0, 0.0, 0.0), precision="fp32"):
+                move_particles=True, nbins=36, body_force=(0.0, 0.0, 0.0), precision="fp32",
+                collision="bgk", tau_bulk=0.0):
     """Fill a susp_params; returns (params, keepalive) — keep the second alive."""
     radius = np.ascontiguousarray(np.asarray(radius, dtype=np.float64).ravel())
     n = radius.size
@@ -390,6 +392,8 @@ def make_params(nx, ny, nz, radius=(), pos=(), vel=None, omega=None, tau=1.0, rh
     p.move_particles, p.nbins = int(bool(move_particles)), int(nbins)
     p.body_force = (C.c_double * 3)(*[float(g) for g in body_force])
     p.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.collision = {"bgk": 0, "ladd": 1}[collision] if isinstance(collision, str) else int(collision)
+    p.tau_bulk = float(tau_bulk)
     return p, keep
 
 

@@ -178,6 +178,31 @@ def test_cell_list_and_two_particles_per_warp_fp64():
         assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_ladd_operator(precision, tol):
+    """Ladd's linear operator (tau = 0.8, tau_bulk = 1.3) through the C ABI
+    against the oracle: random populations under oscillatory Lees-Edwards
+    shear, then moving spheres; populations, viscous stress and centres."""
+    nx, ny, nz = 24, 18, 10
+    kw = dict(tau=0.8, collision="ladd", tau_bulk=1.3)
+    f0 = I.random_populations(nx, ny, nz, seed=61, amplitude=0.03, weights=W_LAT)
+    g, o = _both(nx, ny, nz, precision=precision, **kw)
+    g.set_populations(f0)
+    o.set_populations(f0)
+    _step(g, o, 60, kind=1, gamma0=0.05, omega=2 * math.pi / 200, theta=0.3)
+    assert _pop_err(g, o) < tol
+    sg, _ = g.stress(S.VISCOUS)
+    so, _ = o.stress(S.VISCOUS)
+    assert np.abs(sg - so).max() <= (1e-9 if precision == "fp64" else 1e-4) * np.abs(so).max()
+    w = I.config_small()
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, precision=precision, **_params(w, **kw))
+    _step(g, o, 40, kind=0, rate=2e-3)
+    assert _pop_err(g, o) < tol
+    Rg, _, _ = g.particles()
+    Ro, _, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < (1e-9 if precision == "fp64" else 1e-4)
+
+
 def test_moduli_fp64():
     """Storage and loss moduli (Eq. 17, 18) through the C ABI against the
     oracle: moving spheres under oscillatory shear, one period measured after
