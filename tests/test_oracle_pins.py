@@ -562,3 +562,44 @@ def test_ladd_at_tau_one_is_the_equilibrium_like_bgk():
     b.step(5, sh)
     fa, fb = a.populations(), b.populations()
     assert np.abs(fa - fb).max() < 1e-14
+
+
+# ------------------------------------------- drag on a periodic sphere array
+def _hasimoto_K(c):
+    """Drag correction of a simple cubic array of spheres at volume fraction
+    c (Hasimoto's series with Sangani and Acrivos' higher terms):
+    F = 6 pi eta a U / K(c)."""
+    return (1 - 1.7601 * c ** (1 / 3) + c - 1.5593 * c ** 2 + 3.9799 * c ** (8 / 3)
+            - 3.0734 * c ** (10 / 3))
+
+
+def hasimoto_bracket(L, a, a_map, eta, U):
+    """Hasimoto drags of spheres of radius a_map and a at superficial velocity U."""
+    out = []
+    for r in (a_map, a):
+        c = 4.0 * math.pi / 3.0 * r ** 3 / L ** 3
+        out.append(6.0 * math.pi * eta * r * U / _hasimoto_K(c))
+    return out
+
+
+def test_drag_on_a_periodic_sphere_array_against_hasimoto():
+    """A held sphere in a periodic 24^3 box, the fluid driven by a uniform
+    body force: after the fast viscous modes have decayed the drag follows
+    the instantaneous superficial velocity U as for a cubic array (Stokes
+    flow is quasi-steady), and lies between Hasimoto's drags of spheres of
+    the mapped radius and of the contact radius (the bounce-back surface sits
+    between the two).  A lost factor in the momentum exchange (Eq. 6), the
+    bounce-back term (Eq. 7) or the viscosity fails this."""
+    L, a, tau, g = 24, 3.4, 1.0, 1e-6
+    o = O.Oracle(L, L, L, np.array([a]), np.array([[L / 2, L / 2, L / 2]]), tau=tau,
+                 move_particles=False, body_force=(g, 0.0, 0.0), F0=0.0, lub_cut=0.0)
+    eta = (tau - 0.5) / 3.0
+    o.step(1000, O.shear(kind=0, rate=0.0))     # 11 decay times of the slowest mode
+    F, _ = o.hydro()
+    C, _, _ = O.lattice()
+    f = o.populations().reshape(19, -1)
+    fluid = (o.owner() < 0).ravel()
+    U = (np.asarray(C, dtype=float)[:, 0] @ f)[fluid].sum() / L ** 3
+    lo, hi = hasimoto_bracket(L, a, 0.95 * a, eta, U)
+    assert 0.99 * lo < F[0, 0] < 1.01 * hi
+    assert abs(F[0, 1]) < 1e-6 * F[0, 0] and abs(F[0, 2]) < 1e-6 * F[0, 0]

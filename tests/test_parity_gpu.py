@@ -203,6 +203,25 @@ def test_ladd_operator(precision, tol):
     assert np.abs(Rg - Ro).max() < (1e-9 if precision == "fp64" else 1e-4)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_drag_on_a_periodic_sphere_array(precision):
+    """The oracle's Hasimoto pin at twice its resolution on the GPU path:
+    a held sphere of radius 6.8 in a periodic 48^3 box, fluid driven by a
+    body force; the drag lies between Hasimoto's drags for the mapped and the
+    contact radius at the measured superficial velocity."""
+    from test_oracle_pins import hasimoto_bracket
+    L, a, tau, g = 48, 6.8, 1.0, 1e-6
+    s = S.Suspension(L, L, L, np.array([a]), np.array([[L / 2, L / 2, L / 2]]), precision=precision,
+                     tau=tau, move_particles=False, body_force=(g, 0.0, 0.0), F0=0.0, lub_cut=0.0)
+    s.step(4000, S.make_shear(kind=0, rate=0.0))
+    F, _ = s.hydro()
+    f = s.populations().reshape(19, -1)
+    fluid = (s.owner() < 0).ravel()
+    U = (np.asarray(C_LAT, dtype=float)[:, 0] @ f)[fluid].sum() / L ** 3
+    lo, hi = hasimoto_bracket(L, a, 0.95 * a, (tau - 0.5) / 3.0, U)
+    assert 0.99 * lo < F[0, 0] < 1.01 * hi
+
+
 def test_moduli_fp64():
     """Storage and loss moduli (Eq. 17, 18) through the C ABI against the
     oracle: moving spheres under oscillatory shear, one period measured after
