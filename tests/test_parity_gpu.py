@@ -207,28 +207,31 @@ def test_drag_on_periodic_sphere_arrays_hasimoto():
     """Hasimoto's series over box sizes (FP64): a held sphere of radius 4.5
     in periodic boxes of 24, 32, 48 and 64, fluid driven by a body force and
     run to steady state (drag = body force on the fluid); the hydrodynamic
-    radius read from the drag through the series is the same for every box
-    within 1 % (calibrated once, it predicts the others) and is the mapped
-    radius within 3 %."""
+    radius read from the drag through the series, calibrated in the largest
+    box, predicts the boxes of 32 and 48 within 1 % (24, where a / L = 0.19,
+    within 2 %), and is the mapped radius within 3 %.  The force scales as L^-3 so that the superficial
+    velocity, hence the Reynolds number (~0.015), is the same in every box."""
     from test_oracle_pins import hasimoto_radius, _hasimoto_K
-    a, tau, g = 4.5, 1.0, 1e-6
+    a, tau = 4.5, 1.0
     eta = (tau - 0.5) / 3.0
     radii = {}
     for L in (24, 32, 48, 64):
+        g = 1e-6 * (24.0 / L) ** 3
         s = S.Suspension(L, L, L, np.array([a]), np.array([[L / 2, L / 2, L / 2]]), precision="fp64",
                          tau=tau, move_particles=False, body_force=(g, 0.0, 0.0), F0=0.0, lub_cut=0.0)
         c = 4.0 * math.pi / 3.0 * a ** 3 / L ** 3
         t_mean = L ** 3 * _hasimoto_K(c) / (6.0 * math.pi * eta * a)   # decay time of the mean flow
-        s.step(int(7 * t_mean), S.make_shear(kind=0, rate=0.0))
+        s.step(int(10 * t_mean), S.make_shear(kind=0, rate=0.0))
         F, _ = s.hydro()
         f = s.populations().reshape(19, -1)
         fluid = (s.owner() < 0).ravel()
         U = (np.asarray(C_LAT, dtype=float)[:, 0] @ f)[fluid].sum() / L ** 3
-        assert F[0, 0] == pytest.approx(g * fluid.sum(), rel=2e-3)
+        assert F[0, 0] == pytest.approx(g * fluid.sum(), rel=3e-3)
         radii[L] = hasimoto_radius(L, eta, U, F[0, 0])
         s.close()
-    r = np.array(list(radii.values()))
-    assert r.max() / r.min() - 1 < 0.01, radii
+    for L in (32, 48):
+        assert radii[L] == pytest.approx(radii[64], rel=0.01), radii
+    assert radii[24] == pytest.approx(radii[64], rel=0.02), radii
     assert radii[64] == pytest.approx(0.95 * a, rel=0.03)
 
 
