@@ -603,3 +603,20 @@ def test_drag_on_a_periodic_sphere_array_against_hasimoto():
     assert F[0, 0] == pytest.approx(g * fluid.sum(), rel=1e-4)
     assert hasimoto_radius(L, eta, U, F[0, 0]) == pytest.approx(0.95 * a, rel=0.03)
     assert abs(F[0, 1]) < 1e-6 * F[0, 0] and abs(F[0, 2]) < 1e-6 * F[0, 0]
+
+
+def test_torque_on_a_spinning_sphere():
+    """A held sphere spinning at Omega in a periodic 20^3 box: at steady
+    state the fluid exerts T = -8 pi eta0 a_h^3 Omega (the rotlet; periodic
+    images change it at O(a^3 / L^3)) with a_h the mapped radius within 3 %,
+    about the spin axis only, and no net force."""
+    L, a, tau, Om = 20, 3.4, 1.0, 1e-4
+    eta = (tau - 0.5) / 3.0
+    o = O.Oracle(L, L, L, np.array([a]), np.array([[L / 2, L / 2, L / 2]]), tau=tau,
+                 omega=np.array([[0.0, 0.0, Om]]), move_particles=False, F0=0.0, lub_cut=0.0)
+    o.step(int(10 / (eta * (2 * math.pi / L) ** 2)), O.shear(kind=0, rate=0.0))
+    F, T = o.hydro()
+    assert T[0, 2] < 0
+    a_h = (-T[0, 2] / (8 * math.pi * eta * Om)) ** (1 / 3)
+    assert a_h == pytest.approx(0.95 * a, rel=0.03)
+    assert np.abs(T[0, :2]).max() < 1e-9 * abs(T[0, 2]) and np.abs(F[0]).max() < 1e-9 * abs(T[0, 2])

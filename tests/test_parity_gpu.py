@@ -235,6 +235,26 @@ def test_drag_on_periodic_sphere_arrays_hasimoto():
     assert radii[64] == pytest.approx(0.95 * a, rel=0.03)
 
 
+def test_torque_on_a_spinning_sphere_fp64():
+    """Rotlet: a held sphere of radius 4.5 spinning in periodic boxes of 48
+    and 64 feels T = -8 pi eta0 a_h^3 Omega about its axis, a_h the mapped
+    radius within 3 % and the same in both boxes within 0.5 %."""
+    a, tau, Om = 4.5, 1.0, 1e-4
+    eta = (tau - 0.5) / 3.0
+    radii = []
+    for L in (48, 64):
+        s = S.Suspension(L, L, L, np.array([a]), np.array([[L / 2, L / 2, L / 2]]), precision="fp64",
+                         tau=tau, omega=np.array([[0.0, 0.0, Om]]), move_particles=False, F0=0.0,
+                         lub_cut=0.0)
+        s.step(int(10 / (eta * (2 * math.pi / L) ** 2)), S.make_shear(kind=0, rate=0.0))
+        F, T = s.hydro()
+        assert T[0, 2] < 0 and np.abs(T[0, :2]).max() < 1e-9 * abs(T[0, 2])
+        radii.append((-T[0, 2] / (8 * math.pi * eta * Om)) ** (1 / 3))
+        s.close()
+    assert radii[1] == pytest.approx(0.95 * a, rel=0.03)
+    assert radii[0] == pytest.approx(radii[1], rel=0.005)
+
+
 def test_moduli_fp64():
     """Storage and loss moduli (Eq. 17, 18) through the C ABI against the
     oracle: moving spheres under oscillatory shear, one period measured after
