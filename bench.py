@@ -36,6 +36,24 @@ def workload(seed_offset: int = 0, L: int = 96):
     return inputs.config_dst(seed=1002 + seed_offset, phi3=0.50, L=L, rate=1e-4, precision="fp32")
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Largest value of x over the ranks of the process group (x itself
+    without one); the tensor lives where the backend wants it."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, steps: int, t_max_ms: float) -> float:
+    """Whole-job rate in millions of units per second: every rank advanced
+    its own units (weak scaling), the slowest rank sets the time."""
+    return world * units_per_rank * steps / (t_max_ms / 1e3) / 1e6
+
+
 def peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -462,13 +480,9 @@ def main():
     k1_ms = stages["collide_stream"]
     S.susp_profile(g.h, False)
     st = S.susp_stress(g.h, S.TOTAL, g.nbins)   # raises on any device error flag
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    mlups = world * w.ncell * K / (t_max / 1e3) / 1e6
-    psteps = world * w.n * K / (t_max / 1e3)
+    t_max = max_over_ranks(ms, dist)
+    mlups = job_throughput(world, w.ncell, K, t_max)
+    psteps = job_throughput(world, w.n, K, t_max) * 1e6
 
     # --- end to end through the public API: create (host arrays up), K steps
     # each followed by the read-back of positions and stress into host memory
@@ -486,10 +500,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = (w.n * (8 + 24 + 24 + 24)) / K                # radii, positions, velocities, spins
     # pos / vel / spin, stress sums, counters, histogram and the error word of each read-back
     d2h = 3 * 24 * w.n + 72 * 8 + 2 * 8 + 3 * 8 * g.nbins + 2 * 4
