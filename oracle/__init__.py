@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
-VISCOUS, CONTACT, REPULSIVE, TOTAL, ANGULAR = range(5)
+VISCOUS, CONTACT, REPULSIVE, TOTAL, ANGULAR, LUBRICATION = range(6)
 EOVERLAP, EUNSTABLE, EHIST = 1, 2, 4
 
 
@@ -101,6 +101,8 @@ def lib():
                                   _D, _D, _D, _D, _D]
         L.orc_lubrication.argtypes = [C.c_double, C.c_double, _D, _D, _D, _D, C.c_double,
                                       C.c_double, C.c_double, _D, _D, _D]
+        L.orc_lubrication_stresslet.argtypes = [C.c_double, C.c_double, _D, _D, _D, _D, C.c_double,
+                                                C.c_double, C.c_double, _D]
         L.orc_gamma.restype = C.c_double
         L.orc_gamma.argtypes = [C.POINTER(OrcShear), C.c_double]
         L.orc_le_increment.restype = C.c_double
@@ -155,6 +157,15 @@ def lubrication(ra, rb, d, uab, wa, wb, eta0, delta, hcut):
     lib().orc_lubrication(float(ra), float(rb), _ptr(d), _ptr(uab), _ptr(wa), _ptr(wb),
                           float(eta0), float(delta), float(hcut), _ptr(Fa), _ptr(Ta), _ptr(Tb))
     return Fa, Ta, Tb
+
+
+def lubrication_stresslet(ra, rb, d, uab, wa, wb, eta0, delta, hcut):
+    """S_a + S_b of one pair (3 x 3)."""
+    S = np.zeros(9)
+    d, uab, wa, wb = _vec(d), _vec(uab), _vec(wa), _vec(wb)
+    lib().orc_lubrication_stresslet(float(ra), float(rb), _ptr(d), _ptr(uab), _ptr(wa), _ptr(wb),
+                                    float(eta0), float(delta), float(hcut), _ptr(S))
+    return S.reshape(3, 3)
 
 
 def gamma(sh: OrcShear, t: float) -> float:

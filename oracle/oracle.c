@@ -91,7 +91,7 @@ struct orc_sim {
   long t;
   double delta, delta_c;
   /* stress sums */
-  double s_visc[9], s_slet[9], s_cont[9], s_rep[9];
+  double s_visc[9], s_slet[9], s_cont[9], s_rep[9], s_lub[9];
   /* Eq. 17, 18: sums over the steps of the step's shear stress sigma_xy
    * (total, times V) weighted by cos and sin of omega (t + 1/2) + Theta */
   double s_gc, s_gs;
@@ -637,6 +637,50 @@ void orc_lubrication(double ra, double rb, const double d[3], const double uab[3
   }
 }
 
+/* Lubrication stresslet of the pair (Appendix A, G and H blocks), the same
+ * correction form and normalisation as the forces: for each sphere p of the
+ * pair, with n_p its unit normal towards the partner and a_p, beta_p = a_q /
+ * a_p its own radius and ratio,
+ *   S_p = -[ G(n_p) . (U_p - U_q) + H_pp(n_p) . Omega_p + H_pq(n_p) . Omega_q ],
+ *   G . U = X^G (n n - I/3)(n . U) + Y^G (n U + U n - 2 n n (n . U)),
+ *   H . Omega = Y^H ((Omega x n) n + n (Omega x n)).
+ * Out: S = S_a + S_b (3 x 3, symmetric and traceless). */
+void orc_lubrication_stresslet(double ra, double rb, const double d[3], const double uab[3],
+                               const double wa[3], const double wb[3], double eta0,
+                               double delta, double hcut, double S[9]) {
+  for (int k = 0; k < 9; ++k) S[k] = 0.0;
+  double dist = sqrt(dot(d, d));
+  double h = dist - ra - rb;
+  if (!(h < hcut)) return;
+  if (h < 0.0) h = 0.0;
+  double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+  double sc = 2.0 / (ra + rb);
+  double xi = sc * h, xc = sc * hcut, dl = sc * delta;
+  double inv = 1.0 / (xi + dl) - 1.0 / (xc + dl);
+  double lg = log((xc + dl) / (xi + dl));
+  double un = dot(uab, n);
+  for (int p = 0; p < 2; ++p) {
+    double ap = p == 0 ? ra : rb, be = p == 0 ? rb / ra : ra / rb;
+    const double *wp = p == 0 ? wa : wb, *wq = p == 0 ? wb : wa;
+    /* n_p = +/- n and U_p - U_q = +/- uab: the G terms are odd in each, the
+     * H terms even in n_p, so both spheres use n and uab */
+    double XG = eta0 * 4.0 * M_PI * ap * ap * (3.0 * be * be / pow(1.0 + be, 3)) * inv;
+    double YG = eta0 * 4.0 * M_PI * ap * ap * (be * (4.0 - be + 7.0 * be * be) / (10.0 * pow(1.0 + be, 3))) * lg;
+    double YHs = eta0 * 8.0 * M_PI * ap * ap * ap * (be * (2.0 - be) / (10.0 * pow(1.0 + be, 2))) * lg;
+    double YHo = eta0 * 8.0 * M_PI * ap * ap * ap * (be * be * (1.0 + 7.0 * be) / (20.0 * pow(1.0 + be, 2))) * lg;
+    double ws[3], wo[3];
+    cross(wp, n, ws);
+    cross(wq, n, wo);
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y) {
+        double g = XG * (n[x] * n[y] - (x == y ? 1.0 / 3.0 : 0.0)) * un
+                 + YG * (n[x] * uab[y] + uab[x] * n[y] - 2.0 * n[x] * n[y] * un);
+        double hh = YHs * (ws[x] * n[y] + n[x] * ws[y]) + YHo * (wo[x] * n[y] + n[x] * wo[y]);
+        S[3 * x + y] -= g + hh;
+      }
+  }
+}
+
 /* ---------------- particle sub-steps (Eq. 1) ----------------------------- */
 
 static int hist_find(const orc_sim *s, int buf, int a, int b) {
@@ -730,6 +774,12 @@ static void pair_forces(orc_sim *s, double delta, double ule, double dt, int sam
           s->Fp[3 * a + c] += Fa[c]; s->Fp[3 * b + c] -= Fa[c];
           s->Tp[3 * a + c] += Ta[c]; s->Tp[3 * b + c] += Tb[c];
         }
+        if (sample) {
+          double S[9];
+          orc_lubrication_stresslet(s->rad[a], s->rad[b], d, uab, wa, wb, s->eta0, s->lub_delta,
+                                    s->lub_cut, S);
+          for (int k = 0; k < 9; ++k) s->s_lub[k] += S[k];
+        }
       }
     }
   s->hcur = nxt;
@@ -771,7 +821,7 @@ static void particles_step(orc_sim *s, double delta, double ule, double delta_ne
 /* Total shear stress sigma_xy of the sums so far, times V (the stresslet
  * symmetrised; the contact and double-layer virials enter with a minus). */
 static double sigma_xy_sum(const orc_sim *s) {
-  return s->s_visc[1] + 0.5 * (s->s_slet[1] + s->s_slet[3]) - s->s_cont[1] - s->s_rep[1];
+  return s->s_visc[1] + 0.5 * (s->s_slet[1] + s->s_slet[3]) - s->s_cont[1] - s->s_rep[1] + s->s_lub[1];
 }
 
 int orc_step(orc_sim *s, int nsteps, const orc_shear *sh) {
@@ -827,7 +877,7 @@ int orc_moduli(const orc_sim *s, double gamma0, double *Gp, double *Gpp) {
 /* ---------------- stress (Eq. 12, 14, 15, 26, 27) ------------------------ */
 
 void orc_stress_reset(orc_sim *s) {
-  for (int k = 0; k < 9; ++k) { s->s_visc[k] = s->s_slet[k] = s->s_cont[k] = s->s_rep[k] = 0.0; }
+  for (int k = 0; k < 9; ++k) { s->s_visc[k] = s->s_slet[k] = s->s_cont[k] = s->s_rep[k] = s->s_lub[k] = 0.0; }
   s->s_gc = s->s_gs = 0.0;
   for (int b = 0; b < 3 * s->nbins; ++b) s->hist[b] = 0.0;
   s->nsamples = 0;
@@ -862,7 +912,7 @@ int orc_stress(const orc_sim *s, int kind, double out[9], double *hist, int nbin
   if (s->nsamples == 0) return 0;
   double V = (double)s->nx * s->ny * s->nz;
   double norm = 1.0 / (V * (double)s->nsamples);
-  double visc[9], cont[9], rep[9];
+  double visc[9], cont[9], rep[9], lub[9];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       int k = 3 * a + b, kt = 3 * b + a;
@@ -870,11 +920,13 @@ int orc_stress(const orc_sim *s, int kind, double out[9], double *hist, int nbin
       visc[k] = norm * (s->s_visc[k] + 0.5 * (s->s_slet[k] + s->s_slet[kt]));
       cont[k] = -norm * s->s_cont[k];
       rep[k] = -norm * s->s_rep[k];
+      lub[k] = norm * s->s_lub[k];     /* the pairs' lubrication stresslets */
     }
   if (kind == ORC_VISCOUS) memcpy(out, visc, sizeof visc);
   else if (kind == ORC_CONTACT) memcpy(out, cont, sizeof cont);
   else if (kind == ORC_REPULSIVE) memcpy(out, rep, sizeof rep);
-  else if (kind == ORC_TOTAL) for (int k = 0; k < 9; ++k) out[k] = visc[k] + cont[k] + rep[k];
+  else if (kind == ORC_LUBRICATION) memcpy(out, lub, sizeof lub);
+  else if (kind == ORC_TOTAL) for (int k = 0; k < 9; ++k) out[k] = visc[k] + cont[k] + rep[k] + lub[k];
   else if (kind == ORC_ANGULAR) {
     double asum = 0.0, vol = 0.0, area = 0.0;
     for (int i = 0; i < s->n; ++i) {

@@ -59,7 +59,8 @@ typedef struct {
 } orc_shear;
 
 /* Stress kinds, mirroring the product's enumeration by value. */
-enum { ORC_VISCOUS = 0, ORC_CONTACT = 1, ORC_REPULSIVE = 2, ORC_TOTAL = 3, ORC_ANGULAR = 4 };
+enum { ORC_VISCOUS = 0, ORC_CONTACT = 1, ORC_REPULSIVE = 2, ORC_TOTAL = 3, ORC_ANGULAR = 4,
+       ORC_LUBRICATION = 5 };
 
 /* error bits */
 enum { ORC_EOVERLAP = 1, ORC_EUNSTABLE = 2, ORC_EHIST = 4 };
@@ -105,6 +106,10 @@ void orc_lubrication(double ra, double rb, const double d[3], const double uab[3
                      const double wa[3], const double wb[3], double eta0,
                      double delta, double hcut, double Fa[3], double Ta[3],
                      double Tb[3]);
+/* Lubrication stresslet of one pair (Appendix A, G and H blocks): S = S_a + S_b. */
+void orc_lubrication_stresslet(double ra, double rb, const double d[3], const double uab[3],
+                               const double wa[3], const double wb[3], double eta0,
+                               double delta, double hcut, double S[9]);
 /* Oscillatory protocol, Eq. 16. */
 double orc_gamma(const orc_shear *sh, double t);
 /* Lees-Edwards offset increment of one step (t -> t+1) for a box of height ly. */

@@ -620,3 +620,47 @@ def test_torque_on_a_spinning_sphere():
     a_h = (-T[0, 2] / (8 * math.pi * eta * Om)) ** (1 / 3)
     assert a_h == pytest.approx(0.95 * a, rel=0.03)
     assert np.abs(T[0, :2]).max() < 1e-9 * abs(T[0, 2]) and np.abs(F[0]).max() < 1e-9 * abs(T[0, 2])
+
+
+# ------------------------------------------ lubrication stresslet (G, H blocks)
+@pytest.mark.parametrize("ra,rb,h", [(4.0, 5.6, 0.08), (5.6, 4.0, 0.01), (5.0, 5.0, 0.05), (3.0, 7.0, 0.02)])
+def test_lubrication_stresslet_vanishes_for_rigid_rotation(ra, rb, h):
+    """A pair turning as one rigid body (U_a - U_b = Omega x (R_a - R_b),
+    Omega_a = Omega_b = Omega) deforms no gap, so its near-field stresslet
+    must vanish: the printed functions satisfy Y^H_aa + Y^H_ab =
+    (a_a + a_b) Y^G_aa exactly when each sphere's beta is partner / own
+    radius (the reading the lubrication forces use), leaving only the
+    h / (a_a + a_b + h) remainder of the finite gap.  The printed beta =
+    a_i / a_j breaks this for unequal spheres."""
+    rng = np.random.default_rng(int(100 * ra + 10 * rb))
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    d = (ra + rb + h) * n
+    om = rng.normal(size=3) * 1e-3
+    uab = np.cross(om, -d)
+    S = O.lubrication_stresslet(ra, rb, d, uab, om, om, 1 / 6, 0.04, 0.5)
+    SG = O.lubrication_stresslet(ra, rb, d, uab, np.zeros(3), np.zeros(3), 1 / 6, 0.04, 0.5)
+    assert np.abs(S).max() / np.abs(SG).max() == pytest.approx(h / (ra + rb + h), rel=1e-9)
+
+
+def test_lubrication_stresslet_squeeze_and_shape():
+    """Equal spheres approaching along n: S = -2 X^G (n n - I/3)(n . U) with
+    X^G = eta0 4 pi a^2 (3/8) [1/(xi + delta) - 1/(xi_c + delta)] (the
+    correction form of the forces); any motion gives a symmetric traceless
+    stresslet; none beyond the cut-off, and it goes to zero at the cut-off."""
+    a, eta0, dlt, hc, h = 5.0, 1 / 6, 0.04, 0.5, 0.1
+    n = np.array([0.6, 0.8, 0.0])
+    u = 2e-3
+    Sq = O.lubrication_stresslet(a, a, (2 * a + h) * n, u * n, np.zeros(3), np.zeros(3), eta0, dlt, hc)
+    sc = 2.0 / (2 * a)
+    XG = eta0 * 4 * math.pi * a * a * 3.0 / 8.0 * (1 / (sc * h + sc * dlt) - 1 / (sc * hc + sc * dlt))
+    assert np.allclose(Sq, -2 * XG * (np.outer(n, n) - np.eye(3) / 3) * u, rtol=1e-12, atol=0)
+    rng = np.random.default_rng(9)
+    S = O.lubrication_stresslet(4.0, 5.6, (9.7) * n, rng.normal(size=3) * 1e-3, rng.normal(size=3) * 1e-3,
+                                rng.normal(size=3) * 1e-3, eta0, dlt, hc)
+    assert np.abs(S - S.T).max() < 1e-15 and abs(np.trace(S)) < 1e-15
+    far = O.lubrication_stresslet(a, a, (2 * a + hc + 1e-9) * n, u * n, np.zeros(3), np.zeros(3), eta0, dlt, hc)
+    assert np.abs(far).max() == 0.0
+    near_cut = O.lubrication_stresslet(a, a, (2 * a + hc - 1e-9) * n, u * n, np.zeros(3), np.zeros(3), eta0,
+                                       dlt, hc)
+    assert np.abs(near_cut).max() < 1e-7 * np.abs(Sq).max()     # linear in the distance to h_c
