@@ -104,8 +104,10 @@ typedef enum {
   SUSP_STRESS_VISCOUS = 0,  /* fluid viscous stress + particle stresslet (sigma^h, Appendix A)      */
   SUSP_STRESS_CONTACT = 1,  /* contact virial, Eq. 12                                               */
   SUSP_STRESS_REPULSIVE = 2,/* double-layer virial, Eq. 14                                          */
-  SUSP_STRESS_TOTAL = 3,    /* Eq. 15                                                               */
-  SUSP_STRESS_ANGULAR = 4   /* Eq. 26 (quasi2d) or Eq. 27 from the contact histogram                */
+  SUSP_STRESS_TOTAL = 3,    /* Eq. 15, with the lubrication stresslets                              */
+  SUSP_STRESS_ANGULAR = 4,  /* Eq. 26 (quasi2d) or Eq. 27 from the contact histogram                */
+  SUSP_STRESS_LUBRICATION = 5 /* the pairs' lubrication stresslets (Appendix A, G and H blocks, the
+                               correction form of the lubrication forces), sampled with the virials */
 } susp_stress_kind;
 
 typedef struct susp susp;

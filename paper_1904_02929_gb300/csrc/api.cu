@@ -44,10 +44,11 @@ size_t esize(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
 size_t csize(int prec) { return prec == 0 ? 8 : 4; }
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Compensated time sums per box: 36 stress components (viscous, stresslet,
-// contact and double-layer virials, 3 x 3 each) and the two phase-weighted
-// shear-stress sums of Eq. 17, 18; followed by as many compensation terms.
-constexpr int NSUMS = 38;
+// Compensated time sums per box: 45 stress components (viscous, stresslet,
+// contact and double-layer virials, lubrication stresslets, 3 x 3 each) and
+// the two phase-weighted shear-stress sums of Eq. 17, 18; followed by as
+// many compensation terms.
+constexpr int NSUMS = 47;
 
 struct Layout {
   size_t fa, fb, owner, pm, vacc, views, tabs;
@@ -185,10 +186,11 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
 // time sums and are cleared; then the protocol advances to t+1.
 __global__ void __launch_bounds__(64) k_finalize(Batch B) {
   const View& v = B.views[blockIdx.x];
-  __shared__ double tot[34];
+  __shared__ double tot[40];
   // 0-5 viscous, 6-14 stresslet, 15-23 contact virial, 24 contact count,
-  // 25-33 repulsive virial; the replicas added in a fixed order, then cleared
-  if (threadIdx.x < 34) {
+  // 25-33 repulsive virial, 34-39 lubrication stresslets (xx yy zz xy xz yz);
+  // the replicas added in a fixed order, then cleared
+  if (threadIdx.x < 40) {
     double* a = v.step_acc + threadIdx.x;
     double part[ACC_REP];
 #pragma unroll
@@ -209,21 +211,22 @@ __global__ void __launch_bounds__(64) k_finalize(Batch B) {
   const double phase = om * ((double)pr->t + 0.5) + th0;
   __syncthreads();
   if (threadIdx.x < NSUMS) {
-    // compensated time sums, one entry per thread; the viscous partials are
-    // xx yy zz xy xz yz, expanded to the full 3 x 3; entries 36 and 37: the
-    // step's total shear stress sigma_xy (times V; stresslet symmetrised,
-    // virials with a minus) weighted by cos and sin of the phase
+    // compensated time sums, one entry per thread; the viscous and
+    // lubrication partials are xx yy zz xy xz yz, expanded to the full
+    // 3 x 3; entries 45 and 46: the step's total shear stress sigma_xy
+    // (times V; stresslet symmetrised, virials with a minus) weighted by cos
+    // and sin of the phase
     const int k = threadIdx.x;
+    const int vmap[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
     double x;
-    if (k < 9) {
-      const int vmap[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
-      x = tot[vmap[k]];
-    } else if (k < 18) x = tot[6 + (k - 9)];
+    if (k < 9) x = tot[vmap[k]];
+    else if (k < 18) x = tot[6 + (k - 9)];
     else if (k < 27) x = v.move ? tot[15 + (k - 18)] : 0.0;
     else if (k < 36) x = v.move ? tot[25 + (k - 27)] : 0.0;
+    else if (k < 45) x = v.move ? tot[34 + vmap[k - 36]] : 0.0;
     else {
-      const double sxy = tot[3] + 0.5 * (tot[7] + tot[9]) - (v.move ? tot[16] + tot[26] : 0.0);
-      x = sxy * (k == 36 ? cos(phase) : sin(phase));
+      const double sxy = tot[3] + 0.5 * (tot[7] + tot[9]) - (v.move ? tot[16] + tot[26] - tot[37] : 0.0);
+      x = sxy * (k == 45 ? cos(phase) : sin(phase));
     }
     double* S = v.sums;
     double* Cc = v.sums + NSUMS;
@@ -833,20 +836,22 @@ susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* h
   if (cnt[0] == 0) return SUSP_OK;
   const double V = (double)h->v.nx * h->v.ny * h->v.nz;
   const double norm = 1.0 / (V * (double)cnt[0]);
-  double visc[9], cont[9], rep[9];
+  double visc[9], cont[9], rep[9], lub[9];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       const int k = 3 * a + b, kt = 3 * b + a;
       visc[k] = norm * (sums[k] + 0.5 * (sums[9 + k] + sums[9 + kt]));
       cont[k] = -norm * sums[18 + k];
       rep[k] = -norm * sums[27 + k];
+      lub[k] = norm * sums[36 + k];
     }
   switch (kind) {
     case SUSP_STRESS_VISCOUS: memcpy(out, visc, sizeof visc); break;
     case SUSP_STRESS_CONTACT: memcpy(out, cont, sizeof cont); break;
     case SUSP_STRESS_REPULSIVE: memcpy(out, rep, sizeof rep); break;
+    case SUSP_STRESS_LUBRICATION: memcpy(out, lub, sizeof lub); break;
     case SUSP_STRESS_TOTAL:
-      for (int k = 0; k < 9; ++k) out[k] = visc[k] + cont[k] + rep[k];
+      for (int k = 0; k < 9; ++k) out[k] = visc[k] + cont[k] + rep[k] + lub[k];
       break;
     case SUSP_STRESS_ANGULAR: {
       // Eq. 26 (monolayer) or Eq. 27 from the histogram, midpoint rule over
@@ -895,8 +900,8 @@ susp_status susp_moduli(susp* h, double* Gp, double* Gpp) {
   // the period integral times omega / pi is twice the window's time average
   const double V = (double)h->v.nx * h->v.ny * h->v.nz;
   const double norm = 1.0 / (V * (double)cnt[0]);
-  *Gp = -2.0 * norm * sums[36] / h->shear.gamma0;
-  *Gpp = 2.0 * norm * sums[37] / h->shear.gamma0;
+  *Gp = -2.0 * norm * sums[45] / h->shear.gamma0;
+  *Gpp = 2.0 * norm * sums[46] / h->shear.gamma0;
   return SUSP_OK;
 }
 

@@ -130,6 +130,7 @@ struct PairOut {
   T Fr[3];                 // double-layer part of Fa
   T ht[3];                 // updated tangential spring
   T fn;                    // normal-force magnitude (repulsive positive)
+  T S[6];                  // lubrication stresslet S_a + S_b (xx yy zz xy xz yz), when asked for
   T d[3];                  // R_b - R_a (minimum image)
   int touching;
 };
@@ -170,7 +171,7 @@ __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int
 template <typename T>
 __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
                               int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
-                              const PairConst<T>& pc, PairOut<T>& o) {
+                              const PairConst<T>& pc, PairOut<T>& o, bool want_s) {
   const T* pl = reinterpret_cast<const T*>(v.plb);
   const T ra = pl[12 * a + 9], rb = pl[12 * b + 9];
   const T dist = sqrt(dot3(d, d));
@@ -185,6 +186,7 @@ __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
   }
   o.fn = (T)0;
   o.touching = 0;
+  for (int c = 0; c < 6; ++c) o.S[c] = (T)0;
   // ---- contact
   const T overlap = ra + rb - dist;
   if (h < (T)0) {
@@ -258,6 +260,32 @@ __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
       const T wat = wa[c] - wap * n[c], wbt = wb[c] - wbp * n[c];
       o.Ta[c] += -YBa * nxu[c] - YCaa * wat - YCab * wbt;
       o.Tb[c] += -YBb * nxu[c] - YCbb * wbt - YCab * wat;
+    }
+    if (want_s) {
+      // stresslets of both spheres (G and H blocks), each with its own radius
+      // and beta = partner / own radius; the G terms are odd in (n, U_a - U_b)
+      // and the H terms even in n, so both take n and uab:
+      //   S = -[XG (n n - I/3)(n.U) + YG (n U + U n - 2 n n (n.U))
+      //         + YH_a,self (Om_a x n) n + YH_a,other (Om_b x n) n + (b alike) + transposes]
+      const T XG = e0 * (T)4 * pi * (ra * ra * ((T)3 * be * be / (op * op * op)) +
+                                     rb * rb * ((T)3 * bj * bj / (oq * oq * oq))) * inv;
+      const T YG = e0 * (T)4 * pi * (ra * ra * (be * ((T)4 - be + (T)7 * be * be) / ((T)10 * op * op * op)) +
+                                     rb * rb * (bj * ((T)4 - bj + (T)7 * bj * bj) / ((T)10 * oq * oq * oq))) * lg;
+      const T Hsa = ra * ra * ra * (be * ((T)2 - be) / ((T)10 * op * op));
+      const T Hoa = ra * ra * ra * (be * be * ((T)1 + (T)7 * be) / ((T)20 * op * op));
+      const T Hsb = rb * rb * rb * (bj * ((T)2 - bj) / ((T)10 * oq * oq));
+      const T Hob = rb * rb * rb * (bj * bj * ((T)1 + (T)7 * bj) / ((T)20 * oq * oq));
+      const T YHwa = e0 * (T)8 * pi * (Hsa + Hob) * lg;   // multiplies (Om_a x n) n + n (Om_a x n)
+      const T YHwb = e0 * (T)8 * pi * (Hsb + Hoa) * lg;   // multiplies (Om_b x n) n + n (Om_b x n)
+      const int ix[6] = {0, 1, 2, 0, 0, 1}, iy[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        const int x = ix[m], y = iy[m];
+        const T g = XG * (n[x] * n[y] - (x == y ? (T)1 / (T)3 : (T)0)) * un +
+                    YG * (n[x] * uab[y] + uab[x] * n[y] - (T)2 * n[x] * n[y] * un);
+        const T hh = YHwa * (wan[x] * n[y] + n[x] * wan[y]) + YHwb * (wbn[x] * n[y] + n[x] * wbn[y]);
+        o.S[m] = -(g + hh);
+      }
     }
   }
 }
@@ -555,8 +583,9 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
   if (!sc) load_pair_const<T>(v, pcl);
   const PairConst<T>& pc = sc ? sc->pc : pcl;
   T F[3] = {0, 0, 0}, Tq[3] = {0, 0, 0};
-  T cv[9], rv[9];
+  T cv[9], rv[9], lv[6];
   for (int c = 0; c < 9; ++c) { cv[c] = (T)0; rv[c] = (T)0; }
+  for (int c = 0; c < 6; ++c) lv[c] = (T)0;
   int ncont = 0;
   const double pi = 3.14159265358979323846;
   const double dth = pi / v.nbins;
@@ -576,7 +605,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
       T spring[3];
       for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : ph[3 * c + x];
       PairOut<T> o;
-      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, pc, o);
+      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, pc, o, sample && i == a);
       touching = o.touching != 0;
       for (int x = 0; x < 3; ++x) {
         if (rg) rg->h[slot][x] = touching ? o.ht[x] : (T)0;
@@ -623,6 +652,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
           if (v.F0 > 0.0)
             for (int x = 0; x < 3; ++x)
               for (int y = 0; y < 3; ++y) rv[3 * x + y] += (T)0.5 * (r[x] * o.Fr[y] + r[y] * o.Fr[x]);
+          for (int c = 0; c < 6; ++c) lv[c] += o.S[c];
         }
       } else {
         for (int x = 0; x < 3; ++x) { F[x] -= o.Fa[x]; Tq[x] += o.Tb[x]; }
@@ -636,6 +666,8 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
   for (int c = 0; c < 3; ++c) { F[c] = group_sum<LANES>(F[c]); Tq[c] = group_sum<LANES>(Tq[c]); }
   if (sample) {
     for (int c = 0; c < 9; ++c) { cv[c] = group_sum<LANES>(cv[c]); rv[c] = group_sum<LANES>(rv[c]); }
+    if (pc.lub)
+      for (int c = 0; c < 6; ++c) lv[c] = group_sum<LANES>(lv[c]);
     ncont = group_sum<LANES>(ncont);
   }
   if (last) {
@@ -671,6 +703,8 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
         if (v.F0 > 0.0) atomicAdd(acc_rep(v, i) + 25 + c, (double)rv[c]);
       }
       if (ncont) atomicAdd(acc_rep(v, i) + 24, (double)ncont);
+      if (pc.lub)
+        for (int c = 0; c < 6; ++c) atomicAdd(acc_rep(v, i) + 34 + c, (double)lv[c]);
     }
   }
   __syncwarp();

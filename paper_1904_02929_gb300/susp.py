@@ -20,7 +20,7 @@ SUSP_OK, SUSP_EINVAL, SUSP_ENOMEM, SUSP_ECUDA = 0, -1, -2, -3
 SUSP_EOVERLAP, SUSP_EUNSTABLE, SUSP_ETIMEOUT, SUSP_ESTATE = -4, -5, -6, -7
 SUSP_FP64, SUSP_FP32, SUSP_FP16_DEV, SUSP_BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": SUSP_FP64, "fp32": SUSP_FP32, "fp16": SUSP_FP16_DEV, "bf16": SUSP_BF16_DEV}
-VISCOUS, CONTACT, REPULSIVE, TOTAL, ANGULAR = range(5)
+VISCOUS, CONTACT, REPULSIVE, TOTAL, ANGULAR, LUBRICATION = range(6)
 
 
 class susp_params(C.Structure):

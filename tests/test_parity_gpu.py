@@ -144,12 +144,13 @@ def test_dense_contacts_lubrication_repulsion_fp64():
     assert np.abs(Rg - Ro).max() < 1e-9
     assert (g.owner() == o.owner()).all()
     assert _pop_err(g, o) < 1e-12
-    for kind in (S.VISCOUS, S.CONTACT, S.REPULSIVE, S.TOTAL, S.ANGULAR):
+    for kind in (S.VISCOUS, S.CONTACT, S.REPULSIVE, S.LUBRICATION, S.TOTAL, S.ANGULAR):
         sg, hg = g.stress(kind)
         so, ho = o.stress(kind)
         assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
     assert (hg[:, 0] == ho[:, 0]).all()
     assert hg[:, 0].sum() > 0, "the run should have contacts"
+    assert np.abs(g.stress(S.LUBRICATION)[0]).max() > 0, "the run should have lubricated pairs"
 
 
 def test_cell_list_and_two_particles_per_warp_fp64():
