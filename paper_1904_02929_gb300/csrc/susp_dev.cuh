@@ -93,7 +93,7 @@ __device__ inline double proto_increment(const Proto& s, long long t) {
 // adder takes one of ACC_REP replicas (on separate cache lines), chosen by its
 // block or particle index; the finalisation adds the replicas.
 constexpr int ACC_REP = 16;
-constexpr int ACC_STRIDE = 48;   // doubles per replica (34 used)
+constexpr int ACC_STRIDE = 48;   // doubles per replica (40 used)
 
 // Pair-force constants of a box in one compute type (built on the host in
 // both types, so that no kernel converts them per pair).
@@ -121,9 +121,9 @@ struct View {
   float inv_nx_f, inv_ny_f, inv_nz_f;
   void* fa;                     // population buffers; step t reads fa when t is even
   void* fb;
-  double* step_acc;             // [ACC_REP][ACC_STRIDE] replicas of the 34 sums of the current step:
+  double* step_acc;             // [ACC_REP][ACC_STRIDE] replicas of the 40 sums of the current step:
                                 //  0-5 viscous (xx yy zz xy xz yz), 6-14 stresslet, 15-23 contact
-                                //  virial, 24 contacts, 25-33 repulsive
+                                //  virial, 24 contacts, 25-33 repulsive, 34-39 lubrication stresslets
   int* owner;                   // -1 fluid, else particle
   void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
   // particles
