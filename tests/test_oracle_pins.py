@@ -664,3 +664,20 @@ def test_lubrication_stresslet_squeeze_and_shape():
     near_cut = O.lubrication_stresslet(a, a, (2 * a + hc - 1e-9) * n, u * n, np.zeros(3), np.zeros(3), eta0,
                                        dlt, hc)
     assert np.abs(near_cut).max() < 1e-7 * np.abs(Sq).max()     # linear in the distance to h_c
+
+
+def test_total_stress_is_the_sum_of_its_kinds():
+    """Eq. 15 with the lubrication stresslets: the total is viscous +
+    contact + double layer + lubrication for a sheared dense box."""
+    from paper_1904_02929_gb300 import inputs as I
+    w = I.config_small(n=20)
+    kw = dict(w.params)
+    kw.update(F0=0.2, debye=0.2, lub_cut=0.5, lub_delta=0.04)
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, vel=np.random.default_rng(4).normal(0, 1e-3, (w.n, 3)), **kw)
+    o.step(6, O.shear(kind=0, rate=2e-3))
+    parts = [o.stress(k)[0] for k in (O.VISCOUS, O.CONTACT, O.REPULSIVE, O.LUBRICATION)]
+    total, _ = o.stress(O.TOTAL)
+    assert np.allclose(total, sum(parts), rtol=1e-12, atol=1e-18)
+    lub = parts[3]
+    assert np.abs(lub - lub.T).max() <= 1e-12 * max(np.abs(lub).max(), 1e-300)
+    assert abs(np.trace(lub)) <= 1e-10 * max(np.abs(lub).max(), 1e-300)
