@@ -52,6 +52,7 @@ class OrcParams(C.Structure):
         ("move_particles", C.c_int), ("nbins", C.c_int),
         ("body_force", C.c_double * 3),
         ("collision", C.c_int), ("tau_bulk", C.c_double),
+        ("driven", C.POINTER(C.c_int)),
     ]
 
 
@@ -191,7 +192,7 @@ class Oracle:
                  rho0=1.0, rho_p=1.0, mu=1.0, kn=100.0, kt_ratio=0.2, eta_n=-1.0, F0=0.0,
                  debye=0.08, lub_delta=0.04, lub_cut=0.5, a_map_ratio=0.95,
                  dem_substeps=0, quasi2d=False, move_particles=True, nbins=36,
-                 body_force=(0.0, 0.0, 0.0), collision="bgk", tau_bulk=0.0):
+                 body_force=(0.0, 0.0, 0.0), collision="bgk", tau_bulk=0.0, driven=None):
         self._keep = []
         radius = _vec(radius).ravel()
         n = radius.size
@@ -215,6 +216,11 @@ class Oracle:
         p.body_force = (C.c_double * 3)(*[float(g) for g in body_force])
         p.collision = {"bgk": 0, "ladd": 1}[collision] if isinstance(collision, str) else int(collision)
         p.tau_bulk = float(tau_bulk)
+        if driven is not None and n:
+            dv = np.ascontiguousarray(np.asarray(driven, dtype=np.int32).ravel())
+            assert dv.size == n
+            self._keep.append(dv)
+            p.driven = dv.ctypes.data_as(C.POINTER(C.c_int))
         self.shape = (int(nx), int(ny), int(nz))
         self.nbins = int(nbins)
         self.h = lib().orc_create(C.byref(p))

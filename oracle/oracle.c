@@ -75,6 +75,7 @@ struct orc_sim {
   double tau_bulk;
   int n;
   double *rad, *amap, *mass, *inert;
+  int *drv;                 /* [n] driven (prescribed-velocity) particles */
   double *R, *U, *W;        /* [3n] position, velocity, angular velocity */
   double *Fh, *Th;          /* link sums of the current step             */
   double *Fcov, *Tcov;      /* covering / uncovering impulses, pending   */
@@ -185,6 +186,8 @@ orc_sim *orc_create(const orc_params *p) {
   int n = p->n > 0 ? p->n : 1;
   s->rad = calloc(n, sizeof(double)); s->amap = calloc(n, sizeof(double));
   s->mass = calloc(n, sizeof(double)); s->inert = calloc(n, sizeof(double));
+  s->drv = calloc(n, sizeof(int));
+  for (int i = 0; i < p->n; ++i) s->drv[i] = p->driven ? (p->driven[i] != 0) : 0;
   s->R = calloc(3 * n, sizeof(double)); s->U = calloc(3 * n, sizeof(double));
   s->W = calloc(3 * n, sizeof(double));
   s->Fh = calloc(3 * n, sizeof(double)); s->Th = calloc(3 * n, sizeof(double));
@@ -232,7 +235,7 @@ orc_sim *orc_create(const orc_params *p) {
 
 void orc_destroy(orc_sim *s) {
   if (!s) return;
-  free(s->rad); free(s->amap); free(s->mass); free(s->inert);
+  free(s->rad); free(s->amap); free(s->mass); free(s->inert); free(s->drv);
   free(s->R); free(s->U); free(s->W); free(s->Fh); free(s->Th);
   free(s->Fcov); free(s->Tcov); free(s->Fp); free(s->Tp);
   free(s->fA); free(s->fB); free(s->owner);
@@ -795,11 +798,14 @@ static void particles_step(orc_sim *s, double delta, double ule, double delta_ne
         F[a] = s->Fh[3 * i + a] + s->Fcov[3 * i + a] + s->Fp[3 * i + a];
         T[a] = s->Th[3 * i + a] + s->Tcov[3 * i + a] + s->Tp[3 * i + a];
       }
-      for (int a = 0; a < 3; ++a) {
-        s->U[3 * i + a] += dt * F[a] / s->mass[i];
-        s->W[3 * i + a] += dt * T[a] / s->inert[i];
+      if (!s->drv[i]) {
+        for (int a = 0; a < 3; ++a) {
+          s->U[3 * i + a] += dt * F[a] / s->mass[i];
+          s->W[3 * i + a] += dt * T[a] / s->inert[i];
+        }
+        if (s->quasi2d) { s->U[3 * i + 2] = 0.0; s->W[3 * i] = 0.0; s->W[3 * i + 1] = 0.0; }
       }
-      if (s->quasi2d) { s->U[3 * i + 2] = 0.0; s->W[3 * i] = 0.0; s->W[3 * i + 1] = 0.0; }
+      /* a driven particle (wall) keeps its velocity and spin */
       for (int a = 0; a < 3; ++a) s->R[3 * i + a] += dt * s->U[3 * i + a];
     }
   }
@@ -807,8 +813,9 @@ static void particles_step(orc_sim *s, double delta, double ule, double delta_ne
   /* Lees-Edwards wrap of the centres, then periodic x, z */
   for (int i = 0; i < s->n; ++i) {
     double *R = &s->R[3 * i];
-    if (R[1] >= s->ny) { R[1] -= s->ny; R[0] -= delta_next; s->U[3 * i] -= ule; }
-    else if (R[1] < 0.0) { R[1] += s->ny; R[0] += delta_next; s->U[3 * i] += ule; }
+    const double du = s->drv[i] ? 0.0 : ule;   /* a driven particle keeps its velocity */
+    if (R[1] >= s->ny) { R[1] -= s->ny; R[0] -= delta_next; s->U[3 * i] -= du; }
+    else if (R[1] < 0.0) { R[1] += s->ny; R[0] += delta_next; s->U[3 * i] += du; }
     R[0] -= s->nx * floor(R[0] / s->nx);
     R[2] -= s->nz * floor(R[2] / s->nz);
     double sp = sqrt(dot(&s->U[3 * i], &s->U[3 * i]));

@@ -50,6 +50,8 @@ typedef struct {
   double body_force[3];     /* uniform force density on the fluid                     */
   int collision;            /* 0 BGK (one eigenvalue -1/tau), 1 Ladd's linear operator */
   double tau_bulk;          /* Ladd: bulk eigenvalue -1/tau_bulk (shear: -1/tau)      */
+  const int *driven;        /* [n] or NULL: 1 = moves with its given velocity and spin
+                               whatever the forces (wall particles)                   */
 } orc_params;
 
 typedef struct {

@@ -263,6 +263,54 @@ def batch_sweep(seed: int = 1004, nbox: int = 64, lo: int = 48, hi: int = 96):
     return out
 
 
+def bumpy_wall(nx: int, nz: int, y: float, radius: float, gap: float = 0.5) -> np.ndarray:
+    """Centres of one wall layer: spheres of the given radius on a square
+    lattice in the periodic x-z plane at height y, spaced as evenly as the
+    box allows with at least ``gap`` between neighbours."""
+    s = 2.0 * radius + gap
+    mx, mz = max(1, int(nx // s)), max(1, int(nz // s))
+    xs = (np.arange(mx) + 0.5) * nx / mx
+    zs = (np.arange(mz) + 0.5) * nz / mz
+    X, Z = np.meshgrid(xs, zs, indexing="ij")
+    return np.stack([X.ravel(), np.full(X.size, float(y)), Z.ravel()], axis=1)
+
+
+def config_walls(seed: int = 1006, L: int = 48, a_wall: float = 3.0, phi3: float = 0.30,
+                 wall_speed: float = 0.02, precision: str = "fp64") -> Workload:
+    """Shear driven by bumpy walls made of particles (the paper's driver,
+    Sec. 3): a bottom and a top layer of wall spheres moving at -U/2 and +U/2
+    in x with a bidisperse suspension between them.  The box stays periodic
+    in y through a Lees-Edwards plane whose image velocity is U, so the image
+    of the top wall below the bottom wall moves with the bottom wall and the
+    thin layer across the plane is not sheared.  Returns the workload with
+    ``driven`` (1 for wall spheres) and their velocities in ``params``."""
+    yb, yt = a_wall + 1.0, L - a_wall - 2.0
+    bottom = bumpy_wall(L, L, yb, a_wall)
+    top = bumpy_wall(L, L, yt, a_wall)
+    a_min, gap = 3.0, 0.5
+    # centres of the suspension lie in a band that keeps every sphere clear of
+    # both walls; they are placed in a periodic box of the band's height (its
+    # gaps across the periodic y boundary are only stricter) and lifted
+    band = (yt - a_wall) - (yb + a_wall) - 2 * (1.4 * a_min + gap)
+    n = n_for_phi3(phi3, (L, band + 2 * 1.4 * a_min, L), a_min, 1.4 * a_min) if phi3 > 0 else 0
+    r = bidisperse_radii(n, a_min) if n else np.zeros(0)
+    body = place_spheres((L, band, L), r, seed, min_gap=0.1) if n else np.zeros((0, 3))
+    body[:, 1] += yb + a_wall + 1.4 * a_min + gap
+    pos = np.concatenate([bottom, top, body])
+    rad = np.concatenate([np.full(len(bottom) + len(top), a_wall), r])
+    vel = np.zeros((len(pos), 3))
+    vel[:len(bottom), 0] = -0.5 * wall_speed
+    vel[len(bottom):len(bottom) + len(top), 0] = 0.5 * wall_speed
+    driven = np.zeros(len(pos), dtype=np.int32)
+    driven[:len(bottom) + len(top)] = 1
+    kn = 1.0e3
+    params = dict(tau=1.0, rho0=1.0, rho_p=1.0, mu=1.0, kn=kn, kt_ratio=0.5,
+                  F0=2e-4 * kn, debye=0.02 * a_min, lub_delta=0.01 * a_min, lub_cut=0.5,
+                  a_map_ratio=0.95, quasi2d=False, nbins=36, vel=vel, driven=driven)
+    return Workload(f"walls-{L}^3-phi{phi3:.2f}-N{n}+{len(bottom) + len(top)}", L, L, L, rad, pos,
+                    params, dict(kind=0, rate=wall_speed / L), precision, 2000)
+
+
 def random_populations(nx, ny, nz, seed: int, amplitude: float = 0.02, weights=None):
     """Positive perturbed populations (19, nz, ny, nx) around a rest state.
 

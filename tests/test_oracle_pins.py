@@ -681,3 +681,41 @@ def test_total_stress_is_the_sum_of_its_kinds():
     lub = parts[3]
     assert np.abs(lub - lub.T).max() <= 1e-12 * max(np.abs(lub).max(), 1e-300)
     assert abs(np.trace(lub)) <= 1e-10 * max(np.abs(lub).max(), 1e-300)
+
+
+# ----------------------------------------------- bumpy walls (driven spheres)
+def _couette_profile(o, w):
+    C, _, _ = O.lattice()
+    C = np.asarray(C, dtype=float)
+    f = o.populations().reshape(19, w.nz, w.ny, w.nx)
+    own = o.owner().reshape(w.nz, w.ny, w.nx)
+    rho = f.sum(0)
+    ux = np.where(own < 0, np.tensordot(C[:, 0], f, axes=1) / rho, np.nan)
+    return np.nanmean(ux, axis=(0, 2))
+
+
+def test_bumpy_walls_move_as_prescribed_and_drive_the_suspension():
+    """Wall spheres (driven) keep their velocity whatever the contacts and
+    lubrication forces on them, so their centres advance exactly by U t; the
+    suspension between them is set in motion, and the fluid's mean velocity
+    rises monotonically from -U/2 at the bottom wall to +U/2 at the top one
+    (Sec. 3: shear applied by moving bumpy walls made of particles)."""
+    from paper_1904_02929_gb300 import inputs as I
+    w = I.config_walls(L=32, a_wall=3.0, phi3=0.2, wall_speed=0.02)
+    kw = dict(w.params)
+    drv = kw["driven"].astype(bool)
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
+    R0, U0, W0 = o.particles()
+    T = 200
+    o.step(T, O.shear(**w.shear))
+    assert o.error() == 0
+    R, U, W = o.particles()
+    assert np.array_equal(U[drv], U0[drv]) and np.array_equal(W[drv], W0[drv])
+    d = R[drv] - R0[drv]
+    d[:, 0] -= U0[drv, 0] * T
+    d[:, 0] -= w.nx * np.round(d[:, 0] / w.nx)
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(U[~drv]).max() > 1e-4            # the suspension is driven
+    prof = _couette_profile(o, w)
+    assert np.all(np.diff(prof) > -1e-9)
+    assert prof[0] == pytest.approx(-0.01, rel=0.02) and prof[-1] == pytest.approx(0.01, rel=0.02)
