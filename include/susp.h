@@ -90,6 +90,10 @@ typedef struct {
                                stress relaxed by -1/tau, its trace by -1/tau_bulk, ghost modes
                                removed.  Both coincide at tau = tau_bulk = 1                      */
   double tau_bulk;          /* Ladd: bulk relaxation time (> 0.5); <= 0 selects tau                */
+  const int *driven;        /* [n] or NULL (host; copied): nonzero marks a driven sphere, which keeps
+                               its given velocity and spin whatever the forces (the wall spheres of
+                               the bumpy walls that shear the suspension in Sec. 3); it still takes
+                               part in contacts, lubrication and bounce-back                      */
 } susp_params;
 
 typedef struct {

@@ -53,7 +53,7 @@ constexpr int NSUMS = 47;
 struct Layout {
   size_t fa, fb, owner, pm, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
-  size_t cstart, ccnt, cids, pcell, pj, ph, pcnt, pconst;
+  size_t cstart, ccnt, cids, pcell, pj, ph, pcnt, pconst, drv;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
   size_t sums, hist, counters, proto, err;
   size_t total;
@@ -131,7 +131,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.ncx = ncx; L.ncy = ncy; L.ncz = ncz;
   L.ncells = ncx * ncy * ncz;
   L.csx = (double)p->nx / ncx; L.csy = (double)p->ny / ncy; L.csz = (double)p->nz / ncz;
-  L.pj = take(4 * (size_t)nn * PAIR_SLOTS); L.ph = take(24 * (size_t)nn * PAIR_SLOTS); L.pcnt = take(4 * nn); L.pconst = take(64 * (size_t)nn);
+  L.pj = take(4 * (size_t)nn * PAIR_SLOTS); L.ph = take(24 * (size_t)nn * PAIR_SLOTS); L.pcnt = take(4 * nn); L.pconst = take(64 * (size_t)nn); L.drv = take(4 * (size_t)nn);
   L.cstart = take(4 * (L.ncells + 1)); L.ccnt = take(4 * L.ncells);
   L.cids = take(4 * nn); L.pcell = take(4 * nn);
   L.hc0 = take(4 * nn); L.hp0 = take(4 * (size_t)nn * HSLOTS); L.hv0 = take(24 * (size_t)nn * HSLOTS);
@@ -683,7 +683,9 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.inv_csx = 1.0 / L.csx; v.inv_csy = 1.0 / L.csy; v.inv_csz = 1.0 / L.csz;
   v.cell_start = (int*)(w + L.cstart); v.cell_cnt = (int*)(w + L.ccnt);
   v.cell_ids = (int*)(w + L.cids); v.pcell = (int*)(w + L.pcell);
-  v.pj = (int*)(w + L.pj); v.ph = (double*)(w + L.ph); v.pcnt = (int*)(w + L.pcnt); v.pconst = (void*)(w + L.pconst);
+  v.pj = (int*)(w + L.pj); v.ph = (double*)(w + L.ph); v.pcnt = (int*)(w + L.pcnt); v.pconst = (void*)(w + L.pconst); v.drv = (int*)(w + L.drv);
+  v.has_drv = 0;
+  for (int i = 0; p->driven && i < n; ++i) v.has_drv |= p->driven[i] != 0;
   v.K = HSLOTS;
   v.hcnt0 = (int*)(w + L.hc0); v.hpart0 = (int*)(w + L.hp0); v.hval0 = (double*)(w + L.hv0);
   v.hcnt1 = (int*)(w + L.hc1); v.hpart1 = (int*)(w + L.hp1); v.hval1 = (double*)(w + L.hv1);
@@ -770,6 +772,11 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
     cudaMemcpyAsync(v.inert, inert.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inv_m, im.data(), 8 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(v.inv_I, iI.data(), 8 * n, cudaMemcpyHostToDevice, s);
+  }
+  std::vector<int> drv(n > 0 ? n : 1, 0);
+  if (n > 0 && p->driven) {
+    for (int i = 0; i < n; ++i) drv[i] = p->driven[i] != 0;
+    cudaMemcpyAsync(v.drv, drv.data(), 4 * n, cudaMemcpyHostToDevice, s);
   }
   Proto pr;
   memset(&pr, 0, sizeof pr);

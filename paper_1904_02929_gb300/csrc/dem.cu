@@ -360,18 +360,21 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
                                      double dt, bool last, bool plb_double, const T* k) {
   double R[3], U[3], W[3];
   const T im = k[6], iI = k[7], dtt = (T)dt;
+  // A driven (wall) sphere keeps its velocity and spin whatever the forces.
+  const bool driven = v.has_drv && v.drv[i];
   for (int c = 0; c < 3; ++c) {
     const T F = k[c] + Fp[c];
     const T Tq = k[3 + c] + Tp[c];
-    U[c] = (double)((T)S.U[3 * i + c] + dtt * F * im);
-    W[c] = (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
+    U[c] = driven ? S.U[3 * i + c] : (double)((T)S.U[3 * i + c] + dtt * F * im);
+    W[c] = driven ? S.W[3 * i + c] : (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
   }
-  if (v.quasi2d) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
+  if (v.quasi2d && !driven) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
   for (int c = 0; c < 3; ++c) R[c] = S.R[3 * i + c] + dt * U[c];
   if (last) {
     const Proto* pr = v.proto;
-    if (R[1] >= v.ny) { R[1] -= v.ny; R[0] -= pr->delta_n; U[0] -= pr->ule; }
-    else if (R[1] < 0.0) { R[1] += v.ny; R[0] += pr->delta_n; U[0] += pr->ule; }
+    const double du = driven ? 0.0 : pr->ule;   // a driven sphere's velocity is prescribed
+    if (R[1] >= v.ny) { R[1] -= v.ny; R[0] -= pr->delta_n; U[0] -= du; }
+    else if (R[1] < 0.0) { R[1] += v.ny; R[0] += pr->delta_n; U[0] += du; }
     if (R[0] < 0.0) R[0] += v.nx; else if (R[0] >= v.nx) R[0] -= v.nx;
     if (R[2] < 0.0) R[2] += v.nz; else if (R[2] >= v.nz) R[2] -= v.nz;
     const T sp2 = (T)(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);

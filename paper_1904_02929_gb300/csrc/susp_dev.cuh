@@ -142,6 +142,8 @@ struct View {
   int* pj;
   double* ph;                   // [n][PAIR_SLOTS][3]
   int* pcnt;                    // [n]
+  int* drv;                     // [n] 1: driven sphere (keeps its velocity and spin)
+  int has_drv;                  // some sphere is driven
   void* pconst;                 // [n][8] per-step constants in the compute type: F^h + F^cov,
                                 //  T^h + T^cov, 1 / m, 1 / I (written at the step start)
   // tangential-spring table: per particle a, partners b > a

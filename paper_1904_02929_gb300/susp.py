@@ -40,6 +40,7 @@ class susp_params(C.Structure):
         ("body_force", C.c_double * 3),
         ("prec", C.c_int),
         ("collision", C.c_int), ("tau_bulk", C.c_double),
+        ("driven", C.POINTER(C.c_int)),
     ]
 
 
@@ -366,7 +367,7 @@ def make_params(nx, ny, nz, radius=(), pos=(), vel=None, omega=None, tau=1.0, rh
                 rho_p=1.0, mu=1.0, kn=100.0, kt_ratio=0.2, eta_n=-1.0, F0=0.0, debye=0.08,
                 lub_delta=0.04, lub_cut=0.5, a_map_ratio=0.95, dem_substeps=0, quasi2d=False,
                 move_particles=True, nbins=36, body_force=(0.0, 0.0, 0.0), precision="fp32",
-                collision="bgk", tau_bulk=0.0):
+                collision="bgk", tau_bulk=0.0, driven=None):
     """Fill a susp_params; returns (params, keepalive) — keep the second alive."""
     radius = np.ascontiguousarray(np.asarray(radius, dtype=np.float64).ravel())
     n = radius.size
@@ -394,6 +395,12 @@ def make_params(nx, ny, nz, radius=(), pos=(), vel=None, omega=None, tau=1.0, rh
     p.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.collision = {"bgk": 0, "ladd": 1}[collision] if isinstance(collision, str) else int(collision)
     p.tau_bulk = float(tau_bulk)
+    if driven is not None and n:
+        dv = np.ascontiguousarray(np.asarray(driven, dtype=np.int32).ravel())
+        if dv.size != n:
+            raise ValueError("driven needs one flag per particle")
+        keep.append(dv)
+        p.driven = dv.ctypes.data_as(C.POINTER(C.c_int))
     return p, keep
 
 

@@ -326,6 +326,33 @@ def test_moving_particles_fp32():
     assert np.abs(Rg - Ro).max() < 1e-4
 
 
+
+@pytest.mark.parametrize("precision,pop_tol,r_tol,u_tol,s_tol",
+                         [("fp64", 1e-12, 1e-9, 1e-10, 1e-9), ("fp32", 2e-5, 1e-4, 1e-5, 2e-2)])
+def test_bumpy_walls(precision, pop_tol, r_tol, u_tol, s_tol):
+    """Shear driven by two layers of wall spheres (driven: they keep their
+    velocity and spin) moving at -U/2 and +U/2, with a Lees-Edwards rate U / L
+    so the image of the top wall co-moves with the bottom wall (Sec. 3).
+    Driven spheres take part in contacts, lubrication and bounce-back; their
+    velocities must come back unchanged and their centres advanced by U t."""
+    w = I.config_walls(L=32, a_wall=3.0, phi3=0.2, wall_speed=0.02, precision=precision)
+    kw = _params(w)
+    drv = kw["driven"].astype(bool)
+    g, o = _both(w.nx, w.ny, w.nz, w.radius, w.pos, precision=precision, **kw)
+    _step(g, o, 60, **w.shear)
+    assert o.error() == 0
+    Rg, Ug, Wg = g.particles()
+    Ro, Uo, Wo = o.particles()
+    assert np.array_equal(Ug[drv], kw["vel"][drv]) and not Wg[drv].any()
+    assert np.abs(Rg - Ro).max() < r_tol
+    assert np.abs(Ug - Uo).max() < u_tol
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < pop_tol
+    for kind in (S.VISCOUS, S.CONTACT, S.LUBRICATION, S.TOTAL):
+        sg, _ = g.stress(kind)
+        so, _ = o.stress(kind)
+        assert np.abs(sg - so).max() <= s_tol * max(np.abs(so).max(), 1e-300), kind
+
 # ---------------------------------------------------------------- edge cases
 def test_no_particles_and_minimum_box():
     g = S.Suspension(4, 4, 4, precision="fp32")
