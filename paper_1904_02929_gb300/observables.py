@@ -4,7 +4,9 @@ of the step lives here.
 
 * ``stress_anisotropy``: Delta lambda = sigma_1 - sigma_3 (largest minus
   smallest eigenvalue of the stress tensor) and P = -(sigma_1 + sigma_2 +
-  sigma_3) / 3, with their ratio (Sec. 3.3).
+  sigma_3) / 3, with their ratio (Sec. 3.3); ``stress_anisotropy_2d`` the
+  monolayer's in-plane form sigma_1 - sigma_2 and P = -(sigma_1 + sigma_2) / 2
+  from the x-y block (Sec. 4.4).
 * ``reduced_shear_rate``: gamma_dot* = 6 pi eta0 a_min^2 gamma_dot / F0
   (Sec. 3.2).
 * ``relative_viscosity``: eta / eta0 = sigma_xy / (eta0 gamma_dot) under a
@@ -31,6 +33,17 @@ def stress_anisotropy(sigma) -> tuple[float, float, float]:
     ev = np.linalg.eigvalsh(0.5 * (s + s.T))[::-1]
     dl = float(ev[0] - ev[2])
     p = float(-ev.sum() / 3.0)
+    return dl, p, (dl / p if p != 0.0 else math.inf)
+
+
+def stress_anisotropy_2d(sigma) -> tuple[float, float, float]:
+    """(Delta lambda, P, Delta lambda / P) of the monolayer: eigenvalues
+    sigma_1 >= sigma_2 of the symmetric x-y block of the stress tensor,
+    Delta lambda = sigma_1 - sigma_2, P = -(sigma_1 + sigma_2) / 2."""
+    s = np.asarray(sigma, dtype=float).reshape(3, 3)[:2, :2]
+    ev = np.linalg.eigvalsh(0.5 * (s + s.T))[::-1]
+    dl = float(ev[0] - ev[1])
+    p = float(-ev.sum() / 2.0)
     return dl, p, (dl / p if p != 0.0 else math.inf)
 
 

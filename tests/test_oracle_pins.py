@@ -477,6 +477,16 @@ def test_stress_anisotropy_and_scalings():
     s = 0.3
     dl3, p3, _ = X.stress_anisotropy([[0, s, 0], [s, 0, 0], [0, 0, 0]])
     assert dl3 == pytest.approx(2 * s) and p3 == pytest.approx(0.0, abs=1e-15)
+    # monolayer form: only the x-y block counts, whatever sigma_zz is
+    d2 = np.diag([-1.0, -3.0, -40.0])
+    dl4, p4, r4 = X.stress_anisotropy_2d(d2)
+    assert dl4 == pytest.approx(2.0) and p4 == pytest.approx(2.0) and r4 == pytest.approx(1.0)
+    c, sn = math.cos(0.7), math.sin(0.7)
+    rz = np.array([[c, -sn, 0], [sn, c, 0], [0, 0, 1.0]])
+    dl5, p5, _ = X.stress_anisotropy_2d(rz @ d2 @ rz.T)
+    assert dl5 == pytest.approx(dl4, rel=1e-12) and p5 == pytest.approx(p4, rel=1e-12)
+    dl6, p6, _ = X.stress_anisotropy_2d([[0, s, 0], [s, 0, 0], [0, 0, -9.0]])
+    assert dl6 == pytest.approx(2 * s) and p6 == pytest.approx(0.0, abs=1e-15)
     eta0 = X.solvent_viscosity(1.0)
     assert eta0 == pytest.approx(1.0 / 6.0)
     assert X.reduced_shear_rate(1e-4, eta0, 4.0, 0.2) == pytest.approx(6 * math.pi * eta0 * 16 * 1e-4 / 0.2)
