@@ -62,7 +62,9 @@ typedef enum {
 } susp_precision;
 
 typedef struct {
-  int nx, ny, nz;           /* lattice; x flow, y gradient (Lees-Edwards), z vorticity; each >= 4 */
+  int nx, ny, nz;           /* lattice; x flow, y gradient (Lees-Edwards), z vorticity; each >= 4,
+                               nx, ny <= 2047, nz <= 1023 and nx ny nz < 2^27 per box (element
+                               indices stay 32-bit); larger problems run as many boxes           */
   double tau;               /* BGK relaxation time (> 0.5); eta0 = rho0 (tau - 1/2) / 3            */
   double rho0;              /* reference fluid density, used in Eq. 7                             */
   int n;                    /* number of particles (>= 0)                                          */

@@ -65,6 +65,29 @@ def test_workspace_bytes_and_validation_on_host():
     assert S.susp_workspace_bytes(bad) == 0 and "too large" in S.susp_last_error()
 
 
+def test_lattice_limits_and_parameter_checks_on_host():
+    # the largest accepted box: just under 2^27 nodes
+    ok, k0 = S.make_params(512, 512, 511, precision="fp16")
+    assert S.susp_workspace_bytes(ok) >= 2 * 19 * 512 * 512 * 511 * 2
+    for dims, msg in [((512, 512, 512), "2^27"), ((2048, 8, 8), "2047"), ((8, 8, 1024), "2047")]:
+        bad, kb = S.make_params(*dims, precision="fp16")
+        assert S.susp_workspace_bytes(bad) == 0 and msg in S.susp_last_error(), dims
+    cases = [dict(collision=2), dict(collision="ladd", tau_bulk=0.5), dict(rho0=0.0)]
+    for kw in cases:
+        bad, kb = S.make_params(16, 16, 16, **kw)
+        assert S.susp_workspace_bytes(bad) == 0, kw
+    bad, kb = S.make_params(32, 32, 32, [4.0], [[16.0, float("nan"), 16.0]])
+    assert S.susp_workspace_bytes(bad) == 0 and "finite" in S.susp_last_error()
+    bad, kb = S.make_params(32, 32, 32, [4.0], [[16, 16, 16]], a_map_ratio=1.5)
+    assert S.susp_workspace_bytes(bad) == 0
+    # driven flags: one per particle; they add one int32 per particle to the layout
+    with pytest.raises(ValueError):
+        S.make_params(32, 32, 32, [4.0, 4.0], [[8, 8, 8], [24, 24, 24]], driven=[1])
+    d, kd = S.make_params(32, 32, 32, [4.0, 4.0], [[8, 8, 8], [24, 24, 24]], driven=[1, 0])
+    assert d.driven and d.driven[0] == 1 and d.driven[1] == 0
+    assert S.susp_workspace_bytes(d) > 0
+
+
 def test_create_rejects_bad_workspace_without_touching_the_device():
     p, keep = S.make_params(16, 16, 16, precision="fp32")
     h = C.c_void_p()
