@@ -41,3 +41,50 @@ def test_clock_lines():
     assert r["samples"] == 2 and r["reasons"] == ["hw_thermal_slowdown"]
     assert r["sm_mhz"] == pytest.approx(1785.0)
     assert bench.parse_clock_lines([]) is None
+
+
+def _clk(mhz, reasons=()):
+    return {"sm_mhz": mhz, "sm_max_mhz": 2070.0, "reasons": list(reasons), "samples": 5}
+
+
+def test_clock_records_that_void_a_number():
+    assert not bench.clocks_rejected(None)
+    assert not bench.clocks_rejected(_clk(2070.0))
+    assert not bench.clocks_rejected(_clk(1500.0, ["sw_power_cap"]))      # kept and noted
+    assert bench.clocks_rejected(_clk(2070.0, ["hw_slowdown"]))
+    assert bench.clocks_rejected(_clk(1900.0, ["sw_thermal_slowdown", "sw_power_cap"]))
+    assert bench.clocks_rejected(_clk(1200.0))                             # locked low, no reason
+    assert not bench.clocks_rejected(_clk(1800.0))
+
+
+class _FakeSampler:
+    def __init__(self, rec):
+        self.rec = rec
+
+    def stop(self):
+        return self.rec
+
+
+def test_timed_region_is_retaken_once_on_a_void_clock_record():
+    runs = []
+
+    def run():
+        runs.append(1)
+        return 10.0 * len(runs)
+
+    recs = iter([_clk(2070.0, ["hw_thermal_slowdown"]), _clk(2070.0)])
+    res, clk, first = bench.timed_with_retake(run, lambda: _FakeSampler(next(recs)))
+    assert (res, len(runs)) == (20.0, 2)
+    assert clk["reasons"] == [] and first["reasons"] == ["hw_thermal_slowdown"]
+    # a second void record is reported as it is, not retaken again
+    runs.clear()
+    recs = iter([_clk(1000.0), _clk(1000.0)])
+    res, clk, first = bench.timed_with_retake(run, lambda: _FakeSampler(next(recs)))
+    assert len(runs) == 2 and bench.clocks_rejected(clk) and first is not None
+    # clean first try; ranks without a sampler follow rank 0's decision
+    runs.clear()
+    res, clk, first = bench.timed_with_retake(run, lambda: None)
+    assert (len(runs), clk, first) == (1, None, None)
+    runs.clear()
+    res, clk, first = bench.timed_with_retake(run, lambda: None, agree=lambda f: len(runs) == 1)
+    assert len(runs) == 2
