@@ -18,6 +18,9 @@
 // d -= k (Delta, L_y, 0), and b's image moves with U_b + k U_LE e_x.
 // Integration (Eq. 1): semi-implicit Euler with the hydrodynamic link force
 // held over the sub-steps; Lees-Edwards wrap of the centres at the end.
+// Driven spheres (the bumpy walls of Sec. 3) keep their velocity and spin:
+// only their centres advance, and a Lees-Edwards crossing leaves their
+// velocity as it is.
 #include <cooperative_groups.h>
 
 #include "susp_dev.cuh"
