@@ -218,6 +218,36 @@ def test_momentum_conserved_with_moving_particles():
     assert s.error() == 0
 
 
+def test_sphere_crossing_the_lees_edwards_plane():
+    """A sphere that leaves through y = L_y re-enters at y = 0 shifted by
+    -Delta(t+1) in x with its x velocity lowered by U_LE (and the reverse
+    through y = 0): the image box above moves with +U_LE and is offset by
+    +Delta.  Heavy spheres (rho_p = 1e6) so the fluid's force changes their
+    velocity by ~1e-9 per step; Delta(t) = t L_y rate under a constant rate."""
+    L, rate = 24, 1e-3
+    ule = L * rate
+    o = O.Oracle(L, L, L, [3.0, 3.0], [[6.0, L - 1.0, 6.0], [18.0, 1.0, 18.0]],
+                 vel=[[0.0, 0.04, 0.0], [0.0, -0.04, 0.0]], rho_p=1e6, tau=1.0)
+    sh = O.shear(kind=0, rate=rate)
+    crossed = set()
+    for t in range(40):
+        R0, U0, _ = o.particles()
+        o.step(1, sh)
+        R1, U1, _ = o.particles()
+        d1 = o.delta
+        assert d1 == pytest.approx((t + 1) * ule, rel=1e-12)
+        for i in range(2):
+            if abs(R1[i, 1] - R0[i, 1]) < L / 2:
+                continue
+            s = 1 if R1[i, 1] < R0[i, 1] else -1       # +1: out through the top
+            dx = R1[i, 0] - (R0[i, 0] + U0[i, 0] - s * d1)
+            dx -= L * np.round(dx / L)
+            assert abs(dx) < 1e-7, (t, i)
+            assert U1[i, 0] - (U0[i, 0] - s * ule) == pytest.approx(0.0, abs=1e-7)
+            crossed.add(s)
+    assert crossed == {1, -1} and o.error() == 0
+
+
 # ---------------------------------------------------------------- contacts
 def test_normal_contact_closed_form():
     """Linear spring + dashpot: F = (kn delta_n + eta_n v_n), repulsive,
