@@ -248,6 +248,34 @@ def test_sphere_crossing_the_lees_edwards_plane():
     assert crossed == {1, -1} and o.error() == 0
 
 
+def test_contact_across_the_lees_edwards_plane():
+    """Two heavy spheres at rest on either side of the y boundary touch only
+    through the image box above, offset by +Delta(t): as Delta grows the
+    image of B slides over A, and each step's contact virial (sampled at the
+    step start, Eq. 12) is the closed form -(kn delta / d) r r / V with
+    r = R_A - (R_B + (Delta(t), L_y, 0)), no tangential force (mu = 0) and no
+    dashpot; zero before the image reaches A."""
+    L, rate, kn = 24, 2e-3, 100.0
+    o = O.Oracle(L, L, L, [3.0, 3.0], [[12.0, L - 2.95, 12.0], [8.0, 2.95, 12.0]], rho_p=1e6,
+                 tau=1.0, kn=kn, kt_ratio=0.5, mu=0.0, eta_n=0.0, F0=0.0, lub_cut=0.0)
+    sh = O.shear(kind=0, rate=rate)
+    touching = 0
+    for t in range(72):
+        R, _, _ = o.particles()
+        r = R[0] - (R[1] + np.array([o.delta, L, 0.0]))
+        d = np.linalg.norm(r)
+        o.stress_reset()
+        o.step(1, sh)
+        sc, _ = o.stress(O.CONTACT)
+        if d < 6.0:
+            touching += 1
+            expect = -(kn * (6.0 - d) / d) * np.outer(r, r) / L ** 3
+            np.testing.assert_allclose(sc, expect, rtol=1e-10, atol=1e-12 * np.abs(expect).max())
+        else:
+            assert not sc.any(), t
+    assert touching == 11 and o.error() == 0
+
+
 # ---------------------------------------------------------------- contacts
 def test_normal_contact_closed_form():
     """Linear spring + dashpot: F = (kn delta_n + eta_n v_n), repulsive,
