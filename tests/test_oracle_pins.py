@@ -336,6 +336,26 @@ def test_contact_rolling_without_slip_has_no_tangential_force():
     np.testing.assert_allclose(Ft, 0, atol=1e-16)
 
 
+@pytest.mark.parametrize("h", [0.05, 0.5, 1.9, 2.1])
+def test_double_layer_repulsion_virial(h):
+    """Eq. 13: two heavy spheres at surface gap h (along a diagonal of the
+    x-y plane) repel with F0 exp(-h / lambda) along the line of centres, cut
+    off at h = 10 lambda; the step's double-layer virial (Eq. 14) is
+    -(F / d) r r / V with r = R_a - R_b."""
+    L, F0, lam = 24, 0.3, 0.2
+    d = 6.0 + h
+    dvec = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0) * d
+    pa = np.array([12.0, 12.0, 12.0])
+    o = O.Oracle(L, L, L, [3.0, 3.0], [pa, pa + dvec], rho_p=1e6, tau=1.0, kn=100.0, F0=F0,
+                 debye=lam, lub_cut=0.0)
+    o.step(1, O.shear(kind=0, rate=0.0))
+    sr, _ = o.stress(O.REPULSIVE)
+    f = F0 * math.exp(-h / lam) if h < 10 * lam else 0.0
+    expect = -(f / d) * np.outer(dvec, dvec) / L ** 3
+    np.testing.assert_allclose(sr, expect, rtol=1e-12, atol=1e-22)
+    assert o.error() == 0
+
+
 # ------------------------------------------------------------- lubrication
 ETA0 = 1.0 / 6.0
 
