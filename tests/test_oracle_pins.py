@@ -356,6 +356,35 @@ def test_double_layer_repulsion_virial(h):
     assert o.error() == 0
 
 
+def _restitution(kn, substeps):
+    """Head-on collision of two heavy equal spheres (a = 3, relative speed
+    0.02, no dashpot, friction, lubrication or repulsion): the ratio of the
+    relative speeds after and before."""
+    o = O.Oracle(32, 32, 32, [3.0, 3.0], [[12.75, 16.0, 16.0], [19.25, 16.0, 16.0]],
+                 vel=[[0.01, 0, 0], [-0.01, 0, 0]], rho_p=1e6, tau=1.0, kn=kn, kt_ratio=0.5,
+                 mu=0.0, eta_n=0.0, F0=0.0, lub_cut=0.0, dem_substeps=substeps)
+    _, U0, _ = o.particles()
+    o.step(60, O.shear(kind=0, rate=0.0))
+    _, U, _ = o.particles()
+    return -(U[0, 0] - U[1, 0]) / (U0[0, 0] - U0[1, 0]), o.nsub, o.error()
+
+
+def test_elastic_collision_and_the_substep_rule():
+    """Eq. 1 integrated semi-implicitly over the automatic sub-steps: an
+    elastic head-on collision (contact frequency sqrt(2 kn / m)) returns the
+    approach speed to within the first-order error of the contact's entry and
+    exit, the error shrinks as the sub-steps are refined, and one sub-step per
+    lattice step at the same stiffness pumps energy into the pair (what the
+    automatic count prevents)."""
+    e_auto, ns, err = _restitution(1e9, 0)
+    m = 1e6 * 4.0 / 3.0 * math.pi * 27.0
+    assert ns == math.ceil(math.sqrt(2e9 / m)) and err == 0
+    assert 0.85 < e_auto < 1.15
+    errs = [abs(_restitution(1e9, k)[0] - 1.0) for k in (5, 10, 20, 50)]
+    assert errs == sorted(errs, reverse=True) and errs[-1] < 5e-3
+    assert _restitution(1e9, 1)[0] > 2.0
+
+
 # ------------------------------------------------------------- lubrication
 ETA0 = 1.0 / 6.0
 
