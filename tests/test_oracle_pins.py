@@ -385,6 +385,29 @@ def test_elastic_collision_and_the_substep_rule():
     assert _restitution(1e9, 1)[0] > 2.0
 
 
+@pytest.mark.parametrize("zeta", [0.1, 0.3])
+def test_spring_dashpot_restitution_closed_form(zeta):
+    """Normal contact as a linear spring plus a dashpot on the approach speed
+    (Eq. 11, reading R-normal): a head-on collision of equal spheres (reduced
+    mass m / 2) leaves with the textbook restitution exp(-gamma pi / omega),
+    gamma = eta_n / m, omega^2 = 2 kn / m - gamma^2, here at damping ratios
+    0.1 and 0.3 with 200 sub-steps per lattice step."""
+    m = 1e6 * 4.0 / 3.0 * math.pi * 27.0
+    kn = 1e9
+    w0 = math.sqrt(2.0 * kn / m)
+    g = zeta * w0
+    eta_n = g * m
+    e_th = math.exp(-g * math.pi / math.sqrt(w0 * w0 - g * g))
+    o = O.Oracle(32, 32, 32, [3.0, 3.0], [[12.75, 16.0, 16.0], [19.25, 16.0, 16.0]],
+                 vel=[[0.01, 0, 0], [-0.01, 0, 0]], rho_p=1e6, tau=1.0, kn=kn, kt_ratio=0.5,
+                 mu=0.0, eta_n=eta_n, F0=0.0, lub_cut=0.0, dem_substeps=200)
+    _, U0, _ = o.particles()
+    o.step(60, O.shear(kind=0, rate=0.0))
+    _, U, _ = o.particles()
+    e = -(U[0, 0] - U[1, 0]) / (U0[0, 0] - U0[1, 0])
+    assert e == pytest.approx(e_th, rel=5e-3) and o.error() == 0
+
+
 # ------------------------------------------------------------- lubrication
 ETA0 = 1.0 / 6.0
 
