@@ -353,6 +353,45 @@ def test_bumpy_walls(precision, pop_tol, r_tol, u_tol, s_tol):
         so, _ = o.stress(kind)
         assert np.abs(sg - so).max() <= s_tol * max(np.abs(so).max(), 1e-300), kind
 
+
+def _pair_case(name):
+    """Two heavy spheres (rho_p = 1e6) in the pinned two-body settings:
+    crossing the Lees-Edwards plane, touching through its image, repelling
+    at a gap (Eq. 13), colliding with a dashpot over 200 sub-steps."""
+    heavy = dict(rho_p=1e6, tau=1.0, kt_ratio=0.5)
+    if name == "le_crossing":
+        return (24, [[6.0, 23.0, 6.0], [18.0, 1.0, 18.0]], dict(vel=[[0.0, 0.04, 0.0], [0.0, -0.04, 0.0]],
+                **heavy), dict(kind=0, rate=1e-3), 40)
+    if name == "le_image_contact":
+        return (24, [[12.0, 21.05, 12.0], [8.0, 2.95, 12.0]], dict(kn=100.0, mu=0.0, eta_n=0.0, F0=0.0,
+                lub_cut=0.0, **heavy), dict(kind=0, rate=2e-3), 72)
+    if name == "double_layer":
+        d = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0) * 6.5
+        return (24, [[12.0, 12.0, 12.0], list(12.0 + d)], dict(kn=100.0, F0=0.3, debye=0.2, lub_cut=0.0,
+                **heavy), dict(kind=0, rate=0.0), 20)
+    m = 1e6 * 4.0 / 3.0 * math.pi * 27.0
+    return (32, [[12.75, 16.0, 16.0], [19.25, 16.0, 16.0]], dict(vel=[[0.01, 0, 0], [-0.01, 0, 0]], kn=1e9,
+            mu=0.0, eta_n=0.3 * math.sqrt(2e9 / m) * m, F0=0.0, lub_cut=0.0, dem_substeps=200, **heavy),
+            dict(kind=0, rate=0.0), 60)
+
+
+@pytest.mark.parametrize("name", ["le_crossing", "le_image_contact", "double_layer", "dashpot"])
+def test_two_body_cases_fp64(name):
+    L, pos, kw, sh, T = _pair_case(name)
+    g, o = _both(L, L, L, [3.0, 3.0], pos, **kw)
+    _step(g, o, T, **sh)
+    assert o.error() == 0
+    Rg, Ug, _ = g.particles()
+    Ro, Uo, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9
+    assert np.abs(Ug - Uo).max() <= 1e-9 * np.abs(Uo).max() + 1e-15
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+    for kind in (S.CONTACT, S.REPULSIVE, S.TOTAL):
+        sg, _ = g.stress(kind)
+        so, _ = o.stress(kind)
+        assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
+
 # ---------------------------------------------------------------- edge cases
 def test_no_particles_and_minimum_box():
     g = S.Suspension(4, 4, 4, precision="fp32")
