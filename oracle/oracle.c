@@ -577,7 +577,7 @@ int orc_contact(double ra, double rb, const double d[3], const double uab[3],
   double vt[3] = {v[0] - vn * n[0], v[1] - vn * n[1], v[2] - vn * n[2]};
   /* normal force: spring on the overlap plus dashpot on the approach speed */
   double fn = kn * overlap + eta_n * vn;
-  /* tangential spring: rotate into the tangent plane, then integrate v_t */
+  /* tangential spring: project onto the tangent plane, then integrate v_t */
   double hn = dot(ht, n);
   for (int a = 0; a < 3; ++a) ht[a] = ht[a] - hn * n[a] + vt[a] * dt;
   double ftr[3] = {-kt * ht[0], -kt * ht[1], -kt * ht[2]};

@@ -7,7 +7,7 @@
 // atomics):
 //   contact (Sec. 2, Eq. 11, 11t): F_n = kn delta_n + eta_n v_n along -n,
 //     tangential spring delta_t (kept per pair in a table owned by a),
-//     rotated into the tangent plane and advanced by v_t dt, F_t = -kt delta_t
+//     projected onto the tangent plane and advanced by v_t dt, F_t = -kt delta_t
 //     capped at mu |F_n| (Coulomb slip, spring reset to the slip length),
 //     torques a_a n x F_t and a_b n x F_t;
 //   double-layer repulsion F0 exp(-h / debye) (Eq. 13);

@@ -324,6 +324,21 @@ def test_tangential_spring_and_coulomb_slip():
     assert slipped
 
 
+def test_tangential_spring_is_projected_onto_the_tangent_plane():
+    """When the line of centres turns, the stored spring loses its normal
+    part before v_t dt is added (reading R-tangential): with no tangential
+    motion the spring comes back as its tangent-plane projection and the
+    tangential force is -kt times it, perpendicular to n."""
+    d = np.array([0.0, 7.9, 0.0])                # n = +y
+    h0 = np.array([0.01, 0.02, -0.005])          # carries a normal (y) part
+    t, Fa, Ta, Tb, fn, Ft, ht = O.contact(4.0, 4.0, d, [0, 0, 0], [0, 0, 0], [0, 0, 0], 100.0, 20.0,
+                                          0.0, 10.0, 1.0, h0)
+    assert t
+    np.testing.assert_allclose(ht, [0.01, 0.0, -0.005], rtol=0, atol=1e-17)
+    np.testing.assert_allclose(Ft, -20.0 * np.array([0.01, 0.0, -0.005]), rtol=1e-14)
+    assert abs(np.dot(Ft, d)) < 1e-15
+
+
 def test_contact_rolling_without_slip_has_no_tangential_force():
     """Relative surface velocity includes the spins: equal and opposite rolling
     (U_ab = 0, a Omega_a + b Omega_b = 0) loads no tangential spring."""
