@@ -777,6 +777,36 @@ def test_torque_on_a_spinning_sphere():
     assert np.abs(T[0, :2]).max() < 1e-9 * abs(T[0, 2]) and np.abs(F[0]).max() < 1e-9 * abs(T[0, 2])
 
 
+def test_einstein_viscosity_of_a_held_sphere():
+    """The particle stresslet of the momentum exchange (Eq. 9, 10, reading
+    R-sigma_h) carries the symmetric stress of a rigid sphere in shear: one
+    held sphere (a_map = 0.95 x 3.4) in a 24^3 Lees-Edwards box raises the
+    viscous shear stress by Einstein's 2.5 phi (phi of the mapped radius)
+    plus the few per cent of its hydrodynamic radius and the periodic
+    images.  The fluid nodes alone average to the imposed eta0 rate (inside
+    a rigid sphere the strain rate vanishes), so a missing, halved or
+    sign-flipped stresslet falls outside the band."""
+    L, a, rate, tau = 24, 3.4, 1e-3, 1.0
+    eta0 = (tau - 0.5) / 3.0
+    o = O.Oracle(L, L, L, [a], [[L / 2, L / 2, L / 2]], tau=tau, move_particles=False,
+                 a_map_ratio=0.95)
+    # start from the Couette profile the Lees-Edwards planes impose
+    f = np.zeros((19, L, L, L))
+    for y in range(L):
+        feq = np.asarray(O.equilibrium(1.0, np.array([rate * (y + 0.5 - L / 2), 0.0, 0.0])))
+        f[:, :, y, :] = feq[:, None, None]
+    o.set_populations(f.reshape(19, -1))
+    sh = O.shear(kind=0, rate=rate)
+    o.step(150, sh)
+    o.stress_reset()
+    o.step(100, sh)
+    sv, _ = o.stress(O.VISCOUS)
+    excess = sv[0, 1] / (eta0 * rate) - 1.0
+    phi = 4.0 / 3.0 * math.pi * (0.95 * a) ** 3 / L ** 3
+    assert 1.0 < excess / (2.5 * phi) < 1.15
+    assert o.error() == 0
+
+
 # ------------------------------------------ lubrication stresslet (G, H blocks)
 @pytest.mark.parametrize("ra,rb,h", [(4.0, 5.6, 0.08), (5.6, 4.0, 0.01), (5.0, 5.0, 0.05), (3.0, 7.0, 0.02)])
 def test_lubrication_stresslet_vanishes_for_rigid_rotation(ra, rb, h):
