@@ -276,6 +276,28 @@ def test_contact_across_the_lees_edwards_plane():
     assert touching == 11 and o.error() == 0
 
 
+def test_quasi2d_monolayer_stays_in_its_plane():
+    """Quasi-2D constraint of the monolayer (Sec. 4.1): whatever velocities
+    and spins the spheres start with, after the first step U_z = 0 and
+    Omega_x = Omega_y = 0 exactly and the centres keep their z, while the
+    in-plane motion and the contacts go on (48 x 48 x 20, phi = 0.70,
+    a_max = L_z / 4)."""
+    from paper_1904_02929_gb300 import inputs as I
+    w = I.config_monolayer(Lx=48, Ly=48, Lz=20, phi=0.70, precision="fp64")
+    kw = dict(w.params)
+    rng = np.random.default_rng(5)
+    kw["vel"] = rng.normal(0, 3e-3, (w.n, 3))
+    kw["omega"] = rng.normal(0, 1e-3, (w.n, 3))
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
+    z0 = o.particles()[0][:, 2].copy()
+    o.step(30, O.shear(kind=0, rate=1e-3))
+    R, U, W = o.particles()
+    assert o.error() == 0
+    assert not U[:, 2].any() and not W[:, :2].any() and np.array_equal(R[:, 2], z0)
+    assert np.abs(U[:, :2]).max() > 1e-3 and np.abs(W[:, 2]).max() > 1e-4
+    assert o.stress(O.CONTACT)[1][:, 0].sum() > 0
+
+
 # ---------------------------------------------------------------- contacts
 def test_normal_contact_closed_form():
     """Linear spring + dashpot: F = (kn delta_n + eta_n v_n), repulsive,
