@@ -387,6 +387,55 @@ def monolayer_leg(steps: int, warmup: int):
             "l2": "not flushed: 560 MB of populations per buffer, above L2"}
 
 
+def variant_leg(w, what: str, steps: int, warmup: int, **over):
+    """Throughput of one FP32 box built from workload ``w`` with parameter
+    overrides (Ladd's collision operator, bumpy walls): tuned, L2 flushed
+    between timed steps like the default leg, per-step CUDA events on the
+    box's stream; MLUPS, particle-steps/s, stage times and the
+    collide-stream roofline."""
+    import torch
+    from paper_1904_02929_gb300 import susp as S
+    kw = dict(w.params)
+    kw.update(over)
+    g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **kw)
+    sh = S.make_shear(**w.shear)
+    g.step(warmup, sh)
+    tuned = g.tune()
+    S.susp_profile(g.h, True)
+    g.step(2, sh)
+    torch.cuda.synchronize()
+    S.susp_profile(g.h, True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(g.stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(g.stream)
+            g.step(1, sh)
+            b.record(g.stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    stages, n = S.susp_profile_stages(g.h)
+    S.susp_profile(g.h, False)
+    g.stress(S.TOTAL)                               # raises on any device error flag
+    info = g.info()
+    g.close()
+    del flush
+    k1 = stages["collide_stream"] / n
+    alg = 2 * 19 * 4 * w.ncell
+    peak, kind = peak_hbm()
+    return {"workload": w.name, "variant": what, "lattice": [w.nx, w.ny, w.nz], "particles": w.n,
+            "storage": "fp32", "steps": steps, "value": w.ncell * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms / steps, "particle_steps_per_s": w.n * steps / (ms / 1e3),
+            "dem_substeps": info.dem_substeps,
+            "stage_us": {k: round(1e3 * v / n, 1) for k, v in stages.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_collide_stream<fp32>", "achieved": alg / (k1 / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
+                         "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+            "launch_shape": tuned, "l2": "flushed between timed steps (256 MB write)"}
+
+
 def serving_leg(duration: float = 5.0, rate: float = 20.0, steps: int = 1000, budget: int = 4 << 30):
     """Poisson-arriving requests (rate per second, for ``duration`` seconds)
     drawn 50 / 50 from quasi-2D 512 x 512 and 256 x 256 monolayers (phi
@@ -465,6 +514,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-monolayer", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the Ladd-operator and bumpy-wall legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -591,6 +642,14 @@ def main():
             line["clocks_rejected_first_try"] = clk_rejected
         if world == 1 and not args.no_monolayer:
             line["monolayer"] = monolayer_leg(args.batched_steps * 2, args.warmup)
+        if world == 1 and not args.no_variants:
+            from paper_1904_02929_gb300 import inputs
+            line["ladd"] = variant_leg(w, "Ladd's linear collision operator, tau_bulk = 0.8",
+                                       args.batched_steps * 2, args.warmup, collision="ladd",
+                                       tau_bulk=0.8)
+            line["walls"] = variant_leg(inputs.config_walls(L=96, phi3=0.30, precision="fp32"),
+                                        "bumpy walls of driven spheres, U = 0.02",
+                                        args.batched_steps * 2, args.warmup)
         if world == 1 and not args.no_batched:
             from paper_1904_02929_gb300 import inputs
             line["batched"] = batched_leg(inputs.batch_sweep(), args.batched_steps, args.warmup)
