@@ -13,6 +13,10 @@ of the step lives here.
   constant rate.
 * ``dimensionless_moduli``: G'* = G' / kn, G''* = G'' / kn and
   eta* = G''* / (omega tau_c) (Sec. 4.1).
+* ``strain_window``: the lattice steps over which a constant-rate run is
+  averaged, strains gamma = 5 to 11 (Sec. 3.1); ``wall_shear_rate``: the
+  nominal rate U / (y_top - y_bottom) of bumpy walls moving apart at U
+  (Sec. 3).
 """
 from __future__ import annotations
 
@@ -62,3 +66,18 @@ def dimensionless_moduli(Gp: float, Gpp: float, kn: float, omega: float,
     """(G'*, G''*, eta*) = (G' / kn, G'' / kn, (G'' / kn) / (omega tau_c))."""
     gps, gpps = Gp / kn, Gpp / kn
     return gps, gpps, gpps / (omega * tau_c)
+
+
+def strain_window(rate: float, gamma_start: float = 5.0, gamma_end: float = 11.0) -> tuple[int, int]:
+    """(first, last) lattice step of the averaging window gamma_start <=
+    rate t <= gamma_end: step ``box.step(first)``, ``box.stress_reset()``,
+    then ``box.step(last - first)`` and read the time-averaged stress."""
+    if not rate > 0.0 or not gamma_end > gamma_start >= 0.0:
+        raise ValueError("need rate > 0 and 0 <= gamma_start < gamma_end")
+    return math.ceil(gamma_start / rate - 1e-9), math.floor(gamma_end / rate + 1e-9)
+
+
+def wall_shear_rate(wall_speed: float, y_bottom: float, y_top: float) -> float:
+    """Nominal shear rate of two bumpy walls whose relative speed is
+    ``wall_speed``, from the distance between their centre planes."""
+    return wall_speed / (y_top - y_bottom)

@@ -654,6 +654,12 @@ def test_stress_anisotropy_and_scalings():
     assert dl5 == pytest.approx(dl4, rel=1e-12) and p5 == pytest.approx(p4, rel=1e-12)
     dl6, p6, _ = X.stress_anisotropy_2d([[0, s, 0], [s, 0, 0], [0, 0, -9.0]])
     assert dl6 == pytest.approx(2 * s) and p6 == pytest.approx(0.0, abs=1e-15)
+    # averaging window of Sec. 3.1 (gamma = 5 .. 11) and the walls' nominal rate
+    assert X.strain_window(1e-4) == (50000, 110000)
+    assert X.strain_window(3e-4) == (16667, 36666)
+    with pytest.raises(ValueError):
+        X.strain_window(0.0)
+    assert X.wall_shear_rate(0.02, 4.0, 43.0) == pytest.approx(0.02 / 39.0)
     eta0 = X.solvent_viscosity(1.0)
     assert eta0 == pytest.approx(1.0 / 6.0)
     assert X.reduced_shear_rate(1e-4, eta0, 4.0, 0.2) == pytest.approx(6 * math.pi * eta0 * 16 * 1e-4 / 0.2)
