@@ -1,7 +1,8 @@
 """Plain FP64 CPU oracle for the sheared-suspension LB + particle step.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package; the product path
+CPU-baseline leg and reference arm of ``bench.py`` may import this package
+(``__graft_entry__.build()`` compiles it); the product path
 (``paper_1904_02929_gb300``) never does.  The C source (``oracle.c``) is
 written from arXiv:1904.02929 independently of the CUDA library and shares
 no code with it.

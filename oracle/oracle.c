@@ -1,8 +1,8 @@
 /*
  * oracle.c — plain, slow FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
  *
- * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
- * call this file.  It is deliberately written as straightforward loops in the
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg and
+ * reference arm may call this file.  It is deliberately written as straightforward loops in the
  * order of the paper's equations; no blocking, fusion or reordering.
  *
  * Conventions (lattice units, dx = dt = 1, c_s^2 = 1/3):
