@@ -138,6 +138,25 @@ def test_couette_fixed_point_and_viscous_stress(tau):
     assert sig[1, 0] == pytest.approx(eta0 * rate, rel=1e-12)
 
 
+@pytest.mark.parametrize("tau,tau_bulk", [(0.8, 1.3), (1.2, 0.6)])
+def test_couette_shear_stress_under_ladd_operator(tau, tau_bulk):
+    """Ladd's operator (reading R-BGK): the Couette shear stress is set by the
+    shear eigenvalue alone, eta0 rate with eta0 = rho0 (tau - 1/2) / 3,
+    whatever the bulk relaxation time; mass and momentum stay those of the
+    linear profile."""
+    nx, ny, nz, rate = 8, 16, 4, 2e-3
+    f0 = _couette_state(nx, ny, nz, tau, rate)
+    s = O.Oracle(nx, ny, nz, tau=tau, collision="ladd", tau_bulk=tau_bulk)
+    s.set_populations(f0)
+    s.step(60, O.shear(0, rate=rate))
+    f = s.populations()
+    np.testing.assert_allclose(f.sum(0), f0.sum(0), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(np.einsum("qa,qzyx->azyx", CF, f),
+                               np.einsum("qa,qzyx->azyx", CF, f0), rtol=0, atol=1e-13)
+    sig, _ = s.stress(O.VISCOUS)
+    assert sig[0, 1] == pytest.approx((tau - 0.5) / 3 * rate, rel=1e-12)
+
+
 def test_couette_develops_from_rest():
     """Started at rest, the Lees-Edwards boundary drives the linear profile
     (diffusive time Ly^2 / nu); slope -> rate, sign pinned by the image
