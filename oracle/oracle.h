@@ -6,7 +6,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
  * call this code: only the tests, the smoke check and the CPU-baseline leg
- * of the benchmark use it.  It shares no header, constant table or helper
+ * and reference arm of the benchmark use it.  It shares no header, constant table or helper
  * with the CUDA library; both are written from the paper independently.
  *
  * Every routine follows the paper's equations in the paper's order:
