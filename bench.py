@@ -644,12 +644,17 @@ def main():
             line["monolayer"] = monolayer_leg(args.batched_steps * 2, args.warmup)
         if world == 1 and not args.no_variants:
             from paper_1904_02929_gb300 import inputs
-            line["ladd"] = variant_leg(w, "Ladd's linear collision operator, tau_bulk = 0.8",
-                                       args.batched_steps * 2, args.warmup, collision="ladd",
-                                       tau_bulk=0.8)
-            line["walls"] = variant_leg(inputs.config_walls(L=96, phi3=0.30, precision="fp32"),
-                                        "bumpy walls of driven spheres, U = 0.02",
-                                        args.batched_steps * 2, args.warmup)
+            legs = {"ladd": lambda: variant_leg(w, "Ladd's linear collision operator, tau_bulk = 0.8",
+                                                args.batched_steps * 2, args.warmup, collision="ladd",
+                                                tau_bulk=0.8),
+                    "walls": lambda: variant_leg(inputs.config_walls(L=96, phi3=0.30, precision="fp32"),
+                                                 "bumpy walls of driven spheres, U = 0.02",
+                                                 args.batched_steps * 2, args.warmup)}
+            for name, leg in legs.items():
+                try:
+                    line[name] = leg()
+                except S.SuspError as e:     # a device flag in a side leg: report it, keep the line
+                    line[name] = {"error": str(e)}
         if world == 1 and not args.no_batched:
             from paper_1904_02929_gb300 import inputs
             line["batched"] = batched_leg(inputs.batch_sweep(), args.batched_steps, args.warmup)
