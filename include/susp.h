@@ -6,15 +6,19 @@
  * (arXiv:1904.02929).  One step is
  *   - the D3Q19 lattice-Boltzmann collide-stream update (Appendix A, Eq. 3-5;
  *     BGK, which equals the paper's linear operator when every non-conserved
- *     mode relaxes fully, i.e. tau = 1),
+ *     mode relaxes fully, i.e. tau = 1, or that operator itself with separate
+ *     shear and bulk relaxation times and the ghost modes removed),
  *   - moving-particle bounce-back and link momentum exchange (Eq. 6-10),
  *   - a Lees-Edwards sheared boundary in y (x flow, z vorticity), driven by a
  *     constant rate or the oscillatory strain of Eq. 16,
  *   - per particle: frictional contacts with tangential-spring history and
  *     Coulomb slip (Eq. 11, 11t), double-layer repulsion (Eq. 13), the pairwise
  *     lubrication correction (Appendix A) and rigid-body integration (Eq. 1),
- *   - stress sums (Eq. 12, 14, 15) and angular contact histograms (Eq. 19-23)
- *     for the angular stress of Eq. 26 / 27.
+ *   - stress sums (Eq. 12, 14, 15, with the lubrication stresslets), angular
+ *     contact histograms (Eq. 19-23) for the angular stress of Eq. 26 / 27,
+ *     and the storage and loss moduli of Eq. 17, 18.
+ * Shear can also be applied as in the paper by bumpy walls: spheres flagged
+ * as driven keep their prescribed velocity (Sec. 3).
  *
  * Memory: the caller owns one device workspace of susp_workspace_bytes()
  * bytes (for example a torch uint8 tensor).  The library never allocates
