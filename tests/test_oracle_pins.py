@@ -480,6 +480,20 @@ def test_lubrication_reynolds_limit_equal_spheres():
     np.testing.assert_allclose(Fa[:2], 0, atol=1e-16)
 
 
+@pytest.mark.parametrize("ra,rb", [(3.0, 4.2), (4.2, 3.0), (2.0, 5.0)])
+def test_lubrication_reynolds_limit_unequal_spheres(ra, rb):
+    """Reynolds' squeeze force between unequal spheres, 6 pi eta (a b / (a +
+    b))^2 U / h, minus its value at the cutoff, exactly with delta = 0: the
+    leading X^A term 2 beta^2 / (1 + beta)^3 / xi with beta = a_b / a_a and
+    xi = 2 h / (a_a + a_b) (reading R-lub); beta the other way round is off
+    by ~30 %."""
+    h, hc, U = 1e-3, 2.0, 0.01
+    d = np.array([0.0, 0.0, ra + rb + h])
+    Fa, _, _ = O.lubrication(ra, rb, d, [0, 0, U], [0, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    red = ra * rb / (ra + rb)
+    assert -Fa[2] == pytest.approx(6 * math.pi * ETA0 * red ** 2 * U * (1 / h - 1 / hc), rel=1e-11)
+
+
 def test_lubrication_vanishes_at_cutoff_and_beyond():
     a, b = 4.0, 5.6
     for h in (0.5, 0.5000001, 0.7):
