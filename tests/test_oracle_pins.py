@@ -494,6 +494,27 @@ def test_lubrication_reynolds_limit_unequal_spheres(ra, rb):
     assert -Fa[2] == pytest.approx(6 * math.pi * ETA0 * red ** 2 * U * (1 / h - 1 / hc), rel=1e-11)
 
 
+def test_lubrication_tangential_log_term():
+    """Relative sliding at a small gap: the leading shear resistance is
+    logarithmic, 6 pi eta a_a Y^A U_t ln(1/xi) with Jeffrey and Onishi's
+    Y^A = 4 beta (2 + beta + 2 beta^2) / (15 (1 + beta)^3) (1/6 for equal
+    spheres, i.e. pi eta a U_t ln(1/xi)), here minus its value at the
+    cutoff: pi eta a U ln(h_c / h) for equal spheres; and the force does not
+    depend on which sphere is called a."""
+    h, hc, U = 1e-3, 0.5, 0.01
+    a = 4.0
+    Fa, _, _ = O.lubrication(a, a, [0, 0, 2 * a + h], [U, 0, 0], [0, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    assert -Fa[0] == pytest.approx(math.pi * ETA0 * a * U * math.log(hc / h), rel=1e-11)
+    assert Fa[1] == 0.0 and Fa[2] == 0.0
+    ra, rb = 3.0, 4.2
+    b = rb / ra
+    ya = 4 * b * (2 + b + 2 * b * b) / (15 * (1 + b) ** 3)
+    F1, _, _ = O.lubrication(ra, rb, [0, 0, ra + rb + h], [U, 0, 0], [0, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    F2, _, _ = O.lubrication(rb, ra, [0, 0, ra + rb + h], [U, 0, 0], [0, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    assert -F1[0] == pytest.approx(6 * math.pi * ETA0 * ra * ya * U * math.log(hc / h), rel=1e-11)
+    assert F2[0] == pytest.approx(F1[0], rel=1e-12)
+
+
 def test_lubrication_vanishes_at_cutoff_and_beyond():
     a, b = 4.0, 5.6
     for h in (0.5, 0.5000001, 0.7):
