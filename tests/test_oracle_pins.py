@@ -515,6 +515,22 @@ def test_lubrication_tangential_log_term():
     assert F2[0] == pytest.approx(F1[0], rel=1e-12)
 
 
+@pytest.mark.parametrize("ra,rb", [(4.0, 4.0), (3.0, 4.2)])
+def test_lubrication_rotation_log_terms(ra, rb):
+    """Sphere a spinning about a tangential axis next to sphere b at rest:
+    the torques are the logarithmic leading terms of Jeffrey and Onishi,
+    T_a = -8 pi eta a_a^3 Y^C_11 Omega, T_b = -8 pi eta a_a^3 Y^C_12 Omega,
+    Y^C_11 = 2 beta / (5 (1 + beta)) ln(1/xi), Y^C_12 = beta^2 / (10 (1 + beta))
+    ln(1/xi), each minus its value at the cutoff."""
+    h, hc, w = 1e-3, 0.5, 0.001
+    _, Ta, Tb = O.lubrication(ra, rb, [0, 0, ra + rb + h], [0, 0, 0], [w, 0, 0], [0, 0, 0], ETA0, 0.0, hc)
+    b = rb / ra
+    unit = 8 * math.pi * ETA0 * ra ** 3 * w * math.log(hc / h)
+    assert -Ta[0] == pytest.approx(2 * b / (5 * (1 + b)) * unit, rel=1e-11)
+    assert -Tb[0] == pytest.approx(b * b / (10 * (1 + b)) * unit, rel=1e-11)
+    assert Ta[1] == Ta[2] == Tb[1] == Tb[2] == 0.0
+
+
 def test_lubrication_vanishes_at_cutoff_and_beyond():
     a, b = 4.0, 5.6
     for h in (0.5, 0.5000001, 0.7):
