@@ -456,9 +456,21 @@ static void link_forces(orc_sim *s, double delta, double ule) {
             double cu = ub[0] * CV[q][0] + ub[1] * CV[q][1] + ub[2] * CV[q][2];
             mag = 2.0 * s->fA[q * s->ncell + c] - 6.0 * weight(q) * s->rho0 * cu;
           } else {
-            /* node of another particle touching i's solid: it counts as fluid
-             * at rest, so a particle in a fluid at rest feels no net force */
-            mag = 2.0 * weight(q) * s->rho0;
+            /* node r of another particle j next to i's solid (mapped spheres
+             * closer than one spacing, Appendix A (i)): r stands for a fluid
+             * node in equilibrium at rho0 moving with the mean ubar of the two
+             * surfaces' velocities at r_b, and the wall moves with ubar too:
+             *   mag = 2 n^eq_q(rho0, rho0 ubar) - 6 C^q rho0 (ubar . c_q).
+             * It is even in c_q, so the reverse link of j cancels it exactly
+             * (momentum stays with the pair), and it equals what a fluid
+             * link carries at rest (2 C^q rho0) or in a flow moving with
+             * both surfaces, so the pressure on each particle balances */
+            int j = own;
+            double armj[3], ubj[3], ubar[3], jb[3];
+            link_geometry(s, j, x, y, z, q, delta, ule, armj, ubj);
+            for (int a = 0; a < 3; ++a) { ubar[a] = 0.5 * (ub[a] + ubj[a]); jb[a] = s->rho0 * ubar[a]; }
+            double cub = ubar[0] * CV[q][0] + ubar[1] * CV[q][1] + ubar[2] * CV[q][2];
+            mag = 2.0 * feq1(q, s->rho0, jb) - 6.0 * weight(q) * s->rho0 * cub;
           }
           double fv[3] = {mag * CV[q][0], mag * CV[q][1], mag * CV[q][2]};
           double tq[3];
@@ -743,7 +755,12 @@ static void pair_forces(orc_sim *s, double delta, double ule, double dt, int sam
           for (int x = 0; x < 3; ++x)
             for (int y = 0; y < 3; ++y)
               s->s_cont[3 * x + y] += 0.5 * (r[x] * Fa[y] + r[y] * Fa[x]);
-          /* angular distributions (Eq. 19-23): theta of r folded into [0, pi) */
+          /* angular distributions (Eq. 19-23): theta of r folded into [0, pi);
+           * the tangential force counted positive when it turns the spheres
+           * counter-clockwise (Sec. 3.2): a's contact point lies at -a n from
+           * its centre, so that is -(F_a . t) with t = (-sin, cos) of the
+           * unfolded angle (the same value from b's side, whose angle is
+           * folded by pi and whose force is -F_a) */
           double th = atan2(r[1], r[0]);
           double tx = -sin(th), ty = cos(th);
           if (th < 0.0) th += M_PI;
@@ -753,7 +770,7 @@ static void pair_forces(orc_sim *s, double delta, double ule, double dt, int sam
           if (bin < 0) bin = 0;
           s->hist[3 * bin] += 1.0;
           s->hist[3 * bin + 1] += fn;
-          s->hist[3 * bin + 2] += Fa[0] * tx + Fa[1] * ty;
+          s->hist[3 * bin + 2] -= Fa[0] * tx + Fa[1] * ty;
           s->ncontacts += 1;
         }
       }

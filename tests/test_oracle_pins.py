@@ -188,7 +188,109 @@ def test_rest_state_with_held_sphere_is_exact():
     assert (~fluid).sum() == pytest.approx(4 / 3 * math.pi * (0.95 * 4) ** 3, rel=0.15)
 
 
-def test_moving_sphere_feels_drag_and_drives_fluid():
+def _cross_links(own):
+    """Links between solid nodes of two different particles, from the node
+    map alone (periodic box, no shear): for every node r owned by j and every
+    direction p whose source s = r - c_p is owned by i != j, one link of
+    particle i with c_q = -c_p pointing from r into i's solid.  Returns a list
+    of (i, j, q)."""
+    out = []
+    for p in range(1, 19):
+        src = np.roll(own, shift=tuple(int(v) for v in C[p][::-1]), axis=(0, 1, 2))
+        hit = (own >= 0) & (src >= 0) & (src != own)
+        for idx in zip(*np.nonzero(hit)):
+            out.append((int(src[idx]), int(own[idx]), int(OPP[p])))
+    return out
+
+
+def _touching_pair(vel=None):
+    """Two held spheres, a = 4 (mapped 3.8), centres 8.0 apart along a skew
+    direction: the mapped spheres are 0.4 apart, so solid nodes of the two
+    touch along the gap."""
+    d = np.array([0.6, 0.48, 0.64])
+    R0 = np.array([8.3, 9.1, 8.7])
+    pos = [R0, R0 + 8.0 * d]
+    return O.Oracle(24, 24, 24, radius=[4.0, 4.0], pos=pos, vel=vel, move_particles=False)
+
+
+def test_touching_spheres_at_rest_feel_no_force():
+    """Appendix A (i): mapped spheres closer than one spacing have solid nodes
+    that are each other's link neighbours.  Two such spheres held in fluid at
+    rest must feel no force or torque (hydrostatic balance: a uniform
+    pressure exerts no net force on a closed body), and the fluid must stay
+    at rest.  The test first shows that the pair has links between the two
+    solids, and that without them each sphere would feel the rest pressure of
+    its fluid links alone, -sum 2 C^q rho0 c_q over the missing links."""
+    s = _touching_pair()
+    own = s.owner()[...].transpose(0, 1, 2)
+    links = _cross_links(own)
+    assert len(links) >= 4
+    for i in (0, 1):
+        miss = sum(2 * W[q] * CF[q] for (a, _, q) in links if a == i)
+        assert np.linalg.norm(miss) > 1e-3          # a dropped link would show
+    s.step(5)
+    F, T = s.hydro()
+    np.testing.assert_allclose(F, 0, atol=1e-13)
+    np.testing.assert_allclose(T, 0, atol=1e-13)
+    f = s.populations()
+    fluid = s.owner() < 0
+    np.testing.assert_allclose(f[:, fluid], np.broadcast_to(W[:, None], f[:, fluid].shape),
+                               atol=1e-16)
+
+
+def test_touching_spheres_moving_together_feel_no_force():
+    """The same pair held at one velocity U in fluid moving uniformly with U:
+    the uniform equilibrium n^eq(rho0, rho0 U) is a fixed point of Eq. 7 with
+    u_b = U, so every fluid link carries C^q rho0 [2 + 9 (U.c)^2 - 3 U^2] c_q.
+    Those terms sum to zero over a closed link set, so the pair feels no force
+    or torque only if a link between the two solids carries the same value,
+    i.e. stands for fluid in equilibrium moving with the surfaces.  Counting
+    such a link as fluid at rest instead (2 C^q rho0) leaves each sphere with
+    a force of order rho0 U^2, computed here to show the test would see it."""
+    U = np.array([0.03, -0.02, 0.012])
+    s = _touching_pair(vel=[U, U])
+    nx = 24
+    feq = O.equilibrium(1.0, U)
+    s.set_populations(np.broadcast_to(feq[:, None], (19, nx ** 3)).copy())
+    links = _cross_links(s.owner())
+    for i in (0, 1):
+        resid = sum(W[q] * (9 * (U @ CF[q]) ** 2 - 3 * U @ U) * CF[q]
+                    for (a, _, q) in links if a == i)
+        assert np.linalg.norm(resid) > 1e-6         # the rest reading would show
+    s.step(5)
+    F, T = s.hydro()
+    np.testing.assert_allclose(F, 0, atol=1e-13)
+    np.testing.assert_allclose(T, 0, atol=1e-13)
+    f = s.populations()
+    fluid = s.owner() < 0
+    np.testing.assert_allclose(f[:, fluid], np.broadcast_to(feq[:, None], f[:, fluid].shape),
+                               atol=1e-15)
+
+
+def test_touching_spheres_in_relative_motion_conserve_momentum():
+    """A link between two solids exchanges momentum between the two spheres
+    only (no fluid takes part), so the pair's link forces must cancel exactly
+    whatever their velocities: the sum over both spheres of the links between
+    them is zero.  Checked as total momentum of fluid + held spheres: the held
+    spheres' surfaces inject momentum -sum F^h per step, which must equal the
+    fluid's momentum change; with the pair's internal links unbalanced the
+    two would differ."""
+    Ua = np.array([0.02, -0.01, 0.005])
+    Ub = np.array([-0.015, 0.01, 0.02])
+    s = _touching_pair(vel=[Ua, Ub])
+    fluid = s.owner() < 0
+
+    def jfluid():
+        f = s.populations()
+        return np.einsum("qa,qn->a", CF, f[:, fluid])
+
+    j0 = jfluid()
+    for _ in range(4):
+        s.step(1)
+        F, _ = s.hydro()
+        j1 = jfluid()
+        np.testing.assert_allclose(j1 - j0, -F.sum(0), rtol=0, atol=1e-13)
+        j0 = j1
     """Eq. 7/8 sign: a sphere held at velocity U in fluid at rest receives a
     force against U and gives the fluid momentum along U; a sphere held at
     spin Omega receives a torque against Omega."""
@@ -654,6 +756,43 @@ def test_angular_stress_eq27_as_printed_is_twice_the_virial():
     np.testing.assert_allclose(sig[:2, :2], 2 * vir / V, rtol=1e-12)
 
 
+def test_angular_stress_eq26_matches_full_virial_with_tangential_forces():
+    """P8 with friction: monodisperse disks, contacts at bin centres with
+    |r| = 2a carrying normal AND tangential forces.  The third histogram
+    column holds the tangential force counted positive when it turns the
+    spheres counter-clockwise (Sec. 3.2, Eq. 22): the force on the sphere at
+    the tip of r = R_a - R_b is then F_n n - xi t, since its torque about the
+    centre, (-a n) x (F_n n - xi t), is +a xi along z.  Eq. 26 as printed,
+    [zeta_N n_alpha - zeta_T t_alpha] n_beta (force index first, Appendix C),
+    must then equal the full virial (1/A) sum F_alpha r_beta, compression
+    positive, including its antisymmetric part.  A flipped sign of the
+    tangential term, a transposed index order or a dropped column fails."""
+    nb, a, N, area = 36, 2.5, 60, 5000.0
+    rng = np.random.default_rng(11)
+    dth = math.pi / nb
+    hist = np.zeros((nb, 3))
+    vir = np.zeros((2, 2))
+    ncont = 0
+    for b in range(nb):
+        for _ in range(int(rng.integers(0, 4))):
+            th = (b + 0.5) * dth
+            Fn = float(rng.uniform(0.1, 2.0))
+            xi = float(rng.uniform(-1.0, 1.0)) * Fn
+            n = np.array([math.cos(th), math.sin(th)])
+            t = np.array([-math.sin(th), math.cos(th)])
+            Fa = Fn * n - xi * t
+            torque = np.cross(np.append(-a * n, 0.0), np.append(Fa, 0.0))[2]
+            assert torque == pytest.approx(a * xi, abs=1e-14)   # CCW for xi > 0
+            hist[b] += [1, Fn, xi]
+            vir += np.outer(Fa, 2 * a * n)          # F_alpha r_beta
+            ncont += 1
+    assert np.abs(vir - vir.T).max() > 1e-3 * np.abs(vir).max()   # asymmetric on purpose
+    phi = N * math.pi * a * a / area
+    Z = 2 * ncont / N
+    sig = O.angular_stress(hist, phi, Z, a, True)
+    np.testing.assert_allclose(sig[:2, :2], vir / area, rtol=1e-12, atol=1e-15)
+
+
 def test_histogram_of_a_single_contact():
     """A single overlapping pair, fluid held at rest: one histogram count in
     the bin of the contact angle, the normal force of the spring law, and the
@@ -674,6 +813,39 @@ def test_histogram_of_a_single_contact():
     n = np.array([math.cos(th), math.sin(th), 0.0])
     expect = -np.outer(r * n, kn * 0.1 * n) / 40 ** 3
     np.testing.assert_allclose(sig, expect, rtol=1e-8, atol=1e-18)
+
+
+@pytest.mark.parametrize("th,tip_first", [(math.pi / 2, True), (math.pi / 2, False), (0.9, True),
+                                           (2.4, False)])
+def test_histogram_tangential_column_is_counter_clockwise(th, tip_first):
+    """Sec. 3.2, Eq. 22: the tangential column of the histogram is the
+    tangential contact force counted positive when it turns the spheres
+    counter-clockwise.  One overlapping pair in the x-y plane, the sphere at
+    the tip of the contact direction n = (cos th, sin th) sliding along the
+    tangent t: the first sub-step loads the tangential spring by the sliding
+    displacement, so the force on the tip sphere is -k_t v dt along the
+    sliding direction.  The expected value is that force's torque about the
+    tip sphere's centre (contact point at -a n) divided by a.  The sphere
+    index order must not matter (a contact counts once, in the bin of the
+    folded angle); the force on the wrong sphere or a flipped tangent fails."""
+    a, r, kn, kt_ratio, vt = 4.5, 8.9, 300.0, 0.2, 0.012
+    n = np.array([math.cos(th), math.sin(th), 0.0])
+    t = np.array([-math.sin(th), math.cos(th), 0.0])
+    tip = np.array([20.0, 20.0, 20.0])
+    base = tip - r * n
+    vtip = vt * t
+    pos, vel = ([tip, base], [vtip, np.zeros(3)]) if tip_first else ([base, tip], [np.zeros(3), vtip])
+    s = O.Oracle(40, 40, 40, radius=[a, a], pos=pos, vel=vel, kn=kn, kt_ratio=kt_ratio,
+                 eta_n=0.0, lub_cut=0.0, mu=1.0, dem_substeps=1)
+    s.step(1)
+    _, hist = s.stress(O.CONTACT)
+    F_tip = -kt_ratio * kn * vtip * 1.0                  # spring loaded over dt = 1
+    expect = np.cross(-a * n, F_tip)[2] / a
+    b = int((th % math.pi) / (math.pi / 36))
+    assert hist[b, 0] == 1 and hist[:, 0].sum() == 1
+    assert hist[b, 1] == pytest.approx(kn * (2 * a - r), rel=1e-9)
+    assert hist[b, 2] == pytest.approx(expect, rel=1e-9)
+    assert abs(expect) == pytest.approx(kt_ratio * kn * vt, rel=1e-12)
 
 
 # ------------------------------------------------------- moduli (Eq. 17, 18)
