@@ -21,10 +21,13 @@
 //              exactly what the next collide-stream pulls for (r, p) (r - c_p
 //              = s), and no other receiver pulls it, so the lattice kernel
 //              streams plainly over solid sources.  A node of another
-//              particle in place of r counts as fluid at rest
-//              (f = 2 C^q rho0 c_q): when two mapped spheres come closer than
-//              one lattice spacing their solid nodes touch, and without this
-//              the rest pressure on each particle would not balance.
+//              particle j in place of r (mapped spheres closer than one
+//              spacing) counts as fluid in equilibrium moving with the mean
+//              ubar of the two surfaces' velocities at r_b, against a wall
+//              moving with ubar: f = C^q rho0 (2 + 9 (ubar.c_q)^2 -
+//              3 ubar^2) c_q.  The pressure on each particle then balances at
+//              rest and in a flow moving with both, and the reverse link of j
+//              cancels it exactly.
 // One block per particle scans the cells of the particle's bounding boxes
 // (one per Lees-Edwards image that reaches into the box).  Per-particle sums
 // use a fixed-order block reduction, so they are deterministic.
@@ -441,7 +444,10 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
         const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
         const TC wqq = wq<TC>(q);
         // fluid receiver: momentum exchange and the bounce-back value for the
-        // next pull; another particle's node: fluid at rest
+        // next pull; another particle's node: fluid in equilibrium moving with
+        // the mean ubar of the two surfaces' velocities at r_b, against a wall
+        // moving with ubar, 2 n^eq_q(rho0, rho0 ubar) - 6 C^q rho0 ubar.c_q
+        // = C^q rho0 (2 + 9 (ubar.c_q)^2 - 3 ubar^2)
         TC mag;
         if (ow[u] < 0) {
           const TC wall = (TC)6 * wqq * rho0 * cu;
@@ -451,7 +457,15 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
             f[(long long)p[u] * v.ncell + sidx] = S::enc(nq[u] - wall, (TC)D3Q19::w(p[u]) * rho0, (TC)v.scale);
           }
         } else {
-          mag = (TC)2 * wqq * rho0;
+          const TC* pj = reinterpret_cast<const TC*>(v.plb) + 12 * ow[u];
+          TC ex = (TC)rx[u] + (TC)0.5 * cqx - pj[0], ey = (TC)ry[u] + (TC)0.5 * cqy - pj[1],
+             ez = (TC)rz[u] + (TC)0.5 * cqz - pj[2];
+          const int kj = le_image_v(v, ex, ey, ez, delta);
+          const TC mx = (TC)0.5 * (ubx + pj[3] + (pj[7] * ez - pj[8] * ey) + (TC)kj * ule);
+          const TC my = (TC)0.5 * (uby + pj[4] + (pj[8] * ex - pj[6] * ez));
+          const TC mz = (TC)0.5 * (ubz + pj[5] + (pj[6] * ey - pj[7] * ex));
+          const TC cm = mx * cqx + my * cqy + mz * cqz;
+          mag = wqq * rho0 * ((TC)2 + (TC)9 * cm * cm - (TC)3 * (mx * mx + my * my + mz * mz));
         }
         const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
         acc[0] += fx; acc[1] += fy; acc[2] += fz;

@@ -626,7 +626,10 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
             for (int x = 0; x < 3; ++x)
               for (int y = 0; y < 3; ++y) cv[3 * x + y] += (T)0.5 * (r[x] * o.Fc[y] + r[y] * o.Fc[x]);
             // contact angle theta in [0, pi) and the tangential direction
-            // (-sin theta, cos theta) of the unfolded angle (Eq. 26, 27)
+            // t = (-sin theta, cos theta) of the unfolded angle (Eq. 26, 27);
+            // the tangential force is counted positive when it turns the
+            // spheres counter-clockwise, -(F_a . t) (a's contact point lies
+            // at -a n from its centre)
             int bin;
             double ftan;
             if constexpr (sizeof(T) == 8) {
@@ -635,7 +638,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
               if (th < 0.0) th += pi;
               if (th >= pi) th -= pi;
               bin = (int)floor(th / dth);
-              ftan = (double)o.Fc[0] * tx + (double)o.Fc[1] * ty;
+              ftan = -((double)o.Fc[0] * tx + (double)o.Fc[1] * ty);
             } else {
               // FP32 angles: the same bins but at the edges; the direction
               // straight from r (no trigonometry)
@@ -646,7 +649,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
               if (th < 0.0f) th += pf;
               if (th >= pf) th -= pf;
               bin = (int)floorf(th * ((float)v.nbins / pf));
-              ftan = (double)((float)o.Fc[0] * tx + (float)o.Fc[1] * ty);
+              ftan = -(double)((float)o.Fc[0] * tx + (float)o.Fc[1] * ty);
             }
             if (bin >= v.nbins) bin = v.nbins - 1;
             if (bin < 0) bin = 0;

@@ -36,6 +36,16 @@ def _pop_err(g, o):
     return np.abs(fg[:, fl] - fo[:, fl]).max() / np.abs(fo[:, fl]).max()
 
 
+def _assert_hist_equal(hg, ho):
+    """FP64 angular histograms (Eq. 19-23) bin by bin: contact counts exactly,
+    the summed normal and counter-clockwise tangential forces to 1e-9 of the
+    largest bin."""
+    assert (hg[:, 0] == ho[:, 0]).all()
+    for col in (1, 2):
+        scale = max(np.abs(ho[:, col]).max(), 1e-300)
+        assert np.abs(hg[:, col] - ho[:, col]).max() <= 1e-9 * scale, col
+
+
 def _params(w, **over):
     kw = dict(w.params)
     kw.update(over)
@@ -148,8 +158,9 @@ def test_dense_contacts_lubrication_repulsion_fp64():
         sg, hg = g.stress(kind)
         so, ho = o.stress(kind)
         assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
-    assert (hg[:, 0] == ho[:, 0]).all()
+    _assert_hist_equal(hg, ho)
     assert hg[:, 0].sum() > 0, "the run should have contacts"
+    assert np.abs(hg[:, 2]).max() > 0, "the run should have tangential contact forces"
     assert np.abs(g.stress(S.LUBRICATION)[0]).max() > 0, "the run should have lubricated pairs"
 
 
@@ -174,9 +185,60 @@ def test_cell_list_and_two_particles_per_warp_fp64():
     assert (g.owner() == o.owner()).all()
     assert _pop_err(g, o) < 1e-12
     for kind in (S.CONTACT, S.TOTAL):
-        sg, _ = g.stress(kind)
-        so, _ = o.stress(kind)
+        sg, hg = g.stress(kind)
+        so, ho = o.stress(kind)
         assert np.abs(sg - so).max() <= 1e-9 * max(np.abs(so).max(), 1e-300), kind
+    _assert_hist_equal(hg, ho)
+
+
+@pytest.mark.parametrize("case", ["rest", "comoving", "relative", "moving_le"])
+def test_touching_spheres_fp64(case):
+    """Mapped spheres closer than one spacing (Appendix A (i)): links between
+    the two solids carry the equilibrium of the surfaces' mean velocity.  A
+    held pair at rest and a held pair moving with its uniform fluid feel no
+    force (to round-off, on both sides); a held pair in relative motion, and
+    a free pair in relative motion crossing the Lees-Edwards plane under
+    shear, match the oracle's forces, torques, centres and populations."""
+    d = np.array([0.6, 0.48, 0.64])
+    R0 = np.array([8.3, 9.1, 8.7])
+    sh = dict(kind=0, rate=0.0)
+    held = case != "moving_le"
+    if case == "moving_le":
+        R0 = np.array([8.3, 21.5, 8.7])        # the pair straddles y = L_y
+        sh = dict(kind=0, rate=2e-3)
+    if case in ("relative", "moving_le"):
+        vel = [[0.02, -0.01, 0.005], [-0.015, 0.01, 0.02]]
+    else:
+        U = [0.03, -0.02, 0.012] if case == "comoving" else [0.0, 0.0, 0.0]
+        vel = [U, U]
+    pos = [R0, (R0 + 8.0 * d) % 24.0]
+    g, o = _both(24, 24, 24, [4.0, 4.0], pos, vel=vel, move_particles=not held, kn=1e3,
+                 lub_cut=0.5, dem_substeps=4)
+    if case == "comoving":
+        feq = O.equilibrium(1.0, np.array(vel[0]))
+        f0 = np.broadcast_to(feq[:, None], (19, 24 ** 3)).copy()
+        g.set_populations(f0)
+        o.set_populations(f0)
+    assert (g.owner() == o.owner()).all()
+    _step(g, o, 5, **sh)
+    assert (g.owner() == o.owner()).all()
+    assert _pop_err(g, o) < 1e-12
+    Rg, Ug, _ = g.particles()
+    Ro, Uo, _ = o.particles()
+    assert np.abs(Rg - Ro).max() < 1e-9 and np.abs(Ug - Uo).max() < 1e-9
+    # the library holds the link sums that the next step applies, the oracle
+    # those of the step it took last: one more oracle step lines them up
+    Fg, Tg = g.hydro()
+    o.step(1, O.shear(**sh))
+    Fo, To = o.hydro()
+    if case in ("relative", "moving_le"):
+        scale = np.abs(Fo).max()
+        assert scale > 1e-4
+        assert np.abs(Fg - Fo).max() <= 1e-10 * scale
+        assert np.abs(Tg - To).max() <= 1e-10 * np.abs(To).max()
+    else:
+        assert np.abs(Fg).max() < 1e-13 and np.abs(Tg).max() < 1e-12
+        assert np.abs(Fo).max() < 1e-13
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
