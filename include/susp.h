@@ -222,7 +222,8 @@ susp_status susp_profile_stages(susp *h, double *ms, int *steps);
  * device allocation, or a loop that must not touch the allocator.  It advances
  * a particle-free FP32 box by one step -- the same collide-stream and
  * Lees-Edwards planes as susp_step -- from f_in to f_out (device pointers,
- * [19][nz][ny][nx] post-collision populations, caller-owned, not aliased),
+ * [19][nz][ny][nx] post-collision populations, caller-owned; overlapping
+ * f_in and f_out ranges are rejected with SUSP_EINVAL),
  * with Lees-Edwards offset delta and image velocity u_le for this step, and
  * writes the step's viscous stress (3 x 3, row-major, per unit volume) to the
  * device pointer visc_out.  Its scratch (plane moments and block partials)
@@ -230,7 +231,10 @@ susp_status susp_profile_stages(susp *h, double *ms, int *steps);
  * every GPU that loads the library until the process exits; boxes with
  * nx * nz > 65536 are rejected with SUSP_EINVAL.  The first call on a device
  * looks up that array's address (cudaGetSymbolAddress), so make the first
- * call on each device before any stream capture.  All calls share the array:
+ * call on each device before any stream capture; the address is kept per
+ * device with the ID of the CUDA context it belongs to and looked up again
+ * when another context is current (after a device reset, for instance).  All
+ * calls share the array:
  * calls that overlap on the GPU race.  Nothing is allocated; asynchronous on
  * cuda_stream.  Errors: SUSP_EINVAL, SUSP_ECUDA. */
 susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double tau, double delta, double u_le,

@@ -196,21 +196,38 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
   TC sp[9], dp[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) { sp[k] = n[2 * k + 1] + n[2 * k + 2]; dp[k] = n[2 * k + 1] - n[2 * k + 2]; }
+  // second moments: for FP32 arithmetic from the deviations n - C^q rho0
+  // (exact differences), so that Pi - rho I / 3 does not cancel two values of
+  // size 1/3; rsec is then rho - rho0 instead of rho
+  TC ss[9], rsec;
+  if constexpr (P == 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ss[k] = sp[k];
+    rsec = n[0];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const TC wr = (TC)D3Q19::w(2 * k + 1) * rho0;
+      ss[k] = (n[2 * k + 1] - wr) + (n[2 * k + 2] - wr);
+    }
+    rsec = n[0] - (TC)D3Q19::w(0) * rho0;
+  }
   TC rho = n[0], jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int q = 2 * k + 1;
     const int cxq = D3Q19::cx(q), cyq = D3Q19::cy(q), czq = D3Q19::cz(q);
     rho += sp[k];
+    rsec += ss[k];
     if (cxq) jx += cxq > 0 ? dp[k] : -dp[k];
     if (cyq) jy += cyq > 0 ? dp[k] : -dp[k];
     if (czq) jz += czq > 0 ? dp[k] : -dp[k];
-    if (cxq) pxx += sp[k];
-    if (cyq) pyy += sp[k];
-    if (czq) pzz += sp[k];
-    if (cxq && cyq) pxy += cxq * cyq > 0 ? sp[k] : -sp[k];
-    if (cxq && czq) pxz += cxq * czq > 0 ? sp[k] : -sp[k];
-    if (cyq && czq) pyz += cyq * czq > 0 ? sp[k] : -sp[k];
+    if (cxq) pxx += ss[k];
+    if (cyq) pyy += ss[k];
+    if (czq) pzz += ss[k];
+    if (cxq && cyq) pxy += cxq * cyq > 0 ? ss[k] : -ss[k];
+    if (cxq && czq) pxz += cxq * czq > 0 ? ss[k] : -ss[k];
+    if (cyq && czq) pyz += cyq * czq > 0 ? ss[k] : -ss[k];
   }
   if (!(rho > (TC)0)) atomicOr(v.err, ERR_UNSTABLE);
   const TC inv = (TC)1 / rho;
@@ -227,7 +244,7 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
     //   Pi* = (1 + lambda) bar(Pi^neq) + (1 + lambda_v) tr(Pi^neq) I / 3,
     // the ghost modes removed; viscous stress -(1 + lambda/2) of the
     // traceless and -(1 + lambda_v/2) of the isotropic non-equilibrium stress
-    const TC third = rho / (TC)3;
+    const TC third = rsec / (TC)3;
     const TC nxx = pxx - jx * jx * inv - third, nyy = pyy - jy * jy * inv - third, nzz = pzz - jz * jz * inv - third;
     const TC nxy = pxy - jx * jy * inv, nxz = pxz - jx * jz * inv, nyz = pyz - jy * jz * inv;
     const TC ls = sel<TC>(v.ls_d, v.ls_f), lb = sel<TC>(v.lb_d, v.lb_f);
@@ -306,7 +323,7 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
     fout[(uint32_t)(q + 1) * nc + (uint32_t)idx] = S::enc(oo, w * rho0, (TC)v.scale);
   }
   const TC vf = sel<TC>(v.vf_d, v.vf_f);
-  const TC third = rho / (TC)3;
+  const TC third = rsec / (TC)3;
   acc[0] += vf * (pxx - jx * jx * inv - third);
   acc[1] += vf * (pyy - jy * jy * inv - third);
   acc[2] += vf * (pzz - jz * jz * inv - third);
@@ -316,101 +333,228 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
 }
 
 // ---------------------------------------------------------------------------
-// Staged pulls (FP32 storage).  Each lane copies, one row ahead, the source
-// populations of its node and its owner word from global into shared memory
-// with cp.async, and computes the current row from the previous stage while
-// the next row's copies are in flight.  A lane only ever reads the slots it
-// filled, so no barrier is needed.  Pulls across a Lees-Edwards plane keep
-// their direct path.  (For 16-bit storage the extra registers of the staging
-// cost more occupancy than the overlap gains; those types pull directly.)
+// Row pairs (FP32 compute over FP32, FP16 or BF16 storage).  A lane takes the
+// node (x, y, z) and the node above it, (x, y + 1, z), both off the
+// Lees-Edwards planes, and carries the two through the same arithmetic with
+// the packed FP32x2 instructions of sm_100+ (one instruction per operation
+// for both nodes, each an ordinary FP32 rounding).  The collision runs on
+// deviations from the rest state, u = s (n - C^q rho0) with the storage's
+// scale s (1 for FP32 and BF16): the deviation storages hold u itself, and
+// FP32 storage subtracts C^q rho0 on load (exact, the two are within a factor
+// of two) and adds it back through the stored constants.  The moments of the
+// deviations carry no cancellation against the rest state (Pi_xx - rho / 3 is
+// formed from values of size n^neq, not of size 1/3).  With R = sum_q u_q,
+// J = sum_q u_q c_q and iota = 1 / (R + s rho0) = 1 / (s rho):
+//   u^eq_q = C^q [R + 3 J.c_q + (4.5 (J.c_q)^2 - 1.5 J.J) iota],
+//   u*_q   = u_q + omega (u^eq_q - u_q),
+// which is n^eq of Eq. 4 and the BGK relaxation of Eq. 5 in those units; the
+// viscous stress -(1 - 1/(2 tau)) Pi^neq is (Pi_u - J J iota - R I / 3) times
+// the same factor and 1 / s.  A solid node loads nothing (its loads are
+// predicated off, so it reads no memory; its deviations are zero) and stores
+// the rest state, which nothing reads: the link kernel rewrites every slot
+// that a receiver pulls.
 // ---------------------------------------------------------------------------
-constexpr int STAGE_WORDS = 20;   // 19 populations + owner word
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_s(float a) { return make_float2(a, a); }
 
-__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+template <int P> struct Raw;
+template <> struct Raw<1> {
+  __device__ static float ld(const float* f, uint32_t e) { return __ldg(f + e); }
+  __device__ static void st(float* f, uint32_t e, float u) { f[e] = u; }
+};
+template <> struct Raw<2> {
+  __device__ static float ld(const __half* f, uint32_t e) { return __half2float(__ldg(f + e)); }
+  __device__ static void st(__half* f, uint32_t e, float u) { f[e] = __float2half_rn(u); }
+};
+template <> struct Raw<3> {
+  __device__ static float ld(const __nv_bfloat16* f, uint32_t e) { return __bfloat162float(__ldg(f + e)); }
+  __device__ static void st(__nv_bfloat16* f, uint32_t e, float u) { f[e] = __float2bfloat16_rn(u); }
+};
 
-// Issue the copies of node (y, idx) into the stage words at sbase (word q at
-// sbase + 128 q bytes, owner word at word 19).
-template <int P, bool BND>
-__device__ __forceinline__ void stage_issue(const View& v, const typename Store<P>::T* __restrict__ fin,
-                                            uint32_t sbase, int y, int idx, int dxm, int dxp, int dzm, int dzp) {
-  using T = typename Store<P>::T;
-  const uint32_t nc = (uint32_t)v.ncell;
-  const int nx = v.nx;
-  const char* fb = reinterpret_cast<const char*>(fin);
-#pragma unroll
-  for (int p = 0; p < 19; ++p) {
-    const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
-    if (BND && cpy != 0) {
-      const int sy = y - cpy;
-      if (sy < 0 || sy >= v.ny) continue;   // crossing pull: read directly by le_pull
-    }
-    const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
-    const uint32_t e = (uint32_t)p * nc + (uint32_t)(idx + off);
-    const size_t byte = ((size_t)e * sizeof(T)) & ~(size_t)3;
-    cp_async4(sbase + 128u * (uint32_t)p, fb + byte);
-  }
-  cp_async4(sbase + 128u * 19u, v.owner + idx);
+// +c or -c of a packed pair by the sign of a lattice component (0: nothing).
+template <int c>
+__device__ __forceinline__ float2 p_acc(float2 acc, float2 v) {
+  if constexpr (c > 0) return p_add(acc, v);
+  else if constexpr (c < 0) return p_sub(acc, v);
+  else return acc;
 }
 
-template <int P, int p, bool BND>
-struct StagedAll {
-  __device__ __forceinline__ static void run(const View& v, const typename Store<P>::T* __restrict__ fin,
-                                             const typename Store<P>::C* __restrict__ plb,
-                                             const Proto* __restrict__ pr, int x, int y, int z, int idx,
-                                             int dxm, int dxp, int dzm, int dzp, typename Store<P>::C rho0,
-                                             const uint32_t* sw, typename Store<P>::C (&n)[19]) {
-    using TC = typename Store<P>::C;
+template <int P, int p>
+struct PairPull {
+  __device__ __forceinline__ static void run(const typename Store<P>::T* __restrict__ fin, uint32_t nc, int nx,
+                                             uint32_t iA, int dxm, int dxp, int dzm, int dzp, bool fA, bool fB,
+                                             float rest, float2 (&u)[19]) {
     constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
-    const int sy = y - cpy;
-    if (BND && cpy != 0 && (sy < 0 || sy >= v.ny)) {
-      n[p] = le_pull<P, p>(v, fin, plb, pr, x, y, z, idx);
-    } else {
-      const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * v.nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
-      const uint32_t e = (uint32_t)p * (uint32_t)v.ncell + (uint32_t)(idx + off);
-      n[p] = Store<P>::from_word(sw[32 * p], e, (TC)D3Q19::w(p) * rho0, (TC)v.inv_scale);
-    }
-    StagedAll<P, p + 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, sw, n);
+    const int off = (cpx == 1 ? dxm : (cpx == -1 ? dxp : 0)) - cpy * nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
+    const uint32_t e = (uint32_t)p * nc + iA + (uint32_t)off;
+    // FP32 storage holds n: its deviation from C^q rho0 (rho0 = rest / C^0)
+    const float r = (P == 1) ? (float)D3Q19::w(p) * rest : 0.0f;
+    u[p].x = fA ? Raw<P>::ld(fin, e) - r : 0.0f;
+    u[p].y = fB ? Raw<P>::ld(fin, e + (uint32_t)nx) - r : 0.0f;
+    PairPull<P, p + 1>::run(fin, nc, nx, iA, dxm, dxp, dzm, dzp, fA, fB, rest, u);
   }
 };
-template <int P, bool BND>
-struct StagedAll<P, 19, BND> {
-  __device__ __forceinline__ static void run(const View&, const typename Store<P>::T* __restrict__,
-                                             const typename Store<P>::C* __restrict__, const Proto* __restrict__,
-                                             int, int, int, int, int, int, int, int, typename Store<P>::C,
-                                             const uint32_t*, typename Store<P>::C (&)[19]) {}
+template <int P>
+struct PairPull<P, 19> {
+  __device__ __forceinline__ static void run(const typename Store<P>::T* __restrict__, uint32_t, int, uint32_t,
+                                             int, int, int, int, bool, bool, float, float2 (&)[19]) {}
 };
 
-// One lattice node from its staged words (sw: word 0 of this lane).
-template <int P, bool BND>
-__device__ __forceinline__ void lb_node_staged(const View& v, const typename Store<P>::T* __restrict__ fin,
-                                               typename Store<P>::T* __restrict__ fout, int x, int y, int z,
-                                               int dzm, int dzp, typename Store<P>::C (&acc)[6],
-                                               const uint32_t* sw) {
-  using TC = typename Store<P>::C;
-  using S = Store<P>;
-  const int nx = v.nx;
-  const int idx = x + nx * (y + v.ny * z);
-  const uint32_t nc = (uint32_t)v.ncell;
-  const TC rho0 = sel<TC>(v.rho0, v.rho0_f);
-  if ((int)sw[32 * 19] >= 0) {
-#pragma unroll
-    for (int q = 0; q < 19; ++q)
-      fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc((TC)D3Q19::w(q) * rho0, (TC)D3Q19::w(q) * rho0, (TC)v.scale);
-    return;
+// Collision of the opposite pair (q, q + 1), q = 2k + 1, and its stores.
+template <int P, int k>
+struct PairCollide {
+  __device__ __forceinline__ static void run(typename Store<P>::T* __restrict__ fout, uint32_t nc, uint32_t iA,
+                                             int nx, const float2 (&u)[19], float2 jx, float2 jy, float2 jz,
+                                             float2 omc, float2 a1, float2 b1, float2 a2, float2 b2, float c1,
+                                             float c2, bool hg, float g0, float g1, float g2) {
+    constexpr int q = 2 * k + 1;
+    constexpr int cx = D3Q19::cx(q), cy = D3Q19::cy(q), cz = D3Q19::cz(q);
+    constexpr bool first = (q <= 6);   // C^q = 1/18, else 1/36
+    float2 jc = make_float2(0.0f, 0.0f);
+    if constexpr (cx != 0 && cy == 0 && cz == 0) jc = cx > 0 ? jx : p_sub(jc, jx);
+    else if constexpr (cx == 0 && cy != 0 && cz == 0) jc = cy > 0 ? jy : p_sub(jc, jy);
+    else if constexpr (cx == 0 && cy == 0 && cz != 0) jc = cz > 0 ? jz : p_sub(jc, jz);
+    else {
+      jc = p_acc<cx>(jc, jx);
+      jc = p_acc<cy>(jc, jy);
+      jc = p_acc<cz>(jc, jz);
+    }
+    const float2 sym = p_fma(p_mul(jc, jc), first ? b1 : b2, first ? a1 : a2);
+    const float2 anti = p_mul(jc, p_s(first ? c1 : c2));
+    float2 plus = p_add(sym, anti), minus = p_sub(sym, anti);
+    if (hg) {
+      // body force 3 C^q (g . c_q) (g given in storage units times 3)
+      float gc = 0.0f;
+      if constexpr (cx != 0) gc += cx > 0 ? g0 : -g0;
+      if constexpr (cy != 0) gc += cy > 0 ? g1 : -g1;
+      if constexpr (cz != 0) gc += cz > 0 ? g2 : -g2;
+      const float gq = (first ? 1.0f / 18.0f : 1.0f / 36.0f) * gc;
+      plus = p_add(plus, p_s(gq));
+      minus = p_sub(minus, p_s(gq));
+    }
+    const float2 oq = p_fma(omc, u[q], plus);
+    const float2 oo = p_fma(omc, u[q + 1], minus);
+    const uint32_t eq = (uint32_t)q * nc + iA, eo = (uint32_t)(q + 1) * nc + iA;
+    Raw<P>::st(fout, eq, oq.x);
+    Raw<P>::st(fout, eq + (uint32_t)nx, oq.y);
+    Raw<P>::st(fout, eo, oo.x);
+    Raw<P>::st(fout, eo + (uint32_t)nx, oo.y);
+    PairCollide<P, k + 1>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, g0, g1, g2);
   }
-  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
-  TC n[19];
-  StagedAll<P, 0, BND>::run(v, fin, reinterpret_cast<const TC*>(v.plb), v.proto, x, y, z, idx, dxm, dxp, dzm, dzp,
-                            rho0, sw, n);
-  lb_collide<P>(v, fout, idx, n, acc);
+};
+template <int P>
+struct PairCollide<P, 9> {
+  __device__ __forceinline__ static void run(typename Store<P>::T* __restrict__, uint32_t, uint32_t, int,
+                                             const float2 (&)[19], float2, float2, float2, float2, float2, float2,
+                                             float2, float2, float, float, bool, float, float, float) {}
+};
+
+// Moments of the packed pulled values: R, J and the second moments Pi_u.
+template <int k>
+__device__ __forceinline__ void pair_moments(const float2 (&u)[19], float2& R, float2& jx, float2& jy, float2& jz,
+                                             float2& pxx, float2& pyy, float2& pzz, float2& pxy, float2& pxz,
+                                             float2& pyz) {
+  if constexpr (k < 9) {
+    constexpr int q = 2 * k + 1;
+    constexpr int cx = D3Q19::cx(q), cy = D3Q19::cy(q), cz = D3Q19::cz(q);
+    const float2 sp = p_add(u[q], u[q + 1]), dp = p_sub(u[q], u[q + 1]);
+    R = p_add(R, sp);
+    jx = p_acc<cx>(jx, dp);
+    jy = p_acc<cy>(jy, dp);
+    jz = p_acc<cz>(jz, dp);
+    if constexpr (cx != 0) pxx = p_add(pxx, sp);
+    if constexpr (cy != 0) pyy = p_add(pyy, sp);
+    if constexpr (cz != 0) pzz = p_add(pzz, sp);
+    if constexpr (cx != 0 && cy != 0) pxy = p_acc<cx * cy>(pxy, sp);
+    if constexpr (cx != 0 && cz != 0) pxz = p_acc<cx * cz>(pxz, sp);
+    if constexpr (cy != 0 && cz != 0) pyz = p_acc<cy * cz>(pyz, sp);
+    pair_moments<k + 1>(u, R, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz);
+  }
 }
+
+// Two interior nodes (x, y, z) and (x, y + 1, z): pull, BGK collision, store,
+// viscous-stress sums (packed: acc2[k].x and .y for the two nodes).
+template <int P>
+__device__ __forceinline__ void lb_pair(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                        typename Store<P>::T* __restrict__ fout, int x, int y, int z, int dzm,
+                                        int dzp, float2 (&acc2)[6]) {
+  const int nx = v.nx;
+  const uint32_t iA = (uint32_t)(x + nx * (y + v.ny * z));
+  const uint32_t nc = (uint32_t)v.ncell;   // 19 * ncell < 2^32 for every accepted box
+  const bool fA = v.owner[iA] < 0, fB = v.owner[iA + (uint32_t)nx] < 0;
+  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
+  const float rho0 = v.rho0_f;
+  float2 u[19];
+  PairPull<P, 0>::run(fin, nc, nx, iA, dxm, dxp, dzm, dzp, fA, fB, rho0, u);
+  const float2 zero = make_float2(0.0f, 0.0f);
+  float2 R = u[0], jx = zero, jy = zero, jz = zero, pxx = zero, pyy = zero, pzz = zero, pxy = zero,
+         pxz = zero, pyz = zero;
+  pair_moments<0>(u, R, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz);
+  // R + s rho0 is s rho
+  const float su = (P == 2) ? v.scale : 1.0f;
+  const float2 rs = p_add(R, p_s(su * rho0));
+  if ((fA && !(rs.x > 0.0f)) || (fB && !(rs.y > 0.0f))) atomicOr(v.err, ERR_UNSTABLE);
+  const float2 iota = make_float2(__fdividef(1.0f, rs.x), __fdividef(1.0f, rs.y));
+  const float2 jj = p_fma(jz, jz, p_fma(jy, jy, p_mul(jx, jx)));
+  const float2 base = p_fma(p_s(-1.5f), p_mul(jj, iota), R);
+  const float om = v.omega_f;
+  const float2 omc = p_s(1.0f - om);
+  constexpr float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
+  // omega-scaled equilibrium pieces per weight class, with the rest state
+  // that FP32 storage adds back
+  const float rs0 = (P == 1) ? w0 * rho0 : 0.0f, rs1 = (P == 1) ? w1 * rho0 : 0.0f,
+              rs2 = (P == 1) ? w2 * rho0 : 0.0f;
+  const float2 a0 = p_fma(base, p_s(om * w0), p_s(rs0));
+  const float2 a1 = p_fma(base, p_s(om * w1), p_s(rs1)), a2 = p_fma(base, p_s(om * w2), p_s(rs2));
+  const float2 b1 = p_mul(iota, p_s(4.5f * om * w1)), b2 = p_mul(iota, p_s(4.5f * om * w2));
+  const float c1 = 3.0f * om * w1, c2 = 3.0f * om * w2;
+  const float2 o0 = p_fma(omc, u[0], a0);
+  Raw<P>::st(fout, iA, o0.x);
+  Raw<P>::st(fout, iA + (uint32_t)nx, o0.y);
+  const float gs = 3.0f * su;
+  const bool hg = v.has_g != 0;
+  PairCollide<P, 0>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, gs * v.g_f[0],
+                         gs * v.g_f[1], gs * v.g_f[2]);
+  // viscous stress (Pi_u - J J iota - R I / 3) of the fluid nodes
+  const float2 m = make_float2(fA ? 1.0f : 0.0f, fB ? 1.0f : 0.0f);
+  const float2 r3 = p_mul(R, p_s(1.0f / 3.0f));
+  const float2 jxi = p_mul(jx, iota), jyi = p_mul(jy, iota);
+  acc2[0] = p_fma(m, p_sub(p_sub(pxx, p_mul(jx, jxi)), r3), acc2[0]);
+  acc2[1] = p_fma(m, p_sub(p_sub(pyy, p_mul(jy, jyi)), r3), acc2[1]);
+  acc2[2] = p_fma(m, p_sub(p_sub(pzz, p_mul(jz, p_mul(jz, iota))), r3), acc2[2]);
+  acc2[3] = p_fma(m, p_sub(pxy, p_mul(jy, jxi)), acc2[3]);
+  acc2[4] = p_fma(m, p_sub(pxz, p_mul(jz, jxi)), acc2[4]);
+  acc2[5] = p_fma(m, p_sub(pyz, p_mul(jz, jyi)), acc2[5]);
+}
+
+// One node of a row that has no interior partner (a Lees-Edwards plane row,
+// the last row of an odd L_y, or Ladd's operator): the scalar path, kept out
+// of line so that its registers do not count against the row pairs.
+template <int P>
+__device__ __noinline__ void lb_node_single(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                            typename Store<P>::T* __restrict__ fout, int x, int y, int z, int dzm,
+                                            int dzp, float (&acc)[6]) {
+  if (y == 0 || y == v.ny - 1) lb_node<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc);
+  else lb_node<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc);
+}
+
+// Exact division by a runtime divisor d >= 1 for 0 <= n < 2^31 with one
+// multiply-high (Granlund and Montgomery, 1994): m = ceil(2^(31 + l) / d),
+// l = ceil(log2 d), q = floor(n m / 2^(31 + l)).
+struct FastDiv {
+  uint32_t m;
+  int sh;   // l - 1, or -1 for d = 1
+  __device__ void init(uint32_t d) {
+    if (d <= 1) { m = 0; sh = -1; return; }
+    const int l = 32 - __clz((int)(d - 1));
+    m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+    sh = l - 1;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return sh < 0 ? n : (__umulhi(n, m) >> sh); }
+};
 
 // Persistent grid over the 32 (x) by 2^tile_lg (y) tiles of every box (z slowest
 // within a box); each block takes a contiguous range of tiles, sums its nodes'
@@ -423,7 +567,6 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   using TC = typename Store<P>::C;
   using T = typename Store<P>::T;
   __shared__ TC red[32 * 6];
-  __shared__ uint32_t stage[P == 1 ? 8 : 1][2][STAGE_WORDS][32];   // [warp][stage][word][lane]
   __shared__ int s_next;
   const int total = B.tile_off[B.nbox];
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
@@ -459,7 +602,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
       y = (ty << lg) + (k & (th - 1));
     };
     TC acc[6] = {0, 0, 0, 0, 0, 0};
-    if constexpr (P != 1) {
+    if constexpr (P == 0) {
       for (int k = claim(); k < rows; k = claim()) {
         int x, y, z;
         decode(k, x, y, z);
@@ -471,43 +614,35 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
         }
       }
     } else {
-      const uint32_t sb0 = (uint32_t)__cvta_generic_to_shared(&stage[wid][0][0][lx]);
-      const uint32_t sstride = STAGE_WORDS * 32 * 4;
-      // copies of row k into stage s (nothing for rows outside the box; one
-      // copy group per call in every case)
-      auto issue = [&](int k, int s) {
-        int x, y, z;
-        decode(k, x, y, z);
-        if (x < v.nx && y < v.ny) {
-          const int idx = x + v.nx * (y + v.ny * z);
-          const int dxm = x == 0 ? v.nx - 1 : -1, dxp = x == v.nx - 1 ? 1 - v.nx : 1;
-          const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
-          const uint32_t sb = sb0 + sstride * (uint32_t)s;
-          if (y == 0 || y == v.ny - 1) stage_issue<P, true>(v, fin, sb, y, idx, dxm, dxp, dzm, dzp);
-          else stage_issue<P, false>(v, fin, sb, y, idx, dxm, dxp, dzm, dzp);
-        }
-        cp_async_commit();
-      };
-      int cur = claim();
-      if (cur < rows) issue(cur, 0);
-      for (int it = 0; cur < rows; ++it) {
-        const int nxt = claim();
-        if (nxt < rows) {
-          issue(nxt, (it + 1) & 1);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-        int x, y, z;
-        decode(cur, x, y, z);
+      // row pairs (y, y + 1) of a tile (tile heights are even); the tile
+      // decode divides by the box's tile counts with one multiply-high each
+      FastDiv by_tpp, by_ntx;
+      by_tpp.init((uint32_t)tiles_per_plane);
+      by_ntx.init((uint32_t)ntx);
+      float2 acc2[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc2[k] = make_float2(0.0f, 0.0f);
+      const int pairs = rows >> 1;
+      for (int k2 = claim(); k2 < pairs; k2 = claim()) {
+        const int k = 2 * k2;
+        const int lt = t + (k >> lg) - base;
+        const int z = (int)by_tpp.div((uint32_t)lt);
+        const int r = lt - z * tiles_per_plane;
+        const int ty = (int)by_ntx.div((uint32_t)r), tx = r - ty * ntx;
+        const int x = tx * 32 + lx, y = (ty << lg) + (k & (th - 1));
         const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
-        if (x < v.nx && y < v.ny) {
-          const uint32_t* sw = &stage[wid][it & 1][0][lx];
-          if (y == 0 || y == v.ny - 1) lb_node_staged<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
-          else lb_node_staged<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc, sw);
+        if (x >= v.nx || y >= v.ny) continue;
+        // warp-uniform branches: a warp covers the same two rows
+        if (y + 1 >= v.ny || y == 0 || y + 1 == v.ny - 1 || v.ladd) {
+          lb_node_single<P>(v, fin, fout, x, y, z, dzm, dzp, acc);
+          if (y + 1 < v.ny) lb_node_single<P>(v, fin, fout, x, y + 1, z, dzm, dzp, acc);
+        } else {
+          lb_pair<P>(v, fin, fout, x, y, z, dzm, dzp, acc2);
         }
-        cur = nxt;
       }
+      const float vfe = (P == 2) ? v.vf_f * v.inv_scale : v.vf_f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += vfe * (acc2[k].x + acc2[k].y);
     }
     t = te;
     block_sum<TC, 6>(acc, red);
@@ -727,14 +862,18 @@ __global__ void __launch_bounds__(256) k_fluid_step_noalloc(View v, const float*
     float n[19];
     n[0] = __ldg(fin + idx);
     NoAllocPull<1>::run(v, fin, pm, le, x, y, z, xm, xp, zm, zp, n);
-    float rho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    // second moments from the deviations n - C^q (rho0 = 1; exact
+    // differences), so that Pi - rho I / 3 cancels no values of size 1/3
+    float rho = 0, rdev = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
       const float cxq = (float)D3Q19::cx(q), cyq = (float)D3Q19::cy(q), czq = (float)D3Q19::cz(q);
+      const float d = n[q] - (float)D3Q19::w(q);
       rho += n[q];
+      rdev += d;
       jx += n[q] * cxq; jy += n[q] * cyq; jz += n[q] * czq;
-      pxx += n[q] * cxq * cxq; pyy += n[q] * cyq * cyq; pzz += n[q] * czq * czq;
-      pxy += n[q] * cxq * cyq; pxz += n[q] * cxq * czq; pyz += n[q] * cyq * czq;
+      pxx += d * cxq * cxq; pyy += d * cyq * cyq; pzz += d * czq * czq;
+      pxy += d * cxq * cyq; pxz += d * cxq * czq; pyz += d * cyq * czq;
     }
     const float inv = 1.0f / rho;
 #pragma unroll
@@ -742,7 +881,7 @@ __global__ void __launch_bounds__(256) k_fluid_step_noalloc(View v, const float*
       const float fe = feq<float>(q, rho, jx, jy, jz, inv);
       fout[(long long)q * v.ncell + idx] = n[q] - omega * (n[q] - fe);
     }
-    const float third = rho / 3.0f;
+    const float third = rdev / 3.0f;
     acc[0] += vf * (pxx - jx * jx * inv - third);
     acc[1] += vf * (pyy - jy * jy * inv - third);
     acc[2] += vf * (pzz - jz * jz * inv - third);
@@ -770,8 +909,48 @@ __global__ void k_fluid_visc_noalloc(const double* __restrict__ partials, int nb
 }  // namespace susp_dev
 
 namespace {
+// The scratch array's device address belongs to one CUDA context: a device
+// reset, or another context made current on this device, loads the library's
+// module again at another address.  The address is therefore cached per
+// device together with the unique ID of the context it was looked up in
+// (cuCtxGetId, reached through the runtime's driver entry points so that the
+// library does not link libcuda), and looked up again when the current
+// context's ID differs.
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256];
+struct NoAllocAddr {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+NoAllocAddr g_noalloc_addr[256];
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// ID of the context current on this thread; 0 if there is none yet or the
+// driver entry points are unavailable (the caller then looks the address up
+// on every call).  Called with g_noalloc_mu held.
+unsigned long long current_ctx_id() {
+  if (!g_ctx_fns_tried) {
+    g_ctx_fns_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(fn);
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 }  // namespace
 
 void susp_set_last_error(const char* msg);
@@ -788,6 +967,15 @@ extern "C" susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double ta
     susp_set_last_error("susp_fluid_step_noalloc: nx * nz exceeds 65536 (the size of its static scratch)");
     return SUSP_EINVAL;
   }
+  {
+    // the step reads f_in while it writes f_out: the two ranges must be disjoint
+    const unsigned long long bytes = 19ull * (unsigned long long)nx * ny * nz * sizeof(float);
+    const unsigned long long a0 = (unsigned long long)(uintptr_t)f_in, b0 = (unsigned long long)(uintptr_t)f_out;
+    if (a0 < b0 + bytes && b0 < a0 + bytes) {
+      susp_set_last_error("susp_fluid_step_noalloc: f_in and f_out overlap");
+      return SUSP_EINVAL;
+    }
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 256) {
@@ -796,17 +984,25 @@ extern "C" susp_status susp_fluid_step_noalloc(int nx, int ny, int nz, double ta
   }
   void* scratch = nullptr;
   {
-    // first call on this device: look up the device address of the static array
+    // first call in this device's current context: look up the device
+    // address of the static array
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], susp_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_noalloc_ptr[dev] = nullptr;
+    NoAllocAddr& A = g_noalloc_addr[dev];
+    unsigned long long id = current_ctx_id();
+    if (!A.ptr || id == 0 || id != A.ctx_id) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, susp_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        A.ptr = nullptr;
+        A.ctx_id = 0;
         susp_set_last_error("susp_fluid_step_noalloc: cudaGetSymbolAddress failed");
         return SUSP_ECUDA;
       }
+      if (id == 0) id = current_ctx_id();   // the look-up made the primary context current
+      A.ptr = ptr;
+      A.ctx_id = id;
     }
-    scratch = g_noalloc_ptr[dev];
+    scratch = A.ptr;
   }
   View v;
   memset(&v, 0, sizeof v);

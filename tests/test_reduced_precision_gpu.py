@@ -4,9 +4,12 @@ FP32 arithmetic) against the FP64 oracle.
 Storage rounding bounds the per-step error: FP16 keeps 11 significant bits of
 the scaled deviation (relative 2^-11), BF16 8 bits (2^-8); the deviations are
 ~1e-3 of the populations in these flows, so the population error after many
-steps stays near 1e-6 (FP16) and 1e-5 (BF16) of the populations.  The
-time-averaged total stress is compared with the oracle's as a fraction of its
-largest component.
+steps stays near 1e-5 (FP16) and 1e-4 (BF16) of the populations.  The
+time-averaged total stress must agree with the oracle's within 2 % (the
+reduced-precision target), checked as a fraction of its largest component
+and on the shear component alone; measured on GB300 the errors are about
+1e-6 for both storages, so a second bound of 1e-4 guards against a
+regression far inside the target.
 """
 import numpy as np
 import pytest
@@ -18,8 +21,9 @@ from paper_1904_02929_gb300 import susp as S
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,pop_tol,stress_tol", [("fp16", 2e-4, 0.02), ("bf16", 2e-3, 0.05)])
-def test_deviation_storage_against_oracle(prec, pop_tol, stress_tol):
+@pytest.mark.parametrize("prec,pop_tol", [("fp16", 2e-4), ("bf16", 2e-3)])
+def test_deviation_storage_against_oracle(prec, pop_tol):
+    stress_tol = 0.02
     w = I.config_small(precision=prec)
     kw = dict(w.params)
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision=prec, **kw)
@@ -37,6 +41,7 @@ def test_deviation_storage_against_oracle(prec, pop_tol, stress_tol):
     assert err < pop_tol
     assert serr < stress_tol
     assert abs(sg[0, 1] - so[0, 1]) <= stress_tol * abs(so[0, 1])
+    assert serr < 1e-4
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])

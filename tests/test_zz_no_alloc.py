@@ -68,3 +68,16 @@ def test_noalloc_rejects_oversized_box():
     with pytest.raises(S.SuspError) as e:
         S.susp_fluid_step_noalloc(512, 8, 256, 1.0, 0.0, 0.0, 16, 16, 16, 0)
     assert e.value.status == S.SUSP_EINVAL
+
+
+def test_noalloc_rejects_overlapping_buffers():
+    """The step reads f_in while writing f_out, so an in-place or partly
+    overlapping call is refused before anything is launched."""
+    from paper_1904_02929_gb300 import susp as S
+    nx, ny, nz = 8, 8, 8
+    nbytes = 19 * nx * ny * nz * 4
+    base = 1 << 20
+    for f_out in (base, base + nbytes - 4, base - nbytes + 4):
+        with pytest.raises(S.SuspError) as e:
+            S.susp_fluid_step_noalloc(nx, ny, nz, 1.0, 0.0, 0.0, base, f_out, 16, 0)
+        assert e.value.status == S.SUSP_EINVAL
