@@ -202,8 +202,10 @@ def timed_with_retake(run, sampler, agree=lambda flag: flag):
     raise AssertionError("unreachable")
 
 
-def cpu_baseline(w, budget_s: float = 15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(w, budget_s: float = 15.0, keep=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload.
+    ``keep`` (a list), if given, receives the oracle and its step count, so
+    that the GPU result of the same steps can be compared with it."""
     import oracle as O
     kw = dict(w.params)
     o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
@@ -217,6 +219,8 @@ def cpu_baseline(w, budget_s: float = 15.0):
     o.step(k, sh)
     dt = time.perf_counter() - t0
     steps = k
+    if keep is not None:
+        keep.extend([o, 1 + k])
     return {
         "value": w.ncell * steps / dt / 1e6,
         "unit": "MLUPS",
@@ -264,15 +268,20 @@ def batched_leg(ws, steps: int, warmup: int):
     tuned = batch.tune()                            # collide-stream launch shape for this batch
     for g in boxes:
         g.stress_reset()
+    batch.step(1)                                   # capture the step graph untimed
+    torch.cuda.synchronize()
+    ms_b = timed(bs, lambda: batch.step(steps))
+    sb = [g.stress(S.TOTAL)[0][0, 1] for g in boxes]   # raises on any device error flag
+    # stage times: as many further steps, profiled (event nodes in the graph)
     batch.profile(True)
-    batch.step(1)                                   # capture the profiled graph untimed
+    batch.step(1)
     torch.cuda.synchronize()
     batch.profile(True)
-    ms_b = timed(bs, lambda: batch.step(steps))
+    batch.step(steps)
+    torch.cuda.synchronize()
     stages, k1_n = S.susp_batch_profile_stages(batch.b)
     k1_ms = stages["collide_stream"]
     batch.profile(False)
-    sb = [g.stress(S.TOTAL)[0][0, 1] for g in boxes]   # raises on any device error flag
     launches_b = 2 + 5 + 1 + 3                       # planes, collide, cell list + particles, finalize, node map + links
     mem_b = sum(g.nbytes for g in boxes)
     batch.close()
@@ -340,6 +349,136 @@ def batched_leg(ws, steps: int, warmup: int):
     }
 
 
+def profiled_window(g, sh, steps: int, flush=None):
+    """Stage times of ``steps`` further steps of box ``g`` (CUDA events
+    recorded by event nodes inside the replayed step graph, on the box's
+    stream), with an optional L2 flush before each step; profiling off after."""
+    import torch
+    from paper_1904_02929_gb300 import susp as S
+    S.susp_profile(g.h, True)
+    g.step(1, sh)                           # capture the profiled graph, untimed
+    torch.cuda.synchronize()
+    S.susp_profile(g.h, True)               # a new window
+    with torch.cuda.stream(g.stream):
+        for _ in range(steps):
+            if flush is not None:
+                flush.zero_()
+            g.step(1, sh)
+    torch.cuda.synchronize()
+    stages, n = S.susp_profile_stages(g.h)
+    S.susp_profile(g.h, False)
+    return stages, n
+
+
+def errors_vs_oracle(g, o, kinds=("total",)) -> dict:
+    """Errors of a GPU machine against the FP64 oracle after the same steps from
+    the same state: populations over the nodes fluid on both sides (max
+    absolute difference over the oracle's largest value), centres (max
+    absolute difference, lattice units) and the time-averaged stress (max
+    component difference over the oracle's largest component, and the shear
+    component alone)."""
+    import numpy as np
+    import oracle as O
+    from paper_1904_02929_gb300 import susp as S
+    fo, fg = o.populations(), g.populations()
+    fl = (o.owner() < 0) & (g.owner() < 0)
+    out = {"populations": float(np.abs(fg[:, fl] - fo[:, fl]).max() / np.abs(fo[:, fl]).max()),
+           "node_map_agrees": bool((o.owner() == g.owner()).all())}
+    if o.n:
+        out["centres"] = float(np.abs(g.particles()[0] - o.particles()[0]).max())
+    for name in kinds:
+        so = o.stress(getattr(O, name.upper()))[0]
+        sg = g.stress(getattr(S, name.upper()))[0]
+        out[f"stress_{name}"] = float(np.abs(sg - so).max() / np.abs(so).max())
+        out[f"stress_{name}_xy"] = float(abs(sg[0, 1] - so[0, 1]) / abs(so[0, 1]))
+    return out
+
+
+def precision_leg(oracle_96=None, mono_steps: int = 2):
+    """Each storage's error against the FP64 oracle on the workloads whose
+    rows the reduced-precision target names: the 96^3 bulk-shear box in FP32
+    (the oracle of the CPU baseline, same steps), the 512 x 512 x 28 monolayer
+    in FP16 (``mono_steps`` oracle steps), and the 32^3 20-sphere box in FP32,
+    FP16 and BF16 (200 steps at rate 1e-3)."""
+    import oracle as O
+    from paper_1904_02929_gb300 import inputs
+    from paper_1904_02929_gb300 import susp as S
+    out = {}
+    if oracle_96:
+        o, k = oracle_96
+        w = workload()
+        g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **w.params)
+        g.step(k, S.make_shear(**w.shear))
+        out["dst96_fp32"] = dict(errors_vs_oracle(g, o, ("total", "contact", "viscous")), steps=k)
+        g.close()
+    w = inputs.config_monolayer(seed=1003, phi=0.70, Lz=28, gamma0=0.1, precision="fp16")
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **w.params)
+    o.step(mono_steps, O.shear(**w.shear))
+    g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp16", **w.params)
+    g.step(mono_steps, S.make_shear(**w.shear))
+    out["monolayer_fp16"] = dict(errors_vs_oracle(g, o, ("total", "viscous")), steps=mono_steps)
+    g.close()
+    del o
+    w = inputs.config_small()
+    o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **w.params)
+    sh = dict(kind=0, rate=1e-3)
+    o.step(200, O.shear(**sh))
+    for prec in ("fp32", "fp16", "bf16"):
+        g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision=prec, **w.params)
+        g.step(200, S.make_shear(**sh))
+        out[f"small32_{prec}"] = dict(errors_vs_oracle(g, o, ("total",)), steps=200)
+        g.close()
+    out["note"] = ("max relative errors against the FP64 oracle after the same steps from the same "
+                   "state; populations over nodes fluid on both sides")
+    return out
+
+
+def sweep_leg(steps: int, chunk: int = 500):
+    """The bulk-shear sweep at 96^3 in FP32: phi_3 in {0.50, 0.54, 0.58} and
+    shear rate in {1e-5, 1e-4, 1e-3}.  Each point runs up to ``steps`` lattice
+    steps in chunks, reading the device status after every chunk, and
+    reports the steps completed before any flag (the survival of the dense
+    packing under shear), its throughput, and the time-averaged shear stress
+    with the relative viscosity sigma_xy / (eta0 rate)."""
+    import torch
+    from paper_1904_02929_gb300 import inputs
+    from paper_1904_02929_gb300 import susp as S
+    rows = []
+    for phi in (0.50, 0.54, 0.58):
+        for rate in (1e-5, 1e-4, 1e-3):
+            w = inputs.config_dst(phi3=phi, L=96, rate=rate)
+            g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **w.params)
+            sh = S.make_shear(**w.shear)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            done, status, sxy = 0, "ok", None
+            ms = 0.0
+            while done < steps:
+                n = min(chunk, steps - done)
+                torch.cuda.synchronize()
+                a.record(g.stream)
+                g.step(n, sh)
+                b.record(g.stream)
+                try:
+                    st, _ = g.stress(S.TOTAL)       # synchronises; raises on a device flag
+                except S.SuspError as e:
+                    status = S.status_name(e.status)
+                    break
+                ms += a.elapsed_time(b)
+                done += n
+                sxy = float(st[0, 1])
+            info = g.info()
+            g.close()
+            eta0 = w.params["rho0"] * (w.params["tau"] - 0.5) / 3.0
+            rows.append({"phi3": phi, "rate": rate, "particles": w.n, "dem_substeps": info.dem_substeps,
+                         "steps_completed": done, "status": status,
+                         "mlups": w.ncell * done / (ms / 1e3) / 1e6 if done else None,
+                         "particle_steps_per_s": w.n * done / (ms / 1e3) if done else None,
+                         "sigma_xy": sxy, "eta_rel": sxy / (eta0 * rate) if sxy is not None else None})
+    return {"lattice": [96, 96, 96], "storage": "fp32", "steps_per_point": steps, "chunk": chunk,
+            "points": rows,
+            "note": "steps_completed < steps_per_point means the named device flag ended the run"}
+
+
 def monolayer_leg(steps: int, warmup: int):
     """Quasi-2D oscillatory shear at the paper's resolution: 512 x 512 x 28,
     radii 5 / 7 (L_z = 4 a_max), phi = 0.70 (N = 1580), reduced amplitude
@@ -355,10 +494,7 @@ def monolayer_leg(steps: int, warmup: int):
     sh = S.make_shear(**w.shear)
     g.step(warmup, sh)
     tuned = g.tune()
-    S.susp_profile(g.h, True)
-    g.step(1, sh)
-    torch.cuda.synchronize()
-    S.susp_profile(g.h, True)
+    g.step(1, sh)                                   # capture the step graph, untimed
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     with torch.cuda.stream(g.stream):
@@ -367,8 +503,7 @@ def monolayer_leg(steps: int, warmup: int):
         b.record(g.stream)
     b.synchronize()
     ms = a.elapsed_time(b)
-    stages, n = S.susp_profile_stages(g.h)
-    S.susp_profile(g.h, False)
+    stages, n = profiled_window(g, sh, steps)
     g.stress(S.TOTAL)                               # raises on any device error flag
     info = g.info()
     g.close()
@@ -401,10 +536,8 @@ def variant_leg(w, what: str, steps: int, warmup: int, **over):
     sh = S.make_shear(**w.shear)
     g.step(warmup, sh)
     tuned = g.tune()
-    S.susp_profile(g.h, True)
-    g.step(2, sh)
+    g.step(2, sh)                                   # capture the step graph, untimed
     torch.cuda.synchronize()
-    S.susp_profile(g.h, True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
@@ -416,8 +549,7 @@ def variant_leg(w, what: str, steps: int, warmup: int, **over):
             b.record(g.stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    stages, n = S.susp_profile_stages(g.h)
-    S.susp_profile(g.h, False)
+    stages, n = profiled_window(g, sh, steps, flush)
     g.stress(S.TOTAL)                               # raises on any device error flag
     info = g.info()
     g.close()
@@ -436,14 +568,18 @@ def variant_leg(w, what: str, steps: int, warmup: int, **over):
             "launch_shape": tuned, "l2": "flushed between timed steps (256 MB write)"}
 
 
-def serving_leg(duration: float = 5.0, rate: float = 20.0, steps: int = 1000, budget: int = 4 << 30):
-    """Poisson-arriving requests (rate per second, for ``duration`` seconds)
-    drawn 50 / 50 from quasi-2D 512 x 512 and 256 x 256 monolayers (phi
+def serving_leg(requests: int = 40, rate: float = 20.0, steps: int = 5000, budget_frac: float = 0.8):
+    """A fixed horizon of Poisson-arriving requests (rate per second) drawn
+    50 / 50 from quasi-2D 512 x 512 and 256 x 256 monolayers (phi
     0.70 / 0.75 / 0.80) at the paper's resolution (radii 5 / 7, L_z = 28),
-    each ``steps`` lattice steps in FP16 deviation storage, served by
-    continuous batching within an HBM budget; latency percentiles and
-    aggregate MLUPS."""
+    each ``steps`` lattice steps (chunks of 1000) in FP16 deviation storage,
+    served by continuous batching within an HBM budget of ``budget_frac`` of
+    the device's free memory; queue wait, service time and latency
+    percentiles (also per 1000 steps) and aggregate MLUPS."""
+    import torch
     from paper_1904_02929_gb300 import inputs, serve
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(budget_frac * free)
     big = [inputs.config_monolayer(seed=3000 + k, phi=phi, Lz=28, precision="fp16")
            for k, phi in enumerate((0.70, 0.75, 0.80))]
     small = [inputs.config_monolayer(seed=3100 + k, phi=phi, Lx=256, Ly=256, Lz=28, precision="fp16")
@@ -452,13 +588,14 @@ def serving_leg(duration: float = 5.0, rate: float = 20.0, steps: int = 1000, bu
     # the reduced amplitudes of the protocol: at 512 lattice units of height
     # the initial amplitude 1.0 would drive the Lees-Edwards image at 0.3 per
     # step, far outside the lattice-Boltzmann Mach range
-    reqs = serve.poisson_requests(pool, rate, duration, steps, seed=1005, oscillatory_only=True,
-                                  amplitudes=(0.01, 0.1))
+    reqs = serve.poisson_requests(pool, rate, 0.0, steps, seed=1005, oscillatory_only=True,
+                                  amplitudes=(0.01, 0.1), count=requests)
     srv = serve.Server(budget, max_boxes=64, chunk=25, precision="fp16")
     srv.run(reqs)
     rep = srv.report()
     srv.close()
-    rep.update({"arrival_rate_per_s": rate, "arrival_window_s": duration, "steps_per_request": steps,
+    rep.update({"arrival_rate_per_s": rate, "horizon_requests": requests, "steps_per_request": steps,
+                "chunks_per_request": steps // 1000, "hbm_budget_frac_of_free": budget_frac,
                 "storage": "fp16",
                 "pool": "monolayers 512x512x28 and 256x256x28 (radii 5 / 7) at phi 0.70 / 0.75 / 0.80, drawn 50 / 50",
                 "protocol": "oscillatory, gamma0 in {0.01, 0.1}, omega 6e-4, theta in {0, pi/2}"})
@@ -516,6 +653,11 @@ def main():
     ap.add_argument("--no-monolayer", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the Ladd-operator and bumpy-wall legs")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=5000)
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the serving horizon (200 for the full sweep horizon)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -559,7 +701,9 @@ def main():
     torch.cuda.synchronize()
 
     def run_timed():
-        S.susp_profile(g.h, True)           # new timing window for the timed steps
+        # the timed steps replay the plain step graph: the profiled graph's
+        # per-step event-node updates would put host time inside the region
+        S.susp_profile(g.h, False)
         barrier()
         with torch.cuda.stream(g.stream):
             for k in range(K):
@@ -579,9 +723,10 @@ def main():
 
     ms, clk, clk_rejected = timed_with_retake(
         run_timed, lambda: ClockSampler(torch.cuda.current_device()) if rank == 0 else None, agree)
-    stages, k1_n = S.susp_profile_stages(g.h)   # the timed region's steps only
+    # stage times: the same number of steps right after, L2 flushed the same
+    # way, with CUDA events recorded by event nodes inside the replayed graph
+    stages, k1_n = profiled_window(g, sh, K, flush)
     k1_ms = stages["collide_stream"]
-    S.susp_profile(g.h, False)
     st = S.susp_stress(g.h, S.TOTAL, g.nbins)   # raises on any device error flag
     t_max = max_over_ranks(ms, dist)
     mlups = job_throughput(world, w.ncell, K, t_max)
@@ -626,6 +771,10 @@ def main():
                        "parallelism": f"replicas{world}"},
             "particle_steps_per_s": psteps,
             "stage_us": {k: round(1e3 * v / max(k1_n, 1), 1) for k, v in stages.items()},
+            "stage_timing": ("the timed steps replay the plain step graph; stage times and the "
+                             "collide-stream launch time come from as many steps right after, L2 "
+                             "flushed the same way, timed by event nodes inside the replayed graph "
+                             "on the box's stream"),
             "dominant_kernel": dominant_stage(stages),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -658,10 +807,15 @@ def main():
         if world == 1 and not args.no_batched:
             from paper_1904_02929_gb300 import inputs
             line["batched"] = batched_leg(inputs.batch_sweep(), args.batched_steps, args.warmup)
+        if world == 1 and not args.no_sweep:
+            line["sweep"] = sweep_leg(args.sweep_steps)
         if world == 1 and not args.no_serve:
-            line["serving"] = serving_leg()
+            line["serving"] = serving_leg(args.serve_requests)
+        keep = []
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, keep=keep)
+        if world == 1 and not args.no_precision:
+            line["precision"] = precision_leg(keep if keep else None)
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -31,6 +31,8 @@
 // One block per particle scans the cells of the particle's bounding boxes
 // (one per Lees-Edwards image that reaches into the box).  Per-particle sums
 // use a fixed-order block reduction, so they are deterministic.
+#include <type_traits>
+
 #include "susp_dev.cuh"
 
 namespace susp_dev {
@@ -271,11 +273,12 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
   }
 }
 
-// Node that pulls population p from solid node (x, y, z); returns its index.
-// crossing = the pull passes a Lees-Edwards plane.
-__device__ __forceinline__ long long link_target_nr(const View& v, const Proto* pr, int x, int y, int z,
-                                                    int p, int& rx, int& ry, int& rz, bool& crossing) {
-  const int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+// Node that pulls population p (components cp) from solid node (x, y, z);
+// returns its index (< 2^27 nodes per box).  crossing = the pull passes a
+// Lees-Edwards plane.
+__device__ __forceinline__ uint32_t link_target_nr(const View& v, const Proto* pr, int x, int y, int z,
+                                                   int4 cp, int& rx, int& ry, int& rz, bool& crossing) {
+  const int cpx = cp.x, cpy = cp.y, cpz = cp.z;
   ry = y + cpy;
   rz = z + cpz;
   if (rz < 0) rz += v.nz;
@@ -294,7 +297,29 @@ __device__ __forceinline__ long long link_target_nr(const View& v, const Proto* 
     xx = x + cpx + pr->di + 1 - pr->near_hi;
   }
   rx = crossing ? wrapi(xx, v.nx) : wrap1(xx, v.nx);
-  return rx + (long long)v.nx * (ry + (long long)v.ny * rz);
+  return (uint32_t)(rx + v.nx * (ry + v.ny * rz));
+}
+
+// Momentum exchange of a link from node (rx, ry, rz) of particle j into the
+// solid of a particle whose boundary velocity there is ub (direction q into
+// that solid): the node stands for fluid in equilibrium moving with the mean
+// ubar of the two surfaces' velocities at r_b = r + c_q / 2, against a wall
+// moving with ubar, 2 n^eq_q(rho0, rho0 ubar) - 6 C^q rho0 ubar.c_q =
+// C^q rho0 (2 + 9 (ubar.c_q)^2 - 3 ubar^2).  Such links are rare (mapped
+// spheres closer than one spacing); kept out of line so that their registers
+// do not weigh on the link loop.
+template <typename TC>
+__device__ __noinline__ TC touching_link(const View& v, int j, int rx, int ry, int rz, int q, TC ubx, TC uby,
+                                         TC ubz, TC delta, TC ule, TC rho0) {
+  const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+  const TC* pj = reinterpret_cast<const TC*>(v.plb) + 12 * j;
+  TC ex = (TC)rx + (TC)0.5 * cqx - pj[0], ey = (TC)ry + (TC)0.5 * cqy - pj[1], ez = (TC)rz + (TC)0.5 * cqz - pj[2];
+  const int kj = le_image_v(v, ex, ey, ez, delta);
+  const TC mx = (TC)0.5 * (ubx + pj[3] + (pj[7] * ez - pj[8] * ey) + (TC)kj * ule);
+  const TC my = (TC)0.5 * (uby + pj[4] + (pj[8] * ex - pj[6] * ez));
+  const TC mz = (TC)0.5 * (ubz + pj[5] + (pj[6] * ey - pj[7] * ex));
+  const TC cm = mx * cqx + my * cqy + mz * cqz;
+  return wq<TC>(q) * rho0 * ((TC)2 + (TC)9 * cm * cm - (TC)3 * (mx * mx + my * my + mz * mz));
 }
 
 // Links of one particle in two passes: the block first collects its solid
@@ -304,7 +329,7 @@ constexpr int LINK_NODES_MAX = 2048;
 constexpr int LINK_CHUNK = 4608;     // items of one round: up to 18 per node, one node per thread of 256
 
 template <int P>
-__global__ void __launch_bounds__(256) k_links(Batch B) {
+__global__ void __launch_bounds__(256, P == 0 ? 2 : 3) k_links(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 15];
@@ -312,12 +337,21 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
   __shared__ uint32_t s_node[LINK_NODES_MAX];   // packed (x, y, z) of solid surface nodes
   __shared__ uint32_t s_mask[LINK_NODES_MAX];   // their candidate link directions (bits 1-18)
   __shared__ uint32_t s_items[LINK_CHUNK];      // (node << 5 | direction) items of one round
+  __shared__ int4 s_cp[19];                     // c_p of each direction p
+  __shared__ typename std::conditional<sizeof(TC) == 8, double4, float4>::type s_cq[19];   // c_q, C^q of q = -p
   const int g = blockIdx.x;
   const int bx = box_of(B.part_off, B.nbox, g);
   const View& v = B.views[bx];
   const int i = g - B.part_off[bx];
   typename Store<P>::T* __restrict__ f = static_cast<typename Store<P>::T*>(fin_of(v));
   if (threadIdx.x == 0) { s_nodes = 0; s_items_n = 0; }
+  if (threadIdx.x < 19) {
+    // direction tables: the items index them with a runtime direction
+    const int p = threadIdx.x;
+    s_cp[p] = make_int4(D3Q19::cx(p), D3Q19::cy(p), D3Q19::cz(p), 0);
+    s_cq[p].x = (TC)-D3Q19::cx(p); s_cq[p].y = (TC)-D3Q19::cy(p); s_cq[p].z = (TC)-D3Q19::cz(p);
+    s_cq[p].w = (TC)D3Q19::w(p);
+  }
   __syncthreads();
   const TC* pp = reinterpret_cast<const TC*>(v.plb) + 12 * i;
   const TC Rx = pp[0], Ry = pp[1], Rz = pp[2];
@@ -407,9 +441,10 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
     __syncthreads();
     const int ns = s_items_n;
     // two items per thread and pass: both receivers' loads are in flight together
+    const uint32_t nc = (uint32_t)v.ncell;   // 19 * ncell < 2^32 for every accepted box
     for (int k0 = threadIdx.x; k0 < ns; k0 += 2 * blockDim.x) {
       int x[2], y[2], z[2], p[2], rx[2], ry[2], rz[2], ow[2];
-      long long r[2];
+      uint32_t r[2];
       bool crossing[2], live[2];
       TC nq[2];
 #pragma unroll
@@ -420,7 +455,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
         const uint32_t w = s_node[it >> 5];
         p[u] = (int)(it & 31u);
         x[u] = (int)(w & 2047u); y[u] = (int)((w >> 11) & 2047u); z[u] = (int)(w >> 22);
-        r[u] = link_target_nr(v, pr, x[u], y[u], z[u], p[u], rx[u], ry[u], rz[u], crossing[u]);
+        r[u] = link_target_nr(v, pr, x[u], y[u], z[u], s_cp[p[u]], rx[u], ry[u], rz[u], crossing[u]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -428,13 +463,14 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
         // (the population of a solid receiver is read and discarded)
         const int q = D3Q19::opp(p[u]);
         ow[u] = v.owner[r[u]];
-        nq[u] = S::load(f, (long long)q * v.ncell + r[u], wq<TC>(q) * rho0, (TC)v.inv_scale);
+        nq[u] = S::load(f, (uint32_t)q * nc + r[u], s_cq[p[u]].w * rho0, (TC)v.inv_scale);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         if (!live[u] || ow[u] == i) continue;
         const int q = D3Q19::opp(p[u]);
-        const TC cqx = (TC)D3Q19::cx(q), cqy = (TC)D3Q19::cy(q), cqz = (TC)D3Q19::cz(q);
+        const auto cqv = s_cq[p[u]];
+        const TC cqx = cqv.x, cqy = cqv.y, cqz = cqv.z;
         TC dx = (TC)rx[u] + (TC)0.5 * cqx - Rx, dy = (TC)ry[u] + (TC)0.5 * cqy - Ry,
            dz = (TC)rz[u] + (TC)0.5 * cqz - Rz;
         const int kimg = le_image_v(v, dx, dy, dz, delta);
@@ -442,7 +478,7 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
         const TC uby = pp[4] + (pp[8] * dx - pp[6] * dz);
         const TC ubz = pp[5] + (pp[6] * dy - pp[7] * dx);
         const TC cu = ubx * cqx + uby * cqy + ubz * cqz;
-        const TC wqq = wq<TC>(q);
+        const TC wqq = cqv.w;
         // fluid receiver: momentum exchange and the bounce-back value for the
         // next pull; another particle's node: fluid in equilibrium moving with
         // the mean ubar of the two surfaces' velocities at r_b, against a wall
@@ -453,19 +489,11 @@ __global__ void __launch_bounds__(256) k_links(Batch B) {
           const TC wall = (TC)6 * wqq * rho0 * cu;
           mag = (TC)2 * nq[u] - wall;
           if (!crossing[u]) {
-            const long long sidx = x[u] + (long long)v.nx * (y[u] + (long long)v.ny * z[u]);
-            f[(long long)p[u] * v.ncell + sidx] = S::enc(nq[u] - wall, (TC)D3Q19::w(p[u]) * rho0, (TC)v.scale);
+            const uint32_t sidx = (uint32_t)(x[u] + v.nx * (y[u] + v.ny * z[u]));
+            f[(uint32_t)p[u] * nc + sidx] = S::enc(nq[u] - wall, wqq * rho0, (TC)v.scale);
           }
         } else {
-          const TC* pj = reinterpret_cast<const TC*>(v.plb) + 12 * ow[u];
-          TC ex = (TC)rx[u] + (TC)0.5 * cqx - pj[0], ey = (TC)ry[u] + (TC)0.5 * cqy - pj[1],
-             ez = (TC)rz[u] + (TC)0.5 * cqz - pj[2];
-          const int kj = le_image_v(v, ex, ey, ez, delta);
-          const TC mx = (TC)0.5 * (ubx + pj[3] + (pj[7] * ez - pj[8] * ey) + (TC)kj * ule);
-          const TC my = (TC)0.5 * (uby + pj[4] + (pj[8] * ex - pj[6] * ez));
-          const TC mz = (TC)0.5 * (ubz + pj[5] + (pj[6] * ey - pj[7] * ex));
-          const TC cm = mx * cqx + my * cqy + mz * cqz;
-          mag = wqq * rho0 * ((TC)2 + (TC)9 * cm * cm - (TC)3 * (mx * mx + my * my + mz * mz));
+          mag = touching_link<TC>(v, ow[u], rx[u], ry[u], rz[u], q, ubx, uby, ubz, delta, ule, rho0);
         }
         const TC fx = mag * cqx, fy = mag * cqy, fz = mag * cqz;
         acc[0] += fx; acc[1] += fy; acc[2] += fz;

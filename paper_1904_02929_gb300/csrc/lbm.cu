@@ -404,12 +404,19 @@ struct PairPull<P, 19> {
 };
 
 // Collision of the opposite pair (q, q + 1), q = 2k + 1, and its stores.
-template <int P, int k>
+// Relaxed non-equilibrium stress of Ladd's operator (storage units), per node
+// of the pair: Pi* = (1 + lambda) bar(Pi^neq) + (1 + lambda_v) tr(Pi^neq) I / 3
+// and st3 = tr(Pi*) / 3.
+struct PairPi {
+  float2 xx, yy, zz, xy, xz, yz, st3;
+};
+
+template <int P, int k, bool L>
 struct PairCollide {
   __device__ __forceinline__ static void run(typename Store<P>::T* __restrict__ fout, uint32_t nc, uint32_t iA,
                                              int nx, const float2 (&u)[19], float2 jx, float2 jy, float2 jz,
                                              float2 omc, float2 a1, float2 b1, float2 a2, float2 b2, float c1,
-                                             float c2, bool hg, float g0, float g1, float g2) {
+                                             float c2, bool hg, float g0, float g1, float g2, const PairPi& pi) {
     constexpr int q = 2 * k + 1;
     constexpr int cx = D3Q19::cx(q), cy = D3Q19::cy(q), cz = D3Q19::cz(q);
     constexpr bool first = (q <= 6);   // C^q = 1/18, else 1/36
@@ -425,6 +432,19 @@ struct PairCollide {
     const float2 sym = p_fma(p_mul(jc, jc), first ? b1 : b2, first ? a1 : a2);
     const float2 anti = p_mul(jc, p_s(first ? c1 : c2));
     float2 plus = p_add(sym, anti), minus = p_sub(sym, anti);
+    if constexpr (L) {
+      // Ladd: + (9/2) C^q Pi*:(c_q c_q - I/3), the same for q and -q
+      float2 ccp = make_float2(0.0f, 0.0f);
+      if constexpr (cx != 0) ccp = p_add(ccp, pi.xx);
+      if constexpr (cy != 0) ccp = p_add(ccp, pi.yy);
+      if constexpr (cz != 0) ccp = p_add(ccp, pi.zz);
+      if constexpr (cx != 0 && cy != 0) ccp = p_fma(p_s(2.0f * cx * cy), pi.xy, ccp);
+      if constexpr (cx != 0 && cz != 0) ccp = p_fma(p_s(2.0f * cx * cz), pi.xz, ccp);
+      if constexpr (cy != 0 && cz != 0) ccp = p_fma(p_s(2.0f * cy * cz), pi.yz, ccp);
+      const float2 e = p_mul(p_s(4.5f * (first ? 1.0f / 18.0f : 1.0f / 36.0f)), p_sub(ccp, pi.st3));
+      plus = p_add(plus, e);
+      minus = p_add(minus, e);
+    }
     if (hg) {
       // body force 3 C^q (g . c_q) (g given in storage units times 3)
       float gc = 0.0f;
@@ -442,14 +462,15 @@ struct PairCollide {
     Raw<P>::st(fout, eq + (uint32_t)nx, oq.y);
     Raw<P>::st(fout, eo, oo.x);
     Raw<P>::st(fout, eo + (uint32_t)nx, oo.y);
-    PairCollide<P, k + 1>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, g0, g1, g2);
+    PairCollide<P, k + 1, L>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, g0, g1, g2, pi);
   }
 };
-template <int P>
-struct PairCollide<P, 9> {
+template <int P, bool L>
+struct PairCollide<P, 9, L> {
   __device__ __forceinline__ static void run(typename Store<P>::T* __restrict__, uint32_t, uint32_t, int,
                                              const float2 (&)[19], float2, float2, float2, float2, float2, float2,
-                                             float2, float2, float, float, bool, float, float, float) {}
+                                             float2, float2, float, float, bool, float, float, float,
+                                             const PairPi&) {}
 };
 
 // Moments of the packed pulled values: R, J and the second moments Pi_u.
@@ -475,20 +496,18 @@ __device__ __forceinline__ void pair_moments(const float2 (&u)[19], float2& R, f
   }
 }
 
-// Two interior nodes (x, y, z) and (x, y + 1, z): pull, BGK collision, store,
-// viscous-stress sums (packed: acc2[k].x and .y for the two nodes).
-template <int P>
-__device__ __forceinline__ void lb_pair(const View& v, const typename Store<P>::T* __restrict__ fin,
-                                        typename Store<P>::T* __restrict__ fout, int x, int y, int z, int dzm,
-                                        int dzp, float2 (&acc2)[6]) {
+// Collision of a row pair from its pulled deviations u (zero for a solid
+// node), stores and viscous-stress sums (packed: acc2[k].x and .y for the
+// two nodes).  L: Ladd's linear operator, which is the BGK form at
+// omega = 1 plus the relaxed stress term (9/2) C^q Pi*:(c_q c_q - I/3); its
+// viscous stress -(1 + lambda/2) bar(Pi^neq) - (1 + lambda_v/2) tr I / 3 is
+// summed as bar(Pi^neq) + (vfb / vf) tr I / 3, times vf at the end.
+template <int P, bool L>
+__device__ __forceinline__ void pair_collide(const View& v, typename Store<P>::T* __restrict__ fout, uint32_t iA,
+                                             bool fA, bool fB, float2 (&u)[19], float2 (&acc2)[6]) {
   const int nx = v.nx;
-  const uint32_t iA = (uint32_t)(x + nx * (y + v.ny * z));
-  const uint32_t nc = (uint32_t)v.ncell;   // 19 * ncell < 2^32 for every accepted box
-  const bool fA = v.owner[iA] < 0, fB = v.owner[iA + (uint32_t)nx] < 0;
-  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
+  const uint32_t nc = (uint32_t)v.ncell;
   const float rho0 = v.rho0_f;
-  float2 u[19];
-  PairPull<P, 0>::run(fin, nc, nx, iA, dxm, dxp, dzm, dzp, fA, fB, rho0, u);
   const float2 zero = make_float2(0.0f, 0.0f);
   float2 R = u[0], jx = zero, jy = zero, jz = zero, pxx = zero, pyy = zero, pzz = zero, pxy = zero,
          pxz = zero, pyz = zero;
@@ -500,9 +519,32 @@ __device__ __forceinline__ void lb_pair(const View& v, const typename Store<P>::
   const float2 iota = make_float2(__fdividef(1.0f, rs.x), __fdividef(1.0f, rs.y));
   const float2 jj = p_fma(jz, jz, p_fma(jy, jy, p_mul(jx, jx)));
   const float2 base = p_fma(p_s(-1.5f), p_mul(jj, iota), R);
-  const float om = v.omega_f;
+  const float om = L ? 1.0f : v.omega_f;
   const float2 omc = p_s(1.0f - om);
   constexpr float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
+  // non-equilibrium stress Pi_u - J J iota - R I / 3 (Ladd needs it before
+  // the collision, BGK only for the viscous sums)
+  const float2 r3 = p_mul(R, p_s(1.0f / 3.0f));
+  const float2 jxi = p_mul(jx, iota), jyi = p_mul(jy, iota);
+  PairPi pi;
+  float2 nxx, nyy, nzz, nxy, nxz, nyz, t3;
+  if constexpr (L) {
+    nxx = p_sub(p_sub(pxx, p_mul(jx, jxi)), r3);
+    nyy = p_sub(p_sub(pyy, p_mul(jy, jyi)), r3);
+    nzz = p_sub(p_sub(pzz, p_mul(jz, p_mul(jz, iota))), r3);
+    nxy = p_sub(pxy, p_mul(jy, jxi));
+    nxz = p_sub(pxz, p_mul(jz, jxi));
+    nyz = p_sub(pyz, p_mul(jz, jyi));
+    t3 = p_mul(p_add(p_add(nxx, nyy), nzz), p_s(1.0f / 3.0f));
+    const float2 ls = p_s(v.ls_f), lbt = p_mul(p_s(v.lb_f), t3);
+    pi.xx = p_fma(ls, p_sub(nxx, t3), lbt);
+    pi.yy = p_fma(ls, p_sub(nyy, t3), lbt);
+    pi.zz = p_fma(ls, p_sub(nzz, t3), lbt);
+    pi.xy = p_mul(ls, nxy);
+    pi.xz = p_mul(ls, nxz);
+    pi.yz = p_mul(ls, nyz);
+    pi.st3 = lbt;
+  }
   // omega-scaled equilibrium pieces per weight class, with the rest state
   // that FP32 storage adds back
   const float rs0 = (P == 1) ? w0 * rho0 : 0.0f, rs1 = (P == 1) ? w1 * rho0 : 0.0f,
@@ -511,27 +553,52 @@ __device__ __forceinline__ void lb_pair(const View& v, const typename Store<P>::
   const float2 a1 = p_fma(base, p_s(om * w1), p_s(rs1)), a2 = p_fma(base, p_s(om * w2), p_s(rs2));
   const float2 b1 = p_mul(iota, p_s(4.5f * om * w1)), b2 = p_mul(iota, p_s(4.5f * om * w2));
   const float c1 = 3.0f * om * w1, c2 = 3.0f * om * w2;
-  const float2 o0 = p_fma(omc, u[0], a0);
+  float2 o0 = p_fma(omc, u[0], a0);
+  if constexpr (L) o0 = p_fma(p_s(-4.5f * w0), pi.st3, o0);   // c_0 = 0: only the -I/3 part
   Raw<P>::st(fout, iA, o0.x);
   Raw<P>::st(fout, iA + (uint32_t)nx, o0.y);
   const float gs = 3.0f * su;
   const bool hg = v.has_g != 0;
-  PairCollide<P, 0>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, gs * v.g_f[0],
-                         gs * v.g_f[1], gs * v.g_f[2]);
-  // viscous stress (Pi_u - J J iota - R I / 3) of the fluid nodes
+  PairCollide<P, 0, L>::run(fout, nc, iA, nx, u, jx, jy, jz, omc, a1, b1, a2, b2, c1, c2, hg, gs * v.g_f[0],
+                            gs * v.g_f[1], gs * v.g_f[2], pi);
+  // viscous stress of the fluid nodes
   const float2 m = make_float2(fA ? 1.0f : 0.0f, fB ? 1.0f : 0.0f);
-  const float2 r3 = p_mul(R, p_s(1.0f / 3.0f));
-  const float2 jxi = p_mul(jx, iota), jyi = p_mul(jy, iota);
-  acc2[0] = p_fma(m, p_sub(p_sub(pxx, p_mul(jx, jxi)), r3), acc2[0]);
-  acc2[1] = p_fma(m, p_sub(p_sub(pyy, p_mul(jy, jyi)), r3), acc2[1]);
-  acc2[2] = p_fma(m, p_sub(p_sub(pzz, p_mul(jz, p_mul(jz, iota))), r3), acc2[2]);
-  acc2[3] = p_fma(m, p_sub(pxy, p_mul(jy, jxi)), acc2[3]);
-  acc2[4] = p_fma(m, p_sub(pxz, p_mul(jz, jxi)), acc2[4]);
-  acc2[5] = p_fma(m, p_sub(pyz, p_mul(jz, jyi)), acc2[5]);
+  if constexpr (L) {
+    const float2 tb = p_mul(p_s(v.vfb_f / v.vf_f - 1.0f), t3);   // trace part with vfb instead of vf
+    acc2[0] = p_fma(m, p_add(nxx, tb), acc2[0]);
+    acc2[1] = p_fma(m, p_add(nyy, tb), acc2[1]);
+    acc2[2] = p_fma(m, p_add(nzz, tb), acc2[2]);
+    acc2[3] = p_fma(m, nxy, acc2[3]);
+    acc2[4] = p_fma(m, nxz, acc2[4]);
+    acc2[5] = p_fma(m, nyz, acc2[5]);
+  } else {
+    acc2[0] = p_fma(m, p_sub(p_sub(pxx, p_mul(jx, jxi)), r3), acc2[0]);
+    acc2[1] = p_fma(m, p_sub(p_sub(pyy, p_mul(jy, jyi)), r3), acc2[1]);
+    acc2[2] = p_fma(m, p_sub(p_sub(pzz, p_mul(jz, p_mul(jz, iota))), r3), acc2[2]);
+    acc2[3] = p_fma(m, p_sub(pxy, p_mul(jy, jxi)), acc2[3]);
+    acc2[4] = p_fma(m, p_sub(pxz, p_mul(jz, jxi)), acc2[4]);
+    acc2[5] = p_fma(m, p_sub(pyz, p_mul(jz, jyi)), acc2[5]);
+  }
+}
+
+// Two interior nodes (x, y, z) and (x, y + 1, z): pulls straight from global
+// memory, then the collision above.
+template <int P, bool L>
+__device__ __forceinline__ void lb_pair(const View& v, const typename Store<P>::T* __restrict__ fin,
+                                        typename Store<P>::T* __restrict__ fout, int x, int y, int z, int dzm,
+                                        int dzp, float2 (&acc2)[6]) {
+  const int nx = v.nx;
+  const uint32_t iA = (uint32_t)(x + nx * (y + v.ny * z));
+  const uint32_t nc = (uint32_t)v.ncell;   // 19 * ncell < 2^32 for every accepted box
+  const bool fA = v.owner[iA] < 0, fB = v.owner[iA + (uint32_t)nx] < 0;
+  const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
+  float2 u[19];
+  PairPull<P, 0>::run(fin, nc, nx, iA, dxm, dxp, dzm, dzp, fA, fB, v.rho0_f, u);
+  pair_collide<P, L>(v, fout, iA, fA, fB, u, acc2);
 }
 
 // One node of a row that has no interior partner (a Lees-Edwards plane row,
-// the last row of an odd L_y, or Ladd's operator): the scalar path, kept out
+// or the last row of an odd L_y): the scalar path, kept out
 // of line so that its registers do not count against the row pairs.
 template <int P>
 __device__ __noinline__ void lb_node_single(const View& v, const typename Store<P>::T* __restrict__ fin,
@@ -623,22 +690,35 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) acc2[k] = make_float2(0.0f, 0.0f);
       const int pairs = rows >> 1;
-      for (int k2 = claim(); k2 < pairs; k2 = claim()) {
+      // tile column x0, first row y and plane z of pair k2
+      auto pair_at = [&](int k2, int& x0, int& y, int& z) {
         const int k = 2 * k2;
         const int lt = t + (k >> lg) - base;
-        const int z = (int)by_tpp.div((uint32_t)lt);
+        z = (int)by_tpp.div((uint32_t)lt);
         const int r = lt - z * tiles_per_plane;
         const int ty = (int)by_ntx.div((uint32_t)r), tx = r - ty * ntx;
-        const int x = tx * 32 + lx, y = (ty << lg) + (k & (th - 1));
+        x0 = tx * 32;
+        y = (ty << lg) + (k & (th - 1));
+      };
+      // both rows off the Lees-Edwards planes (warp-uniform)
+      auto interior = [&](int y) { return y >= 1 && y + 1 <= v.ny - 2; };
+      auto direct = [&](int x0, int y, int z) {
+        const int x = x0 + lx;
         const int dzm = z == 0 ? (v.nz - 1) * nxny : -nxny, dzp = z == v.nz - 1 ? (1 - v.nz) * nxny : nxny;
-        if (x >= v.nx || y >= v.ny) continue;
-        // warp-uniform branches: a warp covers the same two rows
-        if (y + 1 >= v.ny || y == 0 || y + 1 == v.ny - 1 || v.ladd) {
+        if (x >= v.nx || y >= v.ny) return;
+        if (!interior(y)) {
           lb_node_single<P>(v, fin, fout, x, y, z, dzm, dzp, acc);
           if (y + 1 < v.ny) lb_node_single<P>(v, fin, fout, x, y + 1, z, dzm, dzp, acc);
+        } else if (v.ladd) {
+          lb_pair<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc2);
         } else {
-          lb_pair<P>(v, fin, fout, x, y, z, dzm, dzp, acc2);
+          lb_pair<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc2);
         }
+      };
+      for (int k2 = claim(); k2 < pairs; k2 = claim()) {
+        int x0, y, z;
+        pair_at(k2, x0, y, z);
+        direct(x0, y, z);
       }
       const float vfe = (P == 2) ? v.vf_f * v.inv_scale : v.vf_f;
 #pragma unroll

@@ -186,6 +186,10 @@ class Server:
         ok = [r for r in self.finished if not r.error]
         lat = np.array([r.latency for r in ok])
         per_k = np.array([r.latency * 1000.0 / r.steps for r in ok])
+        wait = np.array([r.admitted - r.arrival for r in ok])
+        svc = np.array([r.done - r.admitted for r in ok])
+        svc_k = np.array([(r.done - r.admitted) * 1000.0 / r.steps for r in ok])
+        pct = lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
         failed = {}
         for r in self.finished:
             if r.error:
@@ -198,6 +202,9 @@ class Server:
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "latency_per_1000_steps_s": {"p50": float(np.percentile(per_k, 50)),
                                          "p99": float(np.percentile(per_k, 99))},
+            "queue_wait_s": pct(wait),
+            "service_s": pct(svc),
+            "service_per_1000_steps_s": pct(svc_k),
             "aggregate_mlups": self.node_steps / self.wall / 1e6,
             "chunks": self.chunks,
             "hbm_budget_bytes": self.budget,
@@ -214,17 +221,22 @@ class Server:
 
 
 def poisson_requests(pool, rate: float, duration: float, steps: int, seed: int,
-                     oscillatory_only: bool = False, amplitudes=(0.1, 1.0)) -> list[Request]:
+                     oscillatory_only: bool = False, amplitudes=(0.1, 1.0),
+                     count: int | None = None) -> list[Request]:
     """Requests arriving as a Poisson process of the given rate over
-    ``duration`` seconds, each a geometry drawn from ``pool`` (Workload
-    objects) with a shear protocol drawn from the sweep's ranges: constant
-    rate 10^U(-5,-3) (unless ``oscillatory_only``), or oscillatory (Eq. 16)
-    with an amplitude from ``amplitudes``, omega 6e-4 and phase {0, pi/2}."""
+    ``duration`` seconds (or the first ``count`` arrivals, whatever their
+    times, when ``count`` is given), each a geometry drawn from ``pool``
+    (Workload objects) with a shear protocol drawn from the sweep's ranges:
+    constant rate 10^U(-5,-3) (unless ``oscillatory_only``), or oscillatory
+    (Eq. 16) with an amplitude from ``amplitudes``, omega 6e-4 and phase
+    {0, pi/2}."""
     rng = np.random.default_rng(seed)
     out, t, rid = [], 0.0, 0
     while True:
         t += rng.exponential(1.0 / rate)
-        if t >= duration:
+        if count is None and t >= duration:
+            break
+        if count is not None and rid >= count:
             break
         w = pool[int(rng.integers(len(pool)))]
         if not oscillatory_only and rng.random() < 0.5:

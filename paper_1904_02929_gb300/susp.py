@@ -18,6 +18,13 @@ from . import build as _build
 
 SUSP_OK, SUSP_EINVAL, SUSP_ENOMEM, SUSP_ECUDA = 0, -1, -2, -3
 SUSP_EOVERLAP, SUSP_EUNSTABLE, SUSP_ETIMEOUT, SUSP_ESTATE = -4, -5, -6, -7
+STATUS_NAMES = {0: "SUSP_OK", -1: "SUSP_EINVAL", -2: "SUSP_ENOMEM", -3: "SUSP_ECUDA", -4: "SUSP_EOVERLAP",
+                -5: "SUSP_EUNSTABLE", -6: "SUSP_ETIMEOUT", -7: "SUSP_ESTATE"}
+
+
+def status_name(status: int) -> str:
+    """Name of a susp_status value (the number itself if unknown)."""
+    return STATUS_NAMES.get(int(status), str(status))
 SUSP_FP64, SUSP_FP32, SUSP_FP16_DEV, SUSP_BF16_DEV = 0, 1, 2, 3
 PRECISIONS = {"fp64": SUSP_FP64, "fp32": SUSP_FP32, "fp16": SUSP_FP16_DEV, "bf16": SUSP_BF16_DEV}
 VISCOUS, CONTACT, REPULSIVE, TOTAL, ANGULAR, LUBRICATION = range(6)
