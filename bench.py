@@ -92,7 +92,6 @@ def k1_traffic(workload_name: str):
 
 
 STAGE_KERNELS = {
-    "plane_moments": ("k_plane_moments_b", "hbm (two planes, tiny)"),
     "collide_stream": ("k_collide_stream", "hbm"),
     "particles": ("k_dem_step (all particle sub-steps, one cooperative launch)",
                   "latency: one warp per particle, a grid barrier per sub-step, ~0.5 MB of DRAM traffic"),
@@ -282,7 +281,7 @@ def batched_leg(ws, steps: int, warmup: int):
     stages, k1_n = S.susp_batch_profile_stages(batch.b)
     k1_ms = stages["collide_stream"]
     batch.profile(False)
-    launches_b = 2 + 5 + 1 + 3                       # planes, collide, cell list + particles, finalize, node map + links
+    launches_b = 1 + 5 + 1 + 3                       # collide, cell list + particles, finalize, node map + links
     mem_b = sum(g.nbytes for g in boxes)
     batch.close()
     for g in boxes:

@@ -208,12 +208,12 @@ susp_status susp_load(susp *h, const void *host_buf, size_t bytes);
  * starts a new window. */
 susp_status susp_profile(susp *h, int enable);
 susp_status susp_profile_read(susp *h, double *ms_total, int *launches);
-/* The same window split by stage: ms[6] receives the summed times of (0) the
- * Lees-Edwards plane moments, (1) the collide-stream, (2) the particle
- * sub-steps with their cell list, (3) the stress / protocol finalisation,
- * (4) the node-map update (uncover, cover) and (5) the boundary links; *steps
- * the number of profiled steps.  Synchronises and starts a new window (it
- * shares the window with susp_profile_read). */
+/* The same window split by stage: ms[5] receives the summed times of (0) the
+ * collide-stream (which also writes the next step's Lees-Edwards plane
+ * moments), (1) the particle sub-steps with their cell list, (2) the stress /
+ * protocol finalisation, (3) the node-map update (uncover, cover) and (4) the
+ * boundary links; *steps the number of profiled steps.  Synchronises and
+ * starts a new window (it shares the window with susp_profile_read). */
 susp_status susp_profile_stages(susp *h, double *ms, int *steps);
 
 /* Allocation-free fluid step.  The paper has no counterpart: this entry point

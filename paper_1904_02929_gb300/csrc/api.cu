@@ -51,7 +51,7 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int NSUMS = 47;
 
 struct Layout {
-  size_t fa, fb, owner, pm, vacc, views, tabs;
+  size_t fa, fb, owner, pm, pm2, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
   size_t cstart, ccnt, cids, pcell, pj, ph, pcnt, pconst, drv;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
@@ -108,6 +108,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.fb = take(19 * nc * esize(prec));
   L.owner = take(4 * nc);
   L.pm = take(2ULL * p->nx * p->nz * 4 * csize(prec));
+  L.pm2 = take(2ULL * p->nx * p->nz * 4 * csize(prec));
   L.vacc = take(ACC_REP * ACC_STRIDE * 8);
   L.views = take(sizeof(View));
   L.tabs = take(4 * 2 * sizeof(int));   // the one-box batch tables
@@ -277,7 +278,7 @@ struct GraphSlot {
   bool valid = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nodes[7] = {};   // event-record nodes at the stage boundaries (profiled graph)
+  cudaGraphNode_t nodes[6] = {};   // event-record nodes at the stage boundaries (profiled graph)
 };
 
 static const int PROF_MAX = 4096;
@@ -357,10 +358,11 @@ static void eng_drop_graphs(Engine& e) {
   }
 }
 
-// Stage boundaries recorded when a step is profiled: start, after the plane
-// moments, the collide-stream, the particle sub-steps (cell list included),
-// the finalisation, the node-map update, and the boundary links.
-static const int NEV = 7;
+// Stage boundaries recorded when a step is profiled: start, after the
+// collide-stream (which also writes the next step's Lees-Edwards plane
+// moments), the particle sub-steps (cell list included), the finalisation,
+// the node-map update, and the boundary links.
+static const int NEV = 6;
 
 // The launches of one lattice step; evs (optional, NEV events) mark the stage
 // boundaries.
@@ -368,18 +370,16 @@ static cudaError_t eng_enqueue(Engine& e, const cudaEvent_t* evs) {
   cudaStream_t s = e.stream;
   cudaError_t err = cudaSuccess;
   if (evs) cudaEventRecord(evs[0], s);
-  launch_plane_moments(e.prec, e.B, e.nplane, s);
-  if (evs) cudaEventRecord(evs[1], s);
   launch_collide_stream(e.prec, e.B, e.lb_grid, s);
-  if (evs) cudaEventRecord(evs[2], s);
+  if (evs) cudaEventRecord(evs[1], s);
   if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
-  if (evs) cudaEventRecord(evs[3], s);
+  if (evs) cudaEventRecord(evs[2], s);
   k_finalize<<<e.nbox, 64, 0, s>>>(e.B);
-  if (evs) cudaEventRecord(evs[4], s);
+  if (evs) cudaEventRecord(evs[3], s);
   launch_node_update(e.prec, e.B, e.nparts, s);
-  if (evs) cudaEventRecord(evs[5], s);
+  if (evs) cudaEventRecord(evs[4], s);
   launch_links(e.prec, e.B, e.nparts, s);
-  if (evs) cudaEventRecord(evs[6], s);
+  if (evs) cudaEventRecord(evs[5], s);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
 
@@ -471,7 +471,7 @@ static susp_status eng_profile(Engine& e, int enable) {
 static susp_status eng_profile_stages(Engine& e, double* ms, int* steps) {
   susp_status st = cuda_check(cudaStreamSynchronize(e.stream), "sync");
   if (st) return st;
-  double tot[NEV - 1] = {0, 0, 0, 0, 0, 0};
+  double tot[NEV - 1] = {0, 0, 0, 0, 0};
   for (int k = 0; k < e.prof_n; ++k)
     for (int j = 0; j + 1 < NEV; ++j) {
       float m = 0.0f;
@@ -491,7 +491,7 @@ static susp_status eng_profile_read(Engine& e, double* ms_total, int* launches) 
   double ms[NEV - 1];
   susp_status st = eng_profile_stages(e, ms, launches);
   if (st) return st;
-  if (ms_total) *ms_total = ms[1];
+  if (ms_total) *ms_total = ms[0];
   return SUSP_OK;
 }
 
@@ -681,6 +681,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.step_acc = (double*)(w + L.vacc);
   v.owner = (int*)(w + L.owner);
   v.plane_mom = w + L.pm;
+  v.plane_mom2 = w + L.pm2;
   v.n = n;
   v.R = (double*)(w + L.R); v.U = (double*)(w + L.U); v.W = (double*)(w + L.W);
   v.R2 = (double*)(w + L.R2); v.U2 = (double*)(w + L.U2); v.W2 = (double*)(w + L.W2);
@@ -805,6 +806,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   launch_write_plb(v, h->prec == 0, s);
   launch_claim(h->prec, e.B, n, s);
   refresh_links(h);
+  launch_plane_moments(h->prec, e.B, e.nplane, s);
   st = cuda_check(cudaGetLastError(), "launch");
   if (st) { eng_release(h->eng); delete h; return st; }
   st = device_status(h);
@@ -1056,6 +1058,7 @@ susp_status susp_set_populations(susp* h, const double* f) {
   st = cuda_check(cudaMemcpy(fin, raw.data(), raw.size(), cudaMemcpyHostToDevice), "write populations");
   if (st) return st;
   refresh_links(h);
+  launch_plane_moments(h->prec, h->eng.B, h->eng.nplane, stream_of(h));
   return device_status(h);
 }
 
@@ -1084,7 +1087,7 @@ susp_status susp_get_info(susp* h, susp_info* info) {
   int dem = 0;
   if (v.move && v.n > 0) dem = (v.brute ? 0 : 4) + 1;
   info->dem_substeps = v.nsub;
-  info->launches_per_step = 2 + dem + 1 + (v.n > 0 ? 3 : 0);
+  info->launches_per_step = 1 + dem + 1 + (v.n > 0 ? 3 : 0);   // collide, particles, finalize, node map + links
   info->brute_force_pairs = v.brute;
   info->ncell = v.ncell;
   info->workspace_bytes = h->L.total;

@@ -194,6 +194,16 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
       f[(long long)q * v.ncell + c] =
           S::enc(feq<TC>(q, rho0, jx, jy, jz, inv), (TC)D3Q19::w(q) * rho0, (TC)v.scale);
     v.owner[c] = -1;
+    {
+      // a node of a Lees-Edwards plane: the moments its crossing pulls read
+      const long long nxy = (long long)v.nx * v.ny;
+      const int y = (int)((c % nxy) / v.nx);
+      if (y == 0 || y == v.ny - 1) {
+        const long long x = c % v.nx, z = c / nxy;
+        TC* pm = reinterpret_cast<TC*>(pm_in_of(v)) + 4 * ((y == 0 ? 0 : (long long)v.nz * v.nx) + x + v.nx * z);
+        pm[0] = rho0; pm[1] = jx; pm[2] = jy; pm[3] = jz;
+      }
+    }
     acc[0] -= jx; acc[1] -= jy; acc[2] -= jz;
     acc[3] -= dy * jz - dz * jy; acc[4] -= dz * jx - dx * jz; acc[5] -= dx * jy - dy * jx;
   };

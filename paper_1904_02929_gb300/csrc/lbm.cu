@@ -83,7 +83,7 @@ __device__ __forceinline__ typename Store<P>::C le_pull(const View& v, const typ
     const TC self = S::load(fin, (long long)q * nc + idx, base_q, (TC)v.inv_scale);
     return self + wall_term<TC>(v, plb, on, x, y, z, q, delta, ule, rho0);
   }
-  const TC* pm = reinterpret_cast<const TC*>(v.plane_mom) + (below ? 4LL * v.nz * nx : 0);
+  const TC* pm = reinterpret_cast<const TC*>(pm_in_of(v)) + (below ? 4LL * v.nz * nx : 0);
   const long long k0 = 4LL * (c0x + (long long)nx * sz), k1 = 4LL * (c1x + (long long)nx * sz);
   TC val, rho, jx, jy, jz;
   if (v.owner[io] >= 0) {
@@ -149,7 +149,8 @@ struct PullAll<P, 19, BND> {
 
 template <int P>
 __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* __restrict__ fout, int idx,
-                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6]);
+                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6],
+                                           typename Store<P>::C* __restrict__ pmo);
 
 // One lattice node: pull (Eq. 3; bounce-back values sit in the solid
 // sources' slots) with the Lees-Edwards planes, BGK collision (Eq. 4, 5),
@@ -179,7 +180,11 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
   TC n[19];
   n[0] = S::load(fin, (uint32_t)idx, (TC)D3Q19::w(0) * rho0, (TC)v.inv_scale);
   PullAll<P, 1, BND>::run(v, fin, plb, pr, x, y, z, idx, dxm, dxp, dzm, dzp, rho0, n);
-  lb_collide<P>(v, fout, idx, n, acc);
+  // a node on a Lees-Edwards plane also writes the moments of its new
+  // populations, which the next step's crossing pulls read
+  TC* pmo = nullptr;
+  if (BND) pmo = reinterpret_cast<TC*>(pm_out_of(v)) + 4LL * ((y == 0 ? 0 : (long long)v.nz * nx) + x + (long long)nx * z);
+  lb_collide<P>(v, fout, idx, n, acc, pmo);
 }
 
 // Collision (Eq. 4, 5: BGK, or Ladd's linear operator when the box asks for
@@ -187,7 +192,8 @@ __device__ __forceinline__ void lb_node(const View& v, const typename Store<P>::
 // store, viscous-stress accumulation.
 template <int P>
 __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* __restrict__ fout, int idx,
-                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6]) {
+                                           typename Store<P>::C (&n)[19], typename Store<P>::C (&acc)[6],
+                                           typename Store<P>::C* __restrict__ pmo) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   const uint32_t nc = (uint32_t)v.ncell;
@@ -252,9 +258,12 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
     const TC sxx = ls * (nxx - t3) + lb * t3, syy = ls * (nyy - t3) + lb * t3, szz = ls * (nzz - t3) + lb * t3;
     const TC sxy = ls * nxy, sxz = ls * nxz, syz = ls * nyz;
     const TC st3 = (sxx + syy + szz) / (TC)3;
+    TC mr, mjx = 0, mjy = 0, mjz = 0;   // moments of the new populations
     {
       const TC w0 = (TC)D3Q19::w(0);
-      fout[idx] = S::enc(w0 * base - (TC)4.5 * w0 * st3, w0 * rho0, (TC)v.scale);
+      const TC o0 = w0 * base - (TC)4.5 * w0 * st3;
+      fout[idx] = S::enc(o0, w0 * rho0, (TC)v.scale);
+      mr = o0;
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -282,7 +291,12 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
       }
       fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc(oq, w * rho0, (TC)v.scale);
       fout[(uint32_t)(q + 1) * nc + (uint32_t)idx] = S::enc(oo, w * rho0, (TC)v.scale);
+      mr += oq + oo;
+      if (cxq) mjx += cxq > 0 ? oq - oo : oo - oq;
+      if (cyq) mjy += cyq > 0 ? oq - oo : oo - oq;
+      if (czq) mjz += czq > 0 ? oq - oo : oo - oq;
     }
+    if (pmo) { pmo[0] = mr; pmo[1] = mjx; pmo[2] = mjy; pmo[3] = mjz; }
     const TC vf = sel<TC>(v.vf_d, v.vf_f), vfb = sel<TC>(v.vfb_d, v.vfb_f);
     acc[0] += vf * (nxx - t3) + vfb * t3;
     acc[1] += vf * (nyy - t3) + vfb * t3;
@@ -292,10 +306,12 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
     acc[5] += vf * nyz;
     return;
   }
+  TC mr, mjx = 0, mjy = 0, mjz = 0;   // moments of the new populations
   {
     const TC fe = (TC)D3Q19::w(0) * base;
     const TC o = n[0] + omega * (fe - n[0]);
     fout[idx] = S::enc(o, (TC)D3Q19::w(0) * rho0, (TC)v.scale);
+    mr = o;
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -321,7 +337,12 @@ __device__ __forceinline__ void lb_collide(const View& v, typename Store<P>::T* 
     }
     fout[(uint32_t)q * nc + (uint32_t)idx] = S::enc(oq, w * rho0, (TC)v.scale);
     fout[(uint32_t)(q + 1) * nc + (uint32_t)idx] = S::enc(oo, w * rho0, (TC)v.scale);
+    mr += oq + oo;
+    if (cxq) mjx += cxq > 0 ? oq - oo : oo - oq;
+    if (cyq) mjy += cyq > 0 ? oq - oo : oo - oq;
+    if (czq) mjz += czq > 0 ? oq - oo : oo - oq;
   }
+  if (pmo) { pmo[0] = mr; pmo[1] = mjx; pmo[2] = mjy; pmo[3] = mjz; }
   const TC vf = sel<TC>(v.vf_d, v.vf_f);
   const TC third = rsec / (TC)3;
   acc[0] += vf * (pxx - jx * jx * inv - third);
@@ -733,7 +754,10 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
 }
 
 // Moments (rho, j) of the two Lees-Edwards boundary planes of every box, read
-// by the crossing pulls of the same step: plane 0 is y = 0, plane 1 is y = ny-1.
+// by the crossing pulls of the next step: plane 0 is y = 0, plane 1 is
+// y = ny-1.  The collide-stream writes them for the step after it (the
+// plane rows' new populations); this kernel sets them where the populations
+// come from elsewhere (creation, set, load).
 template <int P>
 __global__ void k_plane_moments_b(Batch B) {
   using TC = typename Store<P>::C;
@@ -758,7 +782,7 @@ __global__ void k_plane_moments_b(Batch B) {
     rho += f;
     jx += f * (TC)D3Q19::cx(q); jy += f * (TC)D3Q19::cy(q); jz += f * (TC)D3Q19::cz(q);
   }
-  TC* pm = reinterpret_cast<TC*>(v.plane_mom) + 4 * ((long long)plane * per + r);
+  TC* pm = reinterpret_cast<TC*>(pm_in_of(v)) + 4 * ((long long)plane * per + r);
   pm[0] = rho; pm[1] = jx; pm[2] = jy; pm[3] = jz;
 }
 

@@ -125,7 +125,8 @@ struct View {
                                 //  0-5 viscous (xx yy zz xy xz yz), 6-14 stresslet, 15-23 contact
                                 //  virial, 24 contacts, 25-33 repulsive, 34-39 lubrication stresslets
   int* owner;                   // -1 fluid, else particle
-  void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type
+  void* plane_mom;              // [2][nz][nx] (rho, jx, jy, jz) in compute type, of the populations
+  void* plane_mom2;             //  read at even (plane_mom) and odd (plane_mom2) step counts
   // particles
   int n;
   double *R, *U, *W, *rad, *amap, *mass, *inert, *inv_m, *inv_I;
@@ -212,6 +213,10 @@ template <> __device__ __forceinline__ float sel<float>(double, float f) { retur
 // Population buffer holding n*(t) for the box's current step counter.
 __device__ __forceinline__ void* fin_of(const View& v) { return (v.proto->t & 1) ? v.fb : v.fa; }
 __device__ __forceinline__ void* fout_of(const View& v) { return (v.proto->t & 1) ? v.fa : v.fb; }
+// Lees-Edwards plane moments of fin_of(v) (read by the crossing pulls) and of
+// fout_of(v) (written by the collide-stream for the next step).
+__device__ __forceinline__ void* pm_in_of(const View& v) { return (v.proto->t & 1) ? v.plane_mom2 : v.plane_mom; }
+__device__ __forceinline__ void* pm_out_of(const View& v) { return (v.proto->t & 1) ? v.plane_mom : v.plane_mom2; }
 
 __host__ __device__ inline int wrapi(int v, int L) { int r = v % L; return r < 0 ? r + L : r; }
 // Periodic wrap of an index at most one period outside [0, L).

@@ -260,18 +260,18 @@ def susp_load(h, buf) -> None:
     _check(library().susp_load(h, C.c_void_p(buf.ctypes.data), buf.size), "susp_load")
 
 
-STAGES = ("plane_moments", "collide_stream", "particles", "finalize", "node_map", "links")
+STAGES = ("collide_stream", "particles", "finalize", "node_map", "links")
 
 
 def susp_profile_stages(h):
-    ms = np.zeros(6)
+    ms = np.zeros(len(STAGES))
     n = C.c_int(0)
     _check(library().susp_profile_stages(h, ms.ctypes.data_as(_D), C.byref(n)), "susp_profile_stages")
     return dict(zip(STAGES, ms.tolist())), int(n.value)
 
 
 def susp_batch_profile_stages(b):
-    ms = np.zeros(6)
+    ms = np.zeros(len(STAGES))
     n = C.c_int(0)
     _check(library().susp_batch_profile_stages(b, ms.ctypes.data_as(_D), C.byref(n)),
            "susp_batch_profile_stages")

@@ -289,6 +289,7 @@ def test_drag_on_periodic_sphere_arrays_hasimoto():
         f = s.populations().reshape(19, -1)
         fluid = (s.owner() < 0).ravel()
         U = (np.asarray(C_LAT, dtype=float)[:, 0] @ f)[fluid].sum() / L ** 3
+        print(f"L={L}: drag / body force on the fluid - 1 = {F[0, 0] / (g * fluid.sum()) - 1:.2e}")
         assert F[0, 0] == pytest.approx(g * fluid.sum(), rel=3e-3)
         radii[L] = hasimoto_radius(L, eta, U, F[0, 0])
         s.close()
