@@ -17,6 +17,7 @@ import pytest
 import oracle as O
 from paper_1904_02929_gb300 import inputs as I
 from paper_1904_02929_gb300 import susp as S
+from parity_helpers import fp32_particle_pop_err
 
 pytestmark = pytest.mark.gpu
 
@@ -29,11 +30,9 @@ def test_deviation_storage_against_oracle(prec, pop_tol):
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision=prec, **kw)
     o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
     sh = dict(kind=0, rate=1e-3)
-    g.step(200, S.make_shear(**sh))
-    o.step(200, O.shear(**sh))
-    fo, fg = o.populations(), g.populations()
-    fl = (o.owner() < 0) & (g.owner() < 0)
-    err = np.abs(fg[:, fl] - fo[:, fl]).max() / np.abs(fo[:, fl]).max()
+    # FP32 arithmetic maps nodes from FP32 centres: disagreements of the node
+    # maps with the oracle are allowed on mapped surfaces and excluded
+    err = fp32_particle_pop_err(g, o, 200, w.radius, **sh)
     so, _ = o.stress(O.TOTAL)
     sg, _ = g.stress(S.TOTAL)
     serr = np.abs(sg - so).max() / np.abs(so).max()
