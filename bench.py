@@ -93,9 +93,9 @@ def k1_traffic(workload_name: str):
 
 STAGE_KERNELS = {
     "collide_stream": ("k_collide_stream", "hbm"),
-    "particles": ("k_dem_step (all particle sub-steps, one cooperative launch)",
+    "particles": ("k_dem_step (all particle sub-steps and the step's finalisation, one cooperative launch)",
                   "latency: one warp per particle, a grid barrier per sub-step, ~0.5 MB of DRAM traffic"),
-    "finalize": ("k_finalize", "latency"),
+    "finalize": ("k_finalize (only when no particle moves)", "latency"),
     "node_map": ("k_uncover + k_cover", "latency: bounding-box scans per particle"),
     "links": ("k_links", "latency: surface-shell gather per particle"),
 }
@@ -281,7 +281,7 @@ def batched_leg(ws, steps: int, warmup: int):
     stages, k1_n = S.susp_batch_profile_stages(batch.b)
     k1_ms = stages["collide_stream"]
     batch.profile(False)
-    launches_b = 1 + 5 + 1 + 3                       # collide, cell list + particles, finalize, node map + links
+    launches_b = 1 + 5 + 3                           # collide, cell list + particles (+ finalisation), node map + links
     mem_b = sum(g.nbytes for g in boxes)
     batch.close()
     for g in boxes:

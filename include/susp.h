@@ -211,8 +211,9 @@ susp_status susp_profile_read(susp *h, double *ms_total, int *launches);
 /* The same window split by stage: ms[5] receives the summed times of (0) the
  * collide-stream (which also writes the next step's Lees-Edwards plane
  * moments), (1) the particle sub-steps with their cell list, (2) the stress /
- * protocol finalisation, (3) the node-map update (uncover, cover) and (4) the
- * boundary links; *steps the number of profiled steps.  Synchronises and
+ * protocol finalisation (0 when particles move: the particle kernel then
+ * ends with it and its time is in (1)), (3) the node-map update (uncover,
+ * cover) and (4) the boundary links; *steps the number of profiled steps.  Synchronises and
  * starts a new window (it shares the window with susp_profile_read). */
 susp_status susp_profile_stages(susp *h, double *ms, int *steps);
 

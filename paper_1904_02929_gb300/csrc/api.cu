@@ -12,6 +12,7 @@
 
 #include "../../include/susp.h"
 #include "susp_dev.cuh"
+#include "finalize.cuh"
 
 using namespace susp_dev;
 
@@ -48,7 +49,6 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // contact and double-layer virials, lubrication stresslets, 3 x 3 each) and
 // the two phase-weighted shear-stress sums of Eq. 17, 18; followed by as
 // many compensation terms.
-constexpr int NSUMS = 47;
 
 struct Layout {
   size_t fa, fb, owner, pm, pm2, vacc, views, tabs;
@@ -148,27 +148,6 @@ void make_layout(const susp_params* p, Layout& L) {
 
 // ------------------------------------------------------------ device kernels
 
-__device__ void proto_derive(Proto& s, int nx) {
-  const double dm = s.delta - nx * floor(s.delta / nx);
-  s.di = (int)floor(dm);
-  s.w = dm - s.di;
-  s.near_lo = (s.w < 0.5) ? 0 : 1;
-  s.near_hi = ((1.0 - s.w) < 0.5) ? 0 : 1;
-  s.wf_lo = (float)s.w;
-  s.wf_hi = (float)(1.0 - s.w);
-  s.delta_f = (float)s.delta;
-  s.ule_f = (float)s.ule;
-}
-
-__device__ void kahan_le(double& delta, double& comp, double inc, int nx) {
-  const double y = inc - comp;
-  const double t = delta + y;
-  comp = (t - delta) - y;
-  delta = t;
-  if (delta >= nx) delta -= nx;
-  if (delta < 0.0) delta += nx;
-}
-
 // Set a new shear protocol at the current step (keeps t and Delta_t).
 __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gamma0, double omega,
                             double theta) {
@@ -182,87 +161,9 @@ __global__ void k_proto_set(Proto* pp, int nx, int kind, double rate, double gam
   *pp = s;
 }
 
-// End of step t, one block per box: the step's sums (accumulated by the
-// collide-stream, boundary-link and particle kernels) go into the compensated
-// time sums and are cleared; then the protocol advances to t+1.
-__global__ void __launch_bounds__(64) k_finalize(Batch B) {
-  const View& v = B.views[blockIdx.x];
-  __shared__ double tot[40];
-  // The kernel is a short chain of dependent memory round trips; every
-  // address and every operand that does not depend on the replica sums is
-  // loaded before the barrier so those trips overlap.
-  const int k = threadIdx.x;
-  double* const a = v.step_acc + k;
-  double* const S = v.sums;
-  Proto* const pp = v.proto;
-  const bool move = v.move != 0;
-  unsigned long long* const counters = v.counters;
-  const int nx = v.nx;
-  double s_k = 0.0, c_k = 0.0;
-  if (k < NSUMS) { s_k = S[k]; c_k = S[NSUMS + k]; }
-  Proto s;
-  double ule_nn = 0.0;   // shear increment of step t+2 -> t+3 (needs only the protocol constants)
-  if (k == 0) { s = *pp; ule_nn = proto_increment(s, s.t + 2); }
-  // phase of this step for Eq. 17, 18: the step t -> t+1 shears by
-  // gamma(t+1) - gamma(t), so its stress belongs to omega (t + 1/2) + Theta
-  // (read before thread 0 advances the protocol below)
-  double cs = 0.0;
-  if (k == 45 || k == 46) {
-    const int kind = pp->kind;
-    const double om = kind == 1 ? pp->omega : 0.0, th0 = kind == 1 ? pp->theta : 0.0;
-    const double phase = om * ((double)pp->t + 0.5) + th0;
-    cs = k == 45 ? cos(phase) : sin(phase);
-  }
-  // 0-5 viscous, 6-14 stresslet, 15-23 contact virial, 24 contact count,
-  // 25-33 repulsive virial, 34-39 lubrication stresslets (xx yy zz xy xz yz);
-  // the replicas added in a fixed order, then cleared
-  if (k < 40) {
-    double part[ACC_REP];
-#pragma unroll
-    for (int r = 0; r < ACC_REP; ++r) part[r] = a[r * ACC_STRIDE];   // loads issued together
-    double x = 0.0;
-#pragma unroll
-    for (int r = 0; r < ACC_REP; ++r) {
-      x += part[r];
-      a[r * ACC_STRIDE] = 0.0;
-    }
-    tot[k] = x;
-  }
-  __syncthreads();
-  if (k < NSUMS) {
-    // compensated time sums, one entry per thread; the viscous and
-    // lubrication partials are xx yy zz xy xz yz, expanded to the full
-    // 3 x 3; entries 45 and 46: the step's total shear stress sigma_xy
-    // (times V; stresslet symmetrised, virials with a minus) weighted by cos
-    // and sin of the phase
-    const int vmap[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};
-    double x;
-    if (k < 9) x = tot[vmap[k]];
-    else if (k < 18) x = tot[6 + (k - 9)];
-    else if (k < 27) x = move ? tot[15 + (k - 18)] : 0.0;
-    else if (k < 36) x = move ? tot[25 + (k - 27)] : 0.0;
-    else if (k < 45) x = move ? tot[34 + vmap[k - 36]] : 0.0;
-    else {
-      const double sxy = tot[3] + 0.5 * (tot[7] + tot[9]) - (move ? tot[16] + tot[26] - tot[37] : 0.0);
-      x = sxy * cs;
-    }
-    const double y = x - c_k;
-    const double t = s_k + y;
-    S[NSUMS + k] = (t - s_k) - y;
-    S[k] = t;
-  }
-  if (k != 0) return;
-  counters[0] += 1ULL;
-  if (move) counters[1] += (unsigned long long)(tot[24] + 0.5);
-  // protocol: t -> t+1
-  s.t += 1;
-  s.delta = s.delta_n; s.delta_c = s.delta_nc; s.ule = s.ule_n;
-  s.delta_n = s.delta; s.delta_nc = s.delta_c;
-  kahan_le(s.delta_n, s.delta_nc, s.ule, nx);
-  s.ule_n = ule_nn;
-  proto_derive(s, nx);
-  *pp = s;
-}
+// End of step t, one block per box (boxes whose particles do not move;
+// the particle kernel does the same after its last sub-step otherwise).
+__global__ void __launch_bounds__(64) k_finalize(Batch B) { finalize_box(B.views[blockIdx.x]); }
 
 // Error words of the boxes of a batch, in batch order.
 __global__ void k_gather_err(Batch B, int* out) {
@@ -372,9 +273,11 @@ static cudaError_t eng_enqueue(Engine& e, const cudaEvent_t* evs) {
   if (evs) cudaEventRecord(evs[0], s);
   launch_collide_stream(e.prec, e.B, e.lb_grid, s);
   if (evs) cudaEventRecord(evs[1], s);
-  if (e.any_move) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
+  // the particle kernel ends with the finalisation when it runs
+  const bool dem = e.any_move && e.nparts > 0;
+  if (dem) err = launch_dem_step(e.B, e.nparts, e.ncells, e.prec == 0, e.dem_grid, s);
   if (evs) cudaEventRecord(evs[2], s);
-  k_finalize<<<e.nbox, 64, 0, s>>>(e.B);
+  if (!dem) k_finalize<<<e.nbox, 64, 0, s>>>(e.B);
   if (evs) cudaEventRecord(evs[3], s);
   launch_node_update(e.prec, e.B, e.nparts, s);
   if (evs) cudaEventRecord(evs[4], s);
@@ -1087,7 +990,9 @@ susp_status susp_get_info(susp* h, susp_info* info) {
   int dem = 0;
   if (v.move && v.n > 0) dem = (v.brute ? 0 : 4) + 1;
   info->dem_substeps = v.nsub;
-  info->launches_per_step = 1 + dem + 1 + (v.n > 0 ? 3 : 0);   // collide, particles, finalize, node map + links
+  // collide-stream, particles (which end with the finalisation) or a
+  // separate finalisation, node map + links
+  info->launches_per_step = 1 + (dem ? dem : 1) + (v.n > 0 ? 3 : 0);
   info->brute_force_pairs = v.brute;
   info->ncell = v.ncell;
   info->workspace_bytes = h->L.total;

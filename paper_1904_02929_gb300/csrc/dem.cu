@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 
 #include "susp_dev.cuh"
+#include "finalize.cuh"
 
 namespace susp_dev {
 
@@ -735,6 +736,18 @@ __device__ inline void write_plb(const View& v, int i) {
 #define DEM_WARPS 4
 #endif
 
+// End of the lattice step for every box of the batch, once every sub-step's
+// forces and virials are in: one block per box (a block takes several boxes
+// when the grid is smaller than the batch).  Saves the separate finalisation
+// launch whenever particles move.
+__device__ __forceinline__ void finalize_boxes(const Batch& B, cooperative_groups::grid_group& grid) {
+  grid.sync();
+  for (int b = blockIdx.x; b < B.nbox; b += gridDim.x) {
+    finalize_box(B.views[b]);
+    __syncthreads();   // the block's shared totals are reused by its next box
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
   namespace cg = cooperative_groups;
@@ -825,6 +838,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       }
       if (sub + 1 < B.max_nsub) grid.sync();
     }
+    finalize_boxes(B, grid);
     return;
   }
   // Many particles per warp: two at a time, one per half-warp (16 lanes and
@@ -853,6 +867,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }
+  finalize_boxes(B, grid);
 }
 
 __global__ void k_write_plb(View v, int plb_double) {

@@ -30,14 +30,13 @@ def test_deviation_storage_against_oracle(prec, pop_tol):
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision=prec, **kw)
     o = O.Oracle(w.nx, w.ny, w.nz, w.radius, w.pos, **kw)
     sh = dict(kind=0, rate=1e-3)
-    # FP32 arithmetic maps nodes from FP32 centres: disagreements of the node
-    # maps with the oracle are allowed on mapped surfaces and excluded
-    err = fp32_particle_pop_err(g, o, 200, w.radius, **sh)
+    # FP32 arithmetic moves the centres off the oracle's in the last bits:
+    # node-map disagreements are allowed on mapped surfaces (checked inside)
+    err = fp32_particle_pop_err(g, o, 200, w.radius, pop_tol, **sh)
     so, _ = o.stress(O.TOTAL)
     sg, _ = g.stress(S.TOTAL)
     serr = np.abs(sg - so).max() / np.abs(so).max()
     print(f"{prec}: population error {err:.2e}, total-stress error {serr:.2e}")
-    assert err < pop_tol
     assert serr < stress_tol
     assert abs(sg[0, 1] - so[0, 1]) <= stress_tol * abs(so[0, 1])
     assert serr < 1e-4
