@@ -70,9 +70,10 @@ def peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def k1_traffic(workload_name: str):
+def k1_traffic(workload_name: str, kernel: str):
     """DRAM bytes per collide-stream launch from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only for the kernel captured and while its source is unchanged
+    since the capture."""
     path = os.path.join(ROOT, "profiles", "k_collide_stream_dst96_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -85,14 +86,21 @@ def k1_traffic(workload_name: str):
             fields[k.strip()] = v.strip()
     if fields.get("lbm_cu_sha256_16") != h or fields.get("workload") != workload_name:
         return None
+    if fields.get("kernel", "k_collide_stream<fp32>") != kernel:
+        return None
     try:
         return float(fields["dram_bytes_per_launch"])
     except Exception:
         return None
 
 
+def lb_kernel(shape: dict, storage: str) -> str:
+    """Name of the collide-stream kernel a launch shape runs."""
+    return ("k_collide_stream_tma" if shape.get("staged") else "k_collide_stream") + f"<{storage}>"
+
+
 STAGE_KERNELS = {
-    "collide_stream": ("k_collide_stream", "hbm"),
+    "collide_stream": ("k_collide_stream or k_collide_stream_tma (the tuner's choice)", "hbm"),
     "particles": ("k_dem_step (all particle sub-steps and the step's finalisation, one cooperative launch)",
                   "latency: one warp per particle, a grid barrier per sub-step, ~0.5 MB of DRAM traffic"),
     "finalize": ("k_finalize (only when no particle moves)", "latency"),
@@ -332,7 +340,7 @@ def batched_leg(ws, steps: int, warmup: int):
         "value": mb, "unit": "MLUPS", "ms_per_step": ms_b / steps,
         "particle_steps_per_s": parts * steps / (ms_b / 1e3),
         "k_collide_stream_avg_ms": k1,
-        "roofline": {"bound": "hbm", "kernel": "k_collide_stream<bf16>", "achieved": alg / (k1 / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": lb_kernel(tuned, "bf16"), "achieved": alg / (k1 / 1e3) / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
                      "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
         "launch_shape": tuned,
@@ -514,7 +522,7 @@ def monolayer_leg(steps: int, warmup: int):
             "ms_per_step": ms / steps, "particle_steps_per_s": w.n * steps / (ms / 1e3),
             "dem_substeps": info.dem_substeps,
             "stage_us": {k: round(1e3 * v / n, 1) for k, v in stages.items()},
-            "roofline": {"bound": "hbm", "kernel": "k_collide_stream<fp16>", "achieved": alg / (k1 / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": lb_kernel(tuned, "fp16"), "achieved": alg / (k1 / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
                          "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
             "launch_shape": tuned,
@@ -561,7 +569,7 @@ def variant_leg(w, what: str, steps: int, warmup: int, **over):
             "ms_per_step": ms / steps, "particle_steps_per_s": w.n * steps / (ms / 1e3),
             "dem_substeps": info.dem_substeps,
             "stage_us": {k: round(1e3 * v / n, 1) for k, v in stages.items()},
-            "roofline": {"bound": "hbm", "kernel": "k_collide_stream<fp32>", "achieved": alg / (k1 / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": lb_kernel(tuned, "fp32"), "achieved": alg / (k1 / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
                          "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
             "launch_shape": tuned, "l2": "flushed between timed steps (256 MB write)"}
@@ -757,7 +765,7 @@ def main():
         alg_bytes = 2 * 19 * 4 * w.ncell                 # FP32 populations of every lattice cell
         k1_avg_s = (k1_ms / max(k1_n, 1)) / 1e3
         achieved = alg_bytes / k1_avg_s / 1e9
-        traffic = k1_traffic(w.name)
+        traffic = k1_traffic(w.name, lb_kernel(tuned, "fp32"))
         line = {
             "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
@@ -777,7 +785,7 @@ def main():
             "dominant_kernel": dominant_stage(stages),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_collide_stream<fp32>", "peak_source": peak_kind,
+                         "kernel": lb_kernel(tuned, "fp32"), "peak_source": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": k1_ms / max(k1_n, 1)},
             "e2e": {"value": world * w.ncell * K / e2e_s / 1e6, "unit": "MLUPS",

@@ -253,7 +253,10 @@ susp_status susp_set_graphs(susp *h, int enable);
 /* Launch-shape tuner (no counterpart in the paper; the batched step takes
  * its tile shapes from it).  Times the collide-stream on this machine for each
  * tile height of 4, 8 and 16 rows of 32 nodes and each count of resident
- * blocks per SM that the occupancy allows (three launches per shape after a
+ * blocks per SM that the occupancy allows, and for FP32 / FP16 / BF16
+ * storage also the staged kernel (tiles of 128 x 4 nodes whose source rows
+ * tensor copies bring into shared memory; see susp_set_launch_shape) at each
+ * resident block count (three launches per shape after a
  * warm-up, CUDA events on the handle's stream), keeps the fastest, and
  * reports it: *tile_rows, *blocks_per_sm, and *us, the average launch time
  * of that shape in microseconds (any of the three may be NULL).  Call it
@@ -266,6 +269,21 @@ susp_status susp_set_graphs(susp *h, int enable);
  * box attached to a batch returns SUSP_ESTATE (tune the batch).  Errors:
  * SUSP_EINVAL, SUSP_ESTATE, SUSP_ECUDA. */
 susp_status susp_tune(susp *h, int *tile_rows, int *blocks_per_sm, double *us);
+
+/* The collide-stream launch shape in use, or set explicitly (no counterpart
+ * in the paper).  tile_rows: 4, 8 or 16 rows of 32 nodes per tile;
+ * blocks_per_sm: resident blocks per SM of the persistent grid (capped by
+ * the occupancy); staged: 1 for the kernel whose per-tile source rows of the
+ * 19 populations are brought into shared memory by tensor copies (FP32,
+ * FP16 and BF16 storage; tiles of 128 x 4 nodes, given as tile_rows = 4; a
+ * box whose x rows are not a multiple of 16 bytes pulls from global memory
+ * in that kernel), 0 for direct pulls.  Both kernels give the same populations bit for bit; the
+ * viscous-stress sums differ in summation order only.  Set synchronises and
+ * drops the captured graph; a box attached to a batch returns SUSP_ESTATE
+ * (set the batch's).  Get reports the shape of the batch a box is attached
+ * to.  Errors: SUSP_EINVAL (bad value, NULL handle), SUSP_ESTATE, SUSP_ECUDA. */
+susp_status susp_set_launch_shape(susp *h, int tile_rows, int blocks_per_sm, int staged);
+susp_status susp_get_launch_shape(susp *h, int *tile_rows, int *blocks_per_sm, int *staged);
 
 /* Release the handle (not the caller's workspace). */
 void susp_destroy(susp *h);
@@ -305,6 +323,9 @@ susp_status susp_batch_step(susp_batch *b, int nsteps);
  * persistent collide-stream grid); the choice holds across attach and
  * detach.  SUSP_ESTATE when no box is attached. */
 susp_status susp_batch_tune(susp_batch *b, int *tile_rows, int *blocks_per_sm, double *us);
+/* As susp_set_launch_shape / susp_get_launch_shape, for the batch. */
+susp_status susp_batch_set_launch_shape(susp_batch *b, int tile_rows, int blocks_per_sm, int staged);
+susp_status susp_batch_get_launch_shape(susp_batch *b, int *tile_rows, int *blocks_per_sm, int *staged);
 /* As susp_profile / susp_profile_read, for the batch's collide-stream launch. */
 susp_status susp_batch_profile(susp_batch *b, int enable);
 susp_status susp_batch_profile_read(susp_batch *b, double *ms_total, int *launches);

@@ -18,9 +18,10 @@ using namespace susp_dev;
 
 // launchers defined in the other translation units
 void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s);
-void launch_collide_stream(int prec, const Batch& B, int grid, cudaStream_t s);
-int lb_blocks(int nx, int ny, int nz, int tile_lg);
-void lb_occupancy(int prec, int* per_sm, int* sms);
+void launch_collide_stream(int prec, const Batch& B, int grid, int staged, cudaStream_t s);
+int lb_tensor_maps(int prec, int nx, int ny, int nz, void* fa, void* fb, void* owner, void* out);
+int lb_blocks(int nx, int ny, int nz, int tile_lg, int staged);
+void lb_occupancy(int prec, int staged, int* per_sm, int* sms);
 void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s);
 void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s);
 void launch_links(int prec, const Batch& B, int nparts, cudaStream_t s);
@@ -53,9 +54,10 @@ size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
   size_t fa, fb, owner, pm, pm2, vacc, views, tabs;
   size_t R, U, W, R2, U2, W2, pcx, rad, amap, mass, inert, imass, iinert, plb, Fh, Th, Fcov, Tcov, Fp, Tp;
+  size_t Ro, m32a, m32b, pd, pk;
   size_t cstart, ccnt, cids, pcell, pj, ph, pcnt, pconst, drv;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
-  size_t sums, hist, counters, proto, err;
+  size_t sums, hist, counters, proto, err, tmap;
   size_t total;
   int ncx, ncy, ncz, brute, ncells;
   double csx, csy, csz, hrange;
@@ -114,6 +116,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.tabs = take(4 * 2 * sizeof(int));   // the one-box batch tables
   L.R = take(24 * nn); L.U = take(24 * nn); L.W = take(24 * nn);
   L.R2 = take(24 * nn); L.U2 = take(24 * nn); L.W2 = take(24 * nn); L.pcx = take(4 * 8 * (size_t)nn);
+  L.Ro = take(24 * nn); L.m32a = take(48 * nn); L.m32b = take(48 * nn);
   L.rad = take(8 * nn); L.amap = take(8 * nn); L.mass = take(8 * nn); L.inert = take(8 * nn);
   L.imass = take(8 * nn); L.iinert = take(8 * nn);
   L.plb = take(12 * csize(prec) * nn);
@@ -133,6 +136,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.ncells = ncx * ncy * ncz;
   L.csx = (double)p->nx / ncx; L.csy = (double)p->ny / ncy; L.csz = (double)p->nz / ncz;
   L.pj = take(4 * (size_t)nn * PAIR_SLOTS); L.ph = take(24 * (size_t)nn * PAIR_SLOTS); L.pcnt = take(4 * nn); L.pconst = take(64 * (size_t)nn); L.drv = take(4 * (size_t)nn);
+  L.pd = take(16 * (size_t)nn * PAIR_SLOTS); L.pk = take((size_t)nn * PAIR_SLOTS);
   L.cstart = take(4 * (L.ncells + 1)); L.ccnt = take(4 * L.ncells);
   L.cids = take(4 * nn); L.pcell = take(4 * nn);
   L.hc0 = take(4 * nn); L.hp0 = take(4 * (size_t)nn * HSLOTS); L.hv0 = take(24 * (size_t)nn * HSLOTS);
@@ -143,6 +147,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.counters = take(8 * 4);
   L.proto = take(sizeof(Proto));
   L.err = take(4);
+  L.tmap = take(384);   // three 128-byte tensor maps (256-byte aligned, as they must be 64)
   L.total = o;
 }
 
@@ -196,6 +201,7 @@ struct Engine {
   int lb_grid = 1, dem_grid = 1;
   int tile_lg = 3;           // collide-stream tile height 2^tile_lg (the tuner's choice)
   int bps = 0;               // its resident blocks per SM (0: as many as fit)
+  int staged = 0;            // source rows staged by tensor copies (128 x 4 tiles, tile_lg 2)
   cudaStream_t stream = nullptr;
   bool use_graphs = true;
   GraphSlot graphs[2];       // [timed]
@@ -223,7 +229,7 @@ static void eng_tables(Engine& e, const std::vector<const View*>& vs, std::vecto
   int msub = 1;
   for (int b = 0; b < nb; ++b) {
     const View& v = *vs[b];
-    tile[b + 1] = tile[b] + lb_blocks(v.nx, v.ny, v.nz, e.tile_lg);
+    tile[b + 1] = tile[b] + lb_blocks(v.nx, v.ny, v.nz, e.tile_lg, e.staged && e.prec >= 1);
     part[b + 1] = part[b] + v.n;
     plane[b + 1] = plane[b] + 2 * v.nx * v.nz;
     cell[b + 1] = cell[b] + (v.brute ? 0 : v.ncells);
@@ -235,7 +241,7 @@ static void eng_tables(Engine& e, const std::vector<const View*>& vs, std::vecto
   e.B.max_nsub = msub;
   e.B.tile_lg = e.tile_lg;
   int per = 1, sms = 1;
-  lb_occupancy(e.prec, &per, &sms);
+  lb_occupancy(e.prec, e.staged, &per, &sms);
   const int bps = (e.bps >= 1 && e.bps <= per) ? e.bps : per;
   e.lb_grid = std::max(1, std::min(sms * bps, e.ntiles));
   e.dem_grid = dem_grid_blocks(e.prec == 0, e.nparts);
@@ -271,7 +277,7 @@ static cudaError_t eng_enqueue(Engine& e, const cudaEvent_t* evs) {
   cudaStream_t s = e.stream;
   cudaError_t err = cudaSuccess;
   if (evs) cudaEventRecord(evs[0], s);
-  launch_collide_stream(e.prec, e.B, e.lb_grid, s);
+  launch_collide_stream(e.prec, e.B, e.lb_grid, e.staged, s);
   if (evs) cudaEventRecord(evs[1], s);
   // the particle kernel ends with the finalisation when it runs
   const bool dem = e.any_move && e.nparts > 0;
@@ -427,45 +433,86 @@ static susp_status eng_tune(Engine& e, const std::vector<const View*>& vs, char*
   susp_status st = cuda_check(cudaStreamSynchronize(s), "sync");
   if (st) return st;
   eng_drop_graphs(e);
-  int per = 1, sms = 1;
-  lb_occupancy(e.prec, &per, &sms);
+  // candidate shapes: the direct kernel at tile heights 4, 8, 16 and the
+  // staged one (128 x 4 tiles; FP32 / FP16 / BF16 boxes with tensor maps),
+  // each at every resident block count the occupancy allows
+  bool any_map = false;
+  for (const View* v : vs) any_map = any_map || v->tmap != nullptr;
   cudaEvent_t ea = nullptr, eb = nullptr;
   st = cuda_check(cudaEventCreate(&ea), "cudaEventCreate");
   if (!st) st = cuda_check(cudaEventCreate(&eb), "cudaEventCreate");
   const int reps = 3;
   double best = 1e300;
-  int best_lg = e.tile_lg, best_bps = e.bps;
+  int best_lg = e.tile_lg, best_bps = e.bps, best_staged = e.staged;
   std::vector<int> tabs;
-  for (int lg = 2; lg <= 4 && !st; ++lg)
-    for (int bps = 1; bps <= per && !st; ++bps) {
-      e.tile_lg = lg;
-      e.bps = bps;
-      eng_tables(e, vs, tabs);
-      cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
-      launch_plane_moments(e.prec, e.B, e.nplane, s);
-      launch_collide_stream(e.prec, e.B, e.lb_grid, s);   // warm-up
-      cudaEventRecord(ea, s);
-      for (int r = 0; r < reps; ++r) launch_collide_stream(e.prec, e.B, e.lb_grid, s);
-      cudaEventRecord(eb, s);
-      st = cuda_check(cudaEventSynchronize(eb), "tuning launch");
-      float ms = 0.0f;
-      if (!st) st = cuda_check(cudaEventElapsedTime(&ms, ea, eb), "cudaEventElapsedTime");
-      if (!st && ms / reps < best) { best = ms / reps; best_lg = lg; best_bps = bps; }
-    }
+  for (int staged = 0; staged <= ((e.prec >= 1 && any_map) ? 1 : 0) && !st; ++staged) {
+    int per = 1, sms = 1;
+    lb_occupancy(e.prec, staged, &per, &sms);
+    for (int lg = 2; lg <= (staged ? 2 : 4) && !st; ++lg)
+      for (int bps = 1; bps <= per && !st; ++bps) {
+        e.tile_lg = lg;
+        e.bps = bps;
+        e.staged = staged;
+        eng_tables(e, vs, tabs);
+        cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
+        launch_plane_moments(e.prec, e.B, e.nplane, s);
+        launch_collide_stream(e.prec, e.B, e.lb_grid, e.staged, s);   // warm-up
+        cudaEventRecord(ea, s);
+        for (int r = 0; r < reps; ++r) launch_collide_stream(e.prec, e.B, e.lb_grid, e.staged, s);
+        cudaEventRecord(eb, s);
+        st = cuda_check(cudaEventSynchronize(eb), "tuning launch");
+        float ms = 0.0f;
+        if (!st) st = cuda_check(cudaEventElapsedTime(&ms, ea, eb), "cudaEventElapsedTime");
+        if (!st && ms / reps < best) { best = ms / reps; best_lg = lg; best_bps = bps; best_staged = staged; }
+      }
+  }
   if (ea) cudaEventDestroy(ea);
   if (eb) cudaEventDestroy(eb);
   e.tile_lg = best_lg;
   e.bps = best_bps;
+  e.staged = best_staged;
   eng_tables(e, vs, tabs);
   cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
   k_zero_visc<<<(e.nbox + 127) / 128, 128, 0, s>>>(e.B);
   susp_status st2 = cuda_check(cudaStreamSynchronize(s), "tuner");
   if (st) return st;
   if (st2) return st2;
+  int per = 1, sms = 1;
+  lb_occupancy(e.prec, e.staged, &per, &sms);
   if (tile_rows) *tile_rows = 1 << e.tile_lg;
   if (blocks_per_sm) *blocks_per_sm = std::max(1, std::min(e.bps, per));
   if (us) *us = 1e3 * best;
   return SUSP_OK;
+}
+
+// Set the collide-stream launch shape explicitly (the tuner's alternative).
+static susp_status eng_set_shape(Engine& e, const std::vector<const View*>& vs, char* tabs_dev, int tile_rows,
+                                 int blocks_per_sm, int staged) {
+  int lg = tile_rows == 4 ? 2 : tile_rows == 8 ? 3 : tile_rows == 16 ? 4 : -1;
+  if (lg < 0) return fail(SUSP_EINVAL, "tile_rows must be 4, 8 or 16");
+  if (staged != 0 && staged != 1) return fail(SUSP_EINVAL, "staged must be 0 or 1");
+  if (staged && (e.prec < 1 || lg != 2))
+    return fail(SUSP_EINVAL, "the staged collide-stream needs FP32 / FP16 / BF16 storage and tile_rows = 4");
+  if (blocks_per_sm < 1) return fail(SUSP_EINVAL, "blocks_per_sm must be >= 1");
+  cudaStream_t s = e.stream;
+  susp_status st = cuda_check(cudaStreamSynchronize(s), "sync");
+  if (st) return st;
+  eng_drop_graphs(e);
+  e.tile_lg = lg;
+  e.bps = blocks_per_sm;
+  e.staged = staged;
+  std::vector<int> tabs;
+  eng_tables(e, vs, tabs);
+  cudaMemcpyAsync(tabs_dev, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
+  return cuda_check(cudaStreamSynchronize(s), "set launch shape");
+}
+
+static void eng_get_shape(const Engine& e, int* tile_rows, int* blocks_per_sm, int* staged) {
+  int per = 1, sms = 1;
+  lb_occupancy(e.prec, e.staged, &per, &sms);
+  if (tile_rows) *tile_rows = 1 << e.tile_lg;
+  if (blocks_per_sm) *blocks_per_sm = (e.bps >= 1 && e.bps <= per) ? e.bps : per;
+  if (staged) *staged = e.staged;
 }
 
 // ------------------------------------------------------------ handles
@@ -500,6 +547,7 @@ static susp_status err_status(int err) {
   if (err & ERR_UNSTABLE) return fail(SUSP_EUNSTABLE, "non-positive density or particle speed >= 0.5");
   if (err & ERR_LINKS) return fail(SUSP_ENOMEM, "particle surface larger than the link kernel stages");
   if (err & ERR_PAIRS) return fail(SUSP_ENOMEM, "tangential-spring table full");
+  if (err & ERR_TIMEOUT) return fail(SUSP_ETIMEOUT, "a bounded device wait gave up");
   return SUSP_OK;
 }
 
@@ -588,6 +636,8 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.n = n;
   v.R = (double*)(w + L.R); v.U = (double*)(w + L.U); v.W = (double*)(w + L.W);
   v.R2 = (double*)(w + L.R2); v.U2 = (double*)(w + L.U2); v.W2 = (double*)(w + L.W2);
+  v.Ro = (double*)(w + L.Ro); v.m32[0] = (float*)(w + L.m32a); v.m32[1] = (float*)(w + L.m32b);
+  v.pd = (float4*)(w + L.pd); v.pk = (signed char*)(w + L.pk);
   v.pcx = (int*)(w + L.pcx);
   v.rad = (double*)(w + L.rad); v.amap = (double*)(w + L.amap);
   v.mass = (double*)(w + L.mass); v.inert = (double*)(w + L.inert);
@@ -650,6 +700,9 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   v.sums = (double*)(w + L.sums); v.hist = (double*)(w + L.hist);
   v.counters = (unsigned long long*)(w + L.counters);
   v.proto = (Proto*)(w + L.proto); v.err = (int*)(w + L.err);
+  std::vector<unsigned char> maps(384, 0);
+  v.tmap = lb_tensor_maps(h->prec, v.nx, v.ny, v.nz, v.fa, v.fb, v.owner, maps.data()) ? (const void*)(w + L.tmap)
+                                                                                    : nullptr;
 
   Engine& e = h->eng;
   e.prec = h->prec;
@@ -664,6 +717,7 @@ susp_status susp_create(const susp_params* p, void* dev_workspace, size_t bytes,
   st = cuda_check(cudaMemsetAsync(w + L.owner, 0, L.total - L.owner, s), "memset workspace");
   if (st) { eng_release(h->eng); delete h; return st; }
   cudaMemsetAsync(v.owner, 0xff, 4 * v.ncell, s);
+  if (v.tmap) cudaMemcpyAsync(w + L.tmap, maps.data(), 384, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + L.views, &v, sizeof(View), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + L.tabs, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s);
   std::vector<double> zeros(3 * n, 0.0), im(n), iI(n);
@@ -1099,6 +1153,19 @@ susp_status susp_tune(susp* h, int* tile_rows, int* blocks_per_sm, double* us) {
   return eng_tune(h->eng, std::vector<const View*>{&h->v}, h->ws + h->L.tabs, tile_rows, blocks_per_sm, us);
 }
 
+susp_status susp_set_launch_shape(susp* h, int tile_rows, int blocks_per_sm, int staged) {
+  if (!h) return fail(SUSP_EINVAL, "NULL handle");
+  if (h->batch) return fail(SUSP_ESTATE, "box is attached to a batch: set the batch's shape");
+  return eng_set_shape(h->eng, std::vector<const View*>{&h->v}, h->ws + h->L.tabs, tile_rows, blocks_per_sm,
+                       staged);
+}
+
+susp_status susp_get_launch_shape(susp* h, int* tile_rows, int* blocks_per_sm, int* staged) {
+  if (!h) return fail(SUSP_EINVAL, "NULL handle");
+  eng_get_shape(h->batch ? h->batch->eng : h->eng, tile_rows, blocks_per_sm, staged);
+  return SUSP_OK;
+}
+
 void susp_destroy(susp* h) {
   if (!h) return;
   if (h->batch) susp_batch_detach(h->batch, h);
@@ -1194,6 +1261,20 @@ susp_status susp_batch_tune(susp_batch* b, int* tile_rows, int* blocks_per_sm, d
   std::vector<const View*> vs;
   for (susp* h : b->boxes) vs.push_back(&h->v);
   return eng_tune(b->eng, vs, b->ws + al(sizeof(View) * (size_t)b->max_boxes), tile_rows, blocks_per_sm, us);
+}
+
+susp_status susp_batch_set_launch_shape(susp_batch* b, int tile_rows, int blocks_per_sm, int staged) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  std::vector<const View*> vs;
+  for (susp* h : b->boxes) vs.push_back(&h->v);
+  return eng_set_shape(b->eng, vs, b->ws + al(sizeof(View) * (size_t)b->max_boxes), tile_rows, blocks_per_sm,
+                       staged);
+}
+
+susp_status susp_batch_get_launch_shape(susp_batch* b, int* tile_rows, int* blocks_per_sm, int* staged) {
+  if (!b) return fail(SUSP_EINVAL, "NULL handle");
+  eng_get_shape(b->eng, tile_rows, blocks_per_sm, staged);
+  return SUSP_OK;
 }
 
 susp_status susp_batch_profile(susp_batch* b, int enable) {

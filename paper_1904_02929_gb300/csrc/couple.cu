@@ -71,6 +71,21 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
   return total;
 }
 
+// Whether node (xu, y, zu) (unwrapped coordinates of image k's box) lies
+// inside particle i's mapped sphere, decided from the FP64 centre and offset
+// as the oracle decides it.  Out of line: it runs only for the rare nodes
+// whose FP32 distance lies within rounding of the surface.
+__device__ __noinline__ bool inside_fp64(const View& v, int i, int k, int xu, int y, int zu) {
+  const double cx = v.R[3 * i] + (double)k * v.proto->delta;
+  const double cy = v.R[3 * i + 1] + (double)k * (double)v.ny, cz = v.R[3 * i + 2];
+  double ex = (double)xu - cx, ey = (double)y - cy, ez = (double)zu - cz;
+  // the FP32 box may have wrapped the centre by one period where FP64 does
+  // not (a centre within rounding of x = 0 or L_x): take the nearest image
+  ex -= (double)v.nx * floor(ex * v.inv_nx_d + 0.5);
+  ez -= (double)v.nz * floor(ez * v.inv_nz_d + 0.5);
+  return ex * ex + (ey * ey + ez * ez) < v.amap[i] * v.amap[i];
+}
+
 // Visit the cells of a particle's image boxes: half-warps take (y, z) rows and
 // their 16 lanes run along x (coalesced).  Box corners lie less than one period
 // outside the lattice (reach < L / 2, centres in [0, L)), so one wrap suffices.
@@ -79,13 +94,21 @@ __device__ inline int particle_boxes(const View& v, TC Rx, TC Ry, TC Rz, TC delt
 // that image's centre (reach < L / 2, the boxes of different images do not
 // overlap), so that image is the node's minimum image and the displacement is
 // the unwrapped coordinate minus the image centre.
-// Rows (y, z) whose distance from the image's x axis is row_r or more hold no
-// node closer than row_r and are skipped.  fn also gets d2 = dx^2 + (dy^2 +
-// dz^2), summed in that order so that the row test and every node test agree.
+// Rows (y, z) whose distance from the image's x axis is row_r or more (plus
+// the FP64 window below) hold no node closer than row_r and are skipped.  fn
+// also gets d2 = dx^2 + (dy^2 + dz^2), summed in that order so that the row
+// test and every node test agree.  ip and am are the particle's index and
+// mapped radius (for the FP64 decision near the surface).
 template <typename TC, typename F>
 __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox<TC> (&b)[3], TC Rx, TC Ry, TC Rz,
-                                              TC delta, TC row_r, F&& fn) {
-  const TC row_r2 = row_r * row_r;
+                                              TC delta, TC row_r, F&& fn, int ip, TC am) {
+  // FP32 centres carry up to half an ulp of the box size (~4e-6 at L = 96),
+  // which moves d2 by up to ~3.5 a_map ulp(L); nodes whose d2 lies within
+  // twice that of a_map^2 are decided in FP64, so every kernel testing
+  // d2 < am * am (claim, uncover, cover, links) takes the oracle's decision
+  const TC win = (TC)(4.0 * 1.2e-7) * am * (TC)max(v.nx, max(v.ny, v.nz)) + (TC)1e-5;
+  const TC row_r2 = row_r * row_r + (sizeof(TC) == 4 ? (TC)2 * win : (TC)0);
+  const TC am2 = am * am;
   const int lane = threadIdx.x & 15, half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
 #pragma unroll
   for (int kb = 0; kb < 3; ++kb) {
@@ -103,7 +126,12 @@ __device__ __forceinline__ void for_box_cells(const View& v, const ImgBox<TC> (&
         const TC dx = (TC)xu - B.cx;
         const int k = kb - 1;
         const long long c = x + (long long)v.nx * (y + (long long)v.ny * z);
-        fn(x, y, z, c, dx, dy, dz, k, dx * dx + rho2);
+        TC d2 = dx * dx + rho2;
+        if constexpr (sizeof(TC) == 4) {
+          if (fabsf(d2 - am2) < win)
+            d2 = inside_fp64(v, ip, k, xu, y, zu) ? fminf(d2, nextafterf(am2, 0.0f)) : fmaxf(d2, am2);
+        }
+        fn(x, y, z, c, dx, dy, dz, k, d2);
       }
     }
   }
@@ -133,7 +161,7 @@ __global__ void k_claim(Batch B) {
       const int old = atomicCAS(v.owner + c, -1, i);
       if (old != -1 && old != i) atomicOr(v.err, ERR_OVERLAP);
     }
-  });
+  }, i, am);
 }
 
 // Band nodes of one particle collected by the scan of its bounding boxes, so
@@ -160,7 +188,7 @@ __device__ __forceinline__ bool band_push(BandList<TC>& L, long long c, TC dx, T
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) k_uncover(Batch B) {
+__global__ void __launch_bounds__(256, P == 0 ? 2 : 3) k_uncover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
@@ -214,7 +242,7 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
     // less than 0.5 per step; 0.6 leaves a margin)
     if (d2 < am * am || !(d2 < (am + (TC)0.6) * (am + (TC)0.6))) return;
     if (!band_push(L, c, dx, dy, dz, k)) release(c, dx, dy, dz, k);
-  });
+  }, i, am);
   __syncthreads();
   const int n = min(L.n, BAND_CAP);
   for (int e = threadIdx.x; e < n; e += blockDim.x)
@@ -229,7 +257,7 @@ __global__ void __launch_bounds__(256) k_uncover(Batch B) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(256) k_cover(Batch B) {
+__global__ void __launch_bounds__(256, P == 0 ? 2 : 4) k_cover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
@@ -270,7 +298,7 @@ __global__ void __launch_bounds__(256) k_cover(Batch B) {
     // nodes deeper than a_map - 0.6 were inside before the move (speed < 0.5)
     if (!(d2 < am * am) || d2 < inner * inner) return;
     if (!band_push(L, c, dx, dy, dz, k)) claim(c, dx, dy, dz);
-  });
+  }, i, am);
   __syncthreads();
   const int n = min(L.n, BAND_CAP);
   for (int e = threadIdx.x; e < n; e += blockDim.x) claim((long long)L.c[e], L.d[e][0], L.d[e][1], L.d[e][2]);
@@ -415,7 +443,7 @@ __global__ void __launch_bounds__(256, P == 0 ? 2 : 3) k_links(Batch B) {
     } else {
       overflow = true;
     }
-  });
+  }, i, am);
   if (overflow) atomicOr(v.err, ERR_LINKS);
   __syncthreads();
   const int nn = min(s_nodes, LINK_NODES_MAX);

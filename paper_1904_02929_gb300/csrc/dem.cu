@@ -145,44 +145,34 @@ __device__ __forceinline__ void load_pair_const(const View& v, PairConst<T>& c) 
   else c = v.pc_f;
 }
 
-// Minimum-image displacement R_b - R_a: the centre difference is taken in
-// FP64 (positions are FP64 on every path), the rest in precision T; returns
-// false when the pair is out of range.
+// Minimum-image displacement R_b - R_a and gap h = |d| - (a_a + a_b) of the
+// pair (a, b) in FP64 (the FP32 compute path takes them from the step
+// constants instead, see pairs_of); false when the pair is out of range.
 template <typename T>
 __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int b, T delta,
                                      const PairConst<T>& pc, T d[3], int& k, T& h) {
-  d[0] = (T)(Rs[3 * b] - Rs[3 * a]);
-  d[1] = (T)(Rs[3 * b + 1] - Rs[3 * a + 1]);
-  d[2] = (T)(Rs[3 * b + 2] - Rs[3 * a + 2]);
-  const T fnx = (T)v.nx, fny = (T)v.ny, fnz = (T)v.nz;
-  k = (int)floor(d[1] * sel<T>(v.inv_ny_d, v.inv_ny_f) + (T)0.5);
-  d[1] -= (T)k * fny;
-  d[0] -= (T)k * delta;
-  d[0] -= fnx * floor(d[0] * sel<T>(v.inv_nx_d, v.inv_nx_f) + (T)0.5);
-  d[2] -= fnz * floor(d[2] * sel<T>(v.inv_nz_d, v.inv_nz_f) + (T)0.5);
-  const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  static_assert(sizeof(T) == 8, "FP64 path");
   const T* pl = reinterpret_cast<const T*>(v.plb);
-  const T rsum = pl[12 * a + 9] + pl[12 * b + 9];   // radii from the compute-type copy
+  const T rsum = pl[12 * a + 9] + pl[12 * b + 9];
   const T lim = rsum + pc.hrange + (T)1e-6;
+  d[0] = Rs[3 * b] - Rs[3 * a];
+  d[1] = Rs[3 * b + 1] - Rs[3 * a + 1];
+  d[2] = Rs[3 * b + 2] - Rs[3 * a + 2];
+  k = le_image<T>(d[0], d[1], d[2], delta, v.nx, v.ny, v.nz, v.inv_nx_d, v.inv_ny_d, v.inv_nz_d);
+  const T d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   if (!(d2 < lim * lim)) return false;   // cheap rejection before the square root
   h = sqrt(d2) - rsum;
   return (h < pc.hrange) || (h < (T)0);
 }
 
-// Full interaction of the canonical pair (a, b) in precision T, given the
-// minimum-image displacement d, gap h and the pair's tangential spring as it
-// stood after the previous sub-step (zero for a new contact).
+// uab = U_a - U_b (with the image velocity of b), wa, wb: the spins.
 template <typename T>
-__device__ void pair_interact(const View& v, const double* Us, const double* Ws,
-                              int a, int b, const T d[3], int k, T h, const T spring[3], T ule, T dt,
-                              const PairConst<T>& pc, PairOut<T>& o, bool want_s) {
+__device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, const T uab[3], const T wa[3],
+                              const T wb[3], const T spring[3], T dt, const PairConst<T>& pc, PairOut<T>& o,
+                              bool want_s) {
   const T* pl = reinterpret_cast<const T*>(v.plb);
   const T ra = pl[12 * a + 9], rb = pl[12 * b + 9];
   const T dist = sqrt(dot3(d, d));
-  const T uab[3] = {(T)(Us[3 * a] - Us[3 * b]) - (T)k * ule, (T)(Us[3 * a + 1] - Us[3 * b + 1]),
-                    (T)(Us[3 * a + 2] - Us[3 * b + 2])};
-  const T wa[3] = {(T)Ws[3 * a], (T)Ws[3 * a + 1], (T)Ws[3 * a + 2]};
-  const T wb[3] = {(T)Ws[3 * b], (T)Ws[3 * b + 1], (T)Ws[3 * b + 2]};
   const T n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
   for (int c = 0; c < 3; ++c) {
     o.Fa[c] = o.Ta[c] = o.Tb[c] = o.Fc[c] = o.Fr[c] = o.ht[c] = (T)0;
@@ -192,7 +182,7 @@ __device__ void pair_interact(const View& v, const double* Us, const double* Ws,
   o.touching = 0;
   for (int c = 0; c < 6; ++c) o.S[c] = (T)0;
   // ---- contact
-  const T overlap = ra + rb - dist;
+  const T overlap = -h;   // (a_a + a_b) - |d|, from the accurate gap
   if (h < (T)0) {
     T ht[3] = {spring[0], spring[1], spring[2]};
     const T ws[3] = {ra * wa[0] + rb * wb[0], ra * wa[1] + rb * wb[1], ra * wa[2] + rb * wb[2]};
@@ -307,6 +297,8 @@ __device__ inline T warp_sum(T x) {
 struct State {
   const double *R, *U, *W;   // read: positions and velocities at the sub-step start
   double *Rn, *Un, *Wn;      // write: after the sub-step
+  const float* m;            // FP32 compute: mirror of the read buffer (R - Ro, U, W)
+  float* mn;                 //  and of the write buffer
 };
 
 template <typename TC>
@@ -340,6 +332,7 @@ __device__ inline void integ_const(const View& v, int i, T (&k)[8]) {
 template <typename T>
 struct StepConst {
   T delta, ule;
+  double Ro[3];     // step-start centre (the FP32 mirror's origin)
   T k[8];           // integ_const
   double dt;        // 1 / n_sub
   PairConst<T> pc;
@@ -349,6 +342,7 @@ template <typename T>
 __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   const Proto* pr = v.proto;
   c.delta = sel<T>(pr->delta, pr->delta_f);
+  c.Ro[0] = v.Ro[3 * i]; c.Ro[1] = v.Ro[3 * i + 1]; c.Ro[2] = v.Ro[3 * i + 2];
   c.ule = sel<T>(pr->ule, pr->ule_f);
   integ_const<T>(v, i, c.k);
   c.dt = v.dt_sub;
@@ -361,7 +355,7 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
 // Velocities are updated in precision T; positions always in FP64.
 template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
-                                     double dt, bool last, bool plb_double, const T* k) {
+                                     double dt, bool last, bool plb_double, const T* k, const double* Ro) {
   double R[3], U[3], W[3];
   const T im = k[6], iI = k[7], dtt = (T)dt;
   // A driven (wall) sphere keeps its velocity and spin whatever the forces.
@@ -374,6 +368,15 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
   }
   if (v.quasi2d && !driven) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
   for (int c = 0; c < 3; ++c) R[c] = S.R[3 * i + c] + dt * U[c];
+  if constexpr (sizeof(T) == 4) {
+    // the partners' FP32 view of this particle for the next sub-step
+    float* mm = S.mn + 12 * i;
+    for (int c = 0; c < 3; ++c) {
+      mm[c] = (float)(R[c] - Ro[c]);
+      mm[4 + c] = (float)U[c];
+      mm[8 + c] = (float)W[c];
+    }
+  }
   if (last) {
     const Proto* pr = v.proto;
     const double du = driven ? 0.0 : pr->ule;   // a driven sphere's velocity is prescribed
@@ -545,7 +548,23 @@ __device__ int collect_pairs(const View& v, int i, const SpringTable& old) {
     for (int r = 0; r < rounds; ++r) consider(r < cnt ? v.cell_ids[s0 + r] : -1, r < cnt);
   }
   if (base > PAIR_SLOTS && lane == 0) atomicOr(v.err, ERR_PAIRS);
-  return base < PAIR_SLOTS ? base : PAIR_SLOTS;
+  const int m = base < PAIR_SLOTS ? base : PAIR_SLOTS;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 compute: each candidate's step constants in the canonical
+    // orientation (a < b), so that both partners hold the same bits
+    __syncwarp();
+    for (int c = lane; c < m; c += 32) {
+      const int j = pj[c];
+      const int a = i < j ? i : j, b = i < j ? j : i;
+      double dx = R[3 * b] - R[3 * a], dy = R[3 * b + 1] - R[3 * a + 1], dz = R[3 * b + 2] - R[3 * a + 2];
+      const int k = le_image<double>(dx, dy, dz, delta, v.nx, v.ny, v.nz, v.inv_nx_d, v.inv_ny_d, v.inv_nz_d);
+      const double rs = v.rad[a] + v.rad[b];
+      v.pd[(long long)i * PAIR_SLOTS + c] =
+          make_float4((float)dx, (float)dy, (float)dz, (float)(dx * dx + dy * dy + dz * dz - rs * rs));
+      v.pk[(long long)i * PAIR_SLOTS + c] = (signed char)k;
+    }
+  }
+  return m;
 }
 
 // Pair forces on particle i for one sub-step, computed by one warp: lane l
@@ -561,6 +580,8 @@ template <typename T>
 struct PairRegs {
   int j[PAIR_SLOTS / 32];
   T h[PAIR_SLOTS / 32][3];   // (springs are exact in T: each is a T result)
+  float4 D[PAIR_SLOTS / 32];   // FP32 compute: the pair's step constants (D, c0)
+  int k[PAIR_SLOTS / 32];      //  and image index
 };
 
 // Sum over the LANES lanes of a lane group (a warp or a half-warp).
@@ -605,14 +626,49 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
     if (c >= npairs) continue;
     const int j = rg ? rg->j[slot] : pj[c];
     const int a = i < j ? i : j, b = i < j ? j : i;
-    T d[3], h;
-    int k;
-    bool touching = false;
-    if (pair_geometry<T>(v, S.R, a, b, delta, pc, d, k, h)) {
+    T d[3], h, uab[3], wa[3], wb[3];
+    bool touching = false, inr;
+    if constexpr (sizeof(T) == 8) {
+      int k;
+      inr = pair_geometry<T>(v, S.R, a, b, delta, pc, d, k, h);
+      if (inr) {
+        for (int x = 0; x < 3; ++x) {
+          uab[x] = S.U[3 * a + x] - S.U[3 * b + x];
+          wa[x] = S.W[3 * a + x];
+          wb[x] = S.W[3 * b + x];
+        }
+        uab[0] -= (T)k * ule;
+      }
+    } else {
+      // d = D + (e_b - e_a) with e the FP32 displacements since the step
+      // start; |d|^2 - (a_a + a_b)^2 = c0 + (2 D + e) . e, so the gap keeps
+      // the accuracy of the step's FP64 constants (no cancellation in FP32)
+      const float4 D = rg ? rg->D[slot] : v.pd[(long long)i * PAIR_SLOTS + c];
+      const int k = rg ? rg->k[slot] : (int)v.pk[(long long)i * PAIR_SLOTS + c];
+      const float* ma = S.m + 12 * a;
+      const float* mb = S.m + 12 * b;
+      const float ex = mb[0] - ma[0], ey = mb[1] - ma[1], ez = mb[2] - ma[2];
+      const float num = D.w + ((2.0f * D.x + ex) * ex + ((2.0f * D.y + ey) * ey + (2.0f * D.z + ez) * ez));
+      const float* pl = reinterpret_cast<const float*>(v.plb);
+      const float rsum = pl[12 * a + 9] + pl[12 * b + 9];
+      inr = num < pc.hrange * (2.0f * rsum + pc.hrange) + 1e-5f;
+      if (inr) {
+        d[0] = D.x + ex; d[1] = D.y + ey; d[2] = D.z + ez;
+        h = __fdividef(num, sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) + rsum);
+        inr = (h < pc.hrange) || (h < 0.0f);
+        for (int x = 0; x < 3; ++x) {
+          uab[x] = ma[4 + x] - mb[4 + x];
+          wa[x] = ma[8 + x];
+          wb[x] = mb[8 + x];
+        }
+        uab[0] -= (float)k * ule;
+      }
+    }
+    if (inr) {
       T spring[3];
       for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : ph[3 * c + x];
       PairOut<T> o;
-      pair_interact<T>(v, S.U, S.W, a, b, d, k, h, spring, ule, dt, pc, o, sample && i == a);
+      pair_interact<T>(v, a, b, d, h, uab, wa, wb, spring, dt, pc, o, sample && i == a);
       touching = o.touching != 0;
       for (int x = 0; x < 3; ++x) {
         if (rg) rg->h[slot][x] = touching ? o.ht[x] : (T)0;
@@ -706,7 +762,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
   __syncwarp();
   if (lane == 0 && valid) {
     integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8,
-                     sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i);
+                     sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i, sc ? sc->Ro : v.Ro + 3 * i);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(acc_rep(v, i) + 15 + c, (double)cv[c]);
@@ -769,6 +825,18 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       integ_const<T>(v, i, k);
       T* dst = reinterpret_cast<T*>(v.pconst) + 8 * i;
       for (int c = 0; c < 8; ++c) dst[c] = k[c];
+      if constexpr (sizeof(T) == 4) {
+        // the step's origin and both buffers' FP32 mirrors (zero displacement)
+        for (int c = 0; c < 3; ++c) {
+          v.Ro[3 * i + c] = v.R[3 * i + c];
+          for (int q = 0; q < 2; ++q) {
+            float* mm = v.m32[q] + 12 * i;
+            mm[c] = 0.0f;
+            mm[4 + c] = (float)v.U[3 * i + c];
+            mm[8 + c] = (float)v.W[3 * i + c];
+          }
+        }
+      }
     }
     my_np = np;
   }
@@ -814,8 +882,8 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       if ((threadIdx.x & 31) == 0) load_step_const<T>(v, i, sc);
       __syncwarp();
       nxt = spring_table(v, v.proto->t + 1);
-      toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W};
-      toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2};
+      toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0]};
+      toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1]};
     }
     const T dt = has ? (T)v.dt_sub : (T)0;
     PairRegs<T> rg;
@@ -824,10 +892,16 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const int c = (threadIdx.x & 31) + 32 * slot;
       rg.j[slot] = 0;
       rg.h[slot][0] = rg.h[slot][1] = rg.h[slot][2] = (T)0;
+      rg.D[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      rg.k[slot] = 0;
       if (has && c < my_np) {
         const T* ph = reinterpret_cast<const T*>(v.ph) + 3LL * i * PAIR_SLOTS;
         rg.j[slot] = v.pj[(long long)i * PAIR_SLOTS + c];
         rg.h[slot][0] = ph[3 * c]; rg.h[slot][1] = ph[3 * c + 1]; rg.h[slot][2] = ph[3 * c + 2];
+        if constexpr (sizeof(T) == 4) {
+          rg.D[slot] = v.pd[(long long)i * PAIR_SLOTS + c];
+          rg.k[slot] = v.pk[(long long)i * PAIR_SLOTS + c];
+        }
       }
     }
     for (int sub = 0; sub < B.max_nsub; ++sub) {
@@ -859,8 +933,8 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const int nsub = v.nsub;
       valid = valid && v.move && sub < nsub;
       // sub-step s reads A when (nsub - s) is even, so the last write lands in A
-      const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W};
-      const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2};
+      const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0]};
+      const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1]};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T, 16>(v, i, valid ? v.pcnt[i] : 0, valid, S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
                       spring_table(v, v.proto->t + 1), nullptr, nullptr);

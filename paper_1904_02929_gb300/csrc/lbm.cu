@@ -25,6 +25,10 @@
 //
 // Bytes per fluid node and step: 19 loads + 19 stores of the storage type
 // plus the 4-byte owner word (algorithmic 2 * 19 * s).
+#include <cuda.h>
+
+#include <mutex>
+
 #include "susp_dev.cuh"
 
 namespace susp_dev {
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   const int chunk = (total + gridDim.x - 1) / gridDim.x;
   const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
   if (t0 >= t1) return;
-  const int lx = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lx = threadIdx.x & 31;
   int b = box_of(B.tile_off, B.nbox, t0);
   for (int t = t0; t < t1; ++b) {
     const View& v = B.views[b];
@@ -753,6 +757,299 @@ __global__ void __launch_bounds__(256) k_collide_stream(Batch B) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Collide-stream with the source rows staged in shared memory by tensor copies
+// (FP32, FP16 and BF16 storage).
+//
+// A block takes its tiles of 128 (x) by 4 (y) nodes of one z plane in turn.
+// For each tile and population p one tensor copy brings the source window of
+// p -- x0 - XO .. x0 + 127 + XO (x0 - XO is 16-byte aligned), rows y0 - c_py
+// .. y0 - c_py + 3, plane z - c_pz -- into shared memory, all 19 completing
+// on the stage's mbarrier.  The copy engine's cost goes with the number of
+// box rows, so the windows are wide (288 bytes in 16-bit storage, 544 in
+// FP32) and short.  NSTAGE stages are in flight; the last warp to finish a
+// tile refills its stage with the tile NSTAGE further on; a 20th copy brings
+// the tile's owner words.  Each warp takes one row pair of 32 nodes of a
+// tile: interior pairs pull from shared memory (the x-periodic sources of
+// the two edge nodes of a row from global memory: staging those as well, by
+// 16-byte copies of the rows' other ends, measured slower), Lees-Edwards rows and the last row of an odd L_y take the scalar
+// path from global memory.  The per-node arithmetic is that of the row-pair
+// path, so the populations equal the direct kernel's bit for bit; the
+// viscous sums are reduced per warp instead of per block.  Boxes whose x
+// rows are not a multiple of 16 bytes (no tensor map) pull from global
+// memory in this kernel too.  Every wait is bounded: a stage that never
+// fills raises ERR_TIMEOUT and the block stops after waiting, bounded again,
+// for its copies in flight.
+// ---------------------------------------------------------------------------
+template <int P>
+struct TmaShape {
+  using T = typename Store<P>::T;
+  static constexpr int XO = 16 / (int)sizeof(T);   // window start x0 - XO: 16-byte aligned
+  static constexpr int TW = 128;                   // tile width (four 32-node row segments)
+  static constexpr int XB = TW + 2 * XO;           // window width (elements)
+  static constexpr int TH = 4;                     // tile rows: 8 warps = 4 segments x 2 row pairs
+  static constexpr int PLANE = XB * TH;            // elements per population window
+  static constexpr int POP_BYTES = 19 * PLANE * (int)sizeof(T);
+  static constexpr int OWN_BYTES = TW * TH * 4;                 // the tile's owner words
+  static constexpr int STAGE_BYTES = POP_BYTES + OWN_BYTES;
+  static constexpr int NSTAGE = sizeof(T) == 4 ? 2 : 4;
+  static constexpr int SMEM = NSTAGE * STAGE_BYTES + 8 * NSTAGE + 128;   // + slack to align the base
+};
+static_assert(TmaShape<1>::SMEM <= 113 * 1024 && TmaShape<2>::SMEM <= 113 * 1024,
+              "two staged blocks must fit one SM's shared memory");
+static_assert(TmaShape<1>::XB <= 256 && TmaShape<2>::XB <= 256, "tensor-copy box rows hold at most 256 elements");
+// every tensor copy lands on a 128-byte boundary of shared memory
+static_assert((TmaShape<1>::PLANE * 4) % 128 == 0 && (TmaShape<2>::PLANE * 2) % 128 == 0, "window alignment");
+static_assert(TmaShape<1>::POP_BYTES % 128 == 0 && TmaShape<2>::POP_BYTES % 128 == 0, "owner tile alignment");
+static_assert(TmaShape<1>::STAGE_BYTES % 128 == 0 && TmaShape<2>::STAGE_BYTES % 128 == 0, "stage alignment");
+
+// Tiles of one box for the staged kernel.
+__host__ __device__ inline int tma_tiles(int nx, int ny, int nz) {
+  return ((nx + TmaShape<1>::TW - 1) / TmaShape<1>::TW) * ((ny + TmaShape<1>::TH - 1) / TmaShape<1>::TH) * nz;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity to complete; false after about 2^31
+// SM cycles (about a second) without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  if (mbar_try(a, parity)) return true;
+  const long long c0 = clock64();
+  while (!mbar_try(a, parity))
+    if (clock64() - c0 > (1LL << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* map, int x, int y, int z, int q, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(q), "r"(bar)
+      : "memory");
+}
+
+template <int P> struct Cvt;
+template <> struct Cvt<1> { __device__ static float f(float x) { return x; } };
+template <> struct Cvt<2> { __device__ static float f(__half x) { return __half2float(x); } };
+template <> struct Cvt<3> { __device__ static float f(__nv_bfloat16 x) { return __bfloat162float(x); } };
+
+// Pull of the row pair (x, y), (x, y + 1) from the staged windows st (column
+// col = x - x0 of the tile, rows `row` and row + 1); the x-wrap sources of
+// the edge nodes (eL: x = 0, eR: x = nx - 1) from global memory, as the
+// direct pull takes them.
+template <int P, int p>
+struct StagedPull {
+  using T = typename Store<P>::T;
+  __device__ __forceinline__ static void run(const T* st, const T* __restrict__ fin, uint32_t nc, int nx,
+                                             uint32_t iA, int col, int row, int dxm, int dxp, int dzm, int dzp,
+                                             bool eL, bool eR, bool fA, bool fB, float rest, float2 (&u)[19]) {
+    using Sh = TmaShape<P>;
+    constexpr int cpx = D3Q19::cx(p), cpy = D3Q19::cy(p), cpz = D3Q19::cz(p);
+    const T* s = st + p * Sh::PLANE + row * Sh::XB + (col - cpx + Sh::XO);
+    float a = Cvt<P>::f(s[0]), b = Cvt<P>::f(s[Sh::XB]);
+    if constexpr (cpx != 0) {
+      if (cpx == 1 ? eL : eR) {
+        const int off = (cpx == 1 ? dxm : dxp) - cpy * nx + (cpz == 1 ? dzm : (cpz == -1 ? dzp : 0));
+        const uint32_t e = (uint32_t)p * nc + iA + (uint32_t)off;
+        a = Raw<P>::ld(fin, e);
+        b = Raw<P>::ld(fin, e + (uint32_t)nx);
+      }
+    }
+    const float r = (P == 1) ? (float)D3Q19::w(p) * rest : 0.0f;
+    u[p].x = fA ? a - r : 0.0f;
+    u[p].y = fB ? b - r : 0.0f;
+    StagedPull<P, p + 1>::run(st, fin, nc, nx, iA, col, row, dxm, dxp, dzm, dzp, eL, eR, fA, fB, rest, u);
+  }
+};
+template <int P>
+struct StagedPull<P, 19> {
+  __device__ __forceinline__ static void run(const typename Store<P>::T*, const typename Store<P>::T* __restrict__,
+                                             uint32_t, int, uint32_t, int, int, int, int, int, int, bool, bool,
+                                             bool, bool, float, float2 (&)[19]) {}
+};
+
+// First node (x0, y0) and plane z of staged tile lt of a box.
+__device__ __forceinline__ void tma_tile_xyz(const View& v, int lt, int& x0, int& y0, int& z) {
+  constexpr int TW = TmaShape<1>::TW, TH = TmaShape<1>::TH;
+  const int ntx = (v.nx + TW - 1) / TW, nty = (v.ny + TH - 1) / TH;
+  const int tpp = ntx * nty;
+  z = lt / tpp;
+  const int r = lt - z * tpp;
+  const int ty = r / ntx;
+  x0 = (r - ty * ntx) * TW;
+  y0 = ty * TH;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, 2) k_collide_stream_tma(Batch B) {
+  using T = typename Store<P>::T;
+  using Sh = TmaShape<P>;
+  constexpr int NS = Sh::NSTAGE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // tensor copies land on 128-byte boundaries: align the base whatever the
+  // static shared memory before it
+  unsigned char* const smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  uint64_t* const full = reinterpret_cast<uint64_t*>(smem + NS * Sh::STAGE_BYTES);
+  __shared__ int s_done[NS], s_issued[NS];
+  __shared__ int s_abort;
+  const int total = B.tile_off[B.nbox];
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int t0 = blockIdx.x * chunk, t1 = min(total, t0 + chunk);
+  if (t0 >= t1) return;
+  const int lx = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(full + s), 1);
+      s_done[s] = 0;
+      s_issued[s] = 0;
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // tile t into stage s (one thread)
+  auto issue = [&](int t, int s) {
+    const int b = box_of(B.tile_off, B.nbox, t);
+    const View& v = B.views[b];
+    const uint32_t bar = smem_u32(full + s);
+    ++s_issued[s];
+    if (!v.tmap) {
+      mbar_arrive(bar);   // this box pulls from global memory
+      return;
+    }
+    int x0, y0, z;
+    tma_tile_xyz(v, t - B.tile_off[b], x0, y0, z);
+    // maps: [0] fa, [1] fb (the step's source buffer), [2] the owner words
+    const char* maps = reinterpret_cast<const char*>(v.tmap);
+    const void* map = maps + ((v.proto->t & 1) ? 128 : 0);
+    mbar_expect_tx(bar, (uint32_t)Sh::STAGE_BYTES);
+    const uint32_t dst = smem_u32(smem + (size_t)s * Sh::STAGE_BYTES);
+#pragma unroll
+    for (int p = 0; p < 19; ++p)
+      tma_load_4d(dst + (uint32_t)(p * Sh::PLANE * sizeof(T)), map, x0 - Sh::XO, y0 - D3Q19::cy(p),
+                  wrap1(z - D3Q19::cz(p), v.nz), p, bar);
+    tma_load_3d(dst + (uint32_t)Sh::POP_BYTES, maps + 256, x0, y0, z, bar);
+  };
+  if (threadIdx.x == 0)
+    for (int j = 0; j < NS && t0 + j < t1; ++j) issue(t0 + j, j);
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+  float2 acc2[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc2[k] = make_float2(0.0f, 0.0f);
+  // this warp's viscous sums into its box's accumulator replica
+  auto flush = [&](const View& v) {
+    const float vfe = (P == 2) ? v.vf_f * v.inv_scale : v.vf_f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float a = warp_sum_f(acc[k] + vfe * (acc2[k].x + acc2[k].y));
+      if (lx == 0) atomicAdd(acc_rep(v, blockIdx.x) + k, (double)a);
+      acc[k] = 0.0f;
+      acc2[k] = make_float2(0.0f, 0.0f);
+    }
+  };
+  // the current box's constants, reloaded when the tile range enters a box
+  int cur = -1;
+  const View* vp = B.views;
+  const T* fin = nullptr;
+  T* fout = nullptr;
+  int nx = 0, ny = 0, nz = 0, nxny = 0;
+  bool staged = false, ladd = false;
+  for (int t = t0, j = 0; t < t1; ++t, ++j) {
+    const int s = j % NS;
+    const uint32_t par = (uint32_t)(j / NS) & 1u;
+    const int b = box_of(B.tile_off, B.nbox, t);
+    if (b != cur) {
+      if (cur >= 0) flush(*vp);
+      cur = b;
+      vp = B.views + b;
+      fin = static_cast<const T*>(fin_of(*vp));
+      fout = static_cast<T*>(fout_of(*vp));
+      nx = vp->nx; ny = vp->ny; nz = vp->nz; nxny = nx * ny;
+      staged = vp->tmap != nullptr;
+      ladd = vp->ladd != 0;
+    }
+    const View& v = *vp;
+    int x0, y0, z;
+    tma_tile_xyz(v, t - B.tile_off[b], x0, y0, z);
+    // warp w: 32-node segment w & 3, row pair w >> 2 of the tile
+    const int col = 32 * (wid & 3) + lx, row = 2 * (wid >> 2);
+    const int x = x0 + col, y = y0 + row;
+    const bool live = x < nx && y < ny;
+    const bool pair = live && y >= 1 && y + 1 <= ny - 2;
+    const uint32_t iA = (uint32_t)(x + nx * (y + ny * z));
+    // every lane waits (each acquires the copied data); the outcome and the
+    // stop decision are taken warp-wide so the warp stays converged
+    const bool ok = mbar_wait(smem_u32(full + s), par);
+    if (!__all_sync(0xffffffffu, ok) && lx == 0) {
+      atomicOr(v.err, ERR_TIMEOUT);
+      s_abort = 1;
+    }
+    if (__any_sync(0xffffffffu, *(volatile int*)&s_abort != 0)) break;
+    if (live) {
+      const int dzm = z == 0 ? (nz - 1) * nxny : -nxny, dzp = z == nz - 1 ? (1 - nz) * nxny : nxny;
+      if (!pair) {
+        lb_node_single<P>(v, fin, fout, x, y, z, dzm, dzp, acc);
+        if (y + 1 < ny) lb_node_single<P>(v, fin, fout, x, y + 1, z, dzm, dzp, acc);
+      } else if (!staged) {
+        if (ladd) lb_pair<P, true>(v, fin, fout, x, y, z, dzm, dzp, acc2);
+        else lb_pair<P, false>(v, fin, fout, x, y, z, dzm, dzp, acc2);
+      } else {
+        const unsigned char* st = smem + (size_t)s * Sh::STAGE_BYTES;
+        const int* own = reinterpret_cast<const int*>(st + Sh::POP_BYTES) + row * Sh::TW + col;
+        const bool fA = own[0] < 0, fB = own[Sh::TW] < 0;
+        const int dxm = x == 0 ? nx - 1 : -1, dxp = x == nx - 1 ? 1 - nx : 1;
+        const uint32_t nc = (uint32_t)v.ncell;
+        float2 u[19];
+        StagedPull<P, 0>::run(reinterpret_cast<const T*>(st), fin, nc, nx, iA, col, row, dxm, dxp, dzm, dzp,
+                              x == 0, x == nx - 1, fA, fB, v.rho0_f, u);
+        if (ladd) pair_collide<P, true>(v, fout, iA, fA, fB, u, acc2);
+        else pair_collide<P, false>(v, fout, iA, fA, fB, u, acc2);
+      }
+    }
+    // the stage is read: the last warp to get here refills it
+    __syncwarp();
+    if (lx == 0) {
+      // (the warp's shared-memory reads of the stage are complete: their
+      // values went into the stores above)
+      if (atomicAdd(&s_done[s], 1) == nwarp - 1) {
+        s_done[s] = 0;
+        if (t + NS < t1) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(t + NS, s);
+        }
+      }
+    }
+  }
+  if (cur >= 0) flush(*vp);
+  __syncthreads();
+  // copies still in flight (only after a timeout): wait for them, bounded,
+  // before the block's shared memory is released
+  if (threadIdx.x == 0)
+    for (int s = 0; s < NS; ++s)
+      if (s_issued[s] > 0) mbar_wait(smem_u32(full + s), (uint32_t)(s_issued[s] - 1) & 1u);
+}
+
 // Moments (rho, j) of the two Lees-Edwards boundary planes of every box, read
 // by the crossing pulls of the next step: plane 0 is y = 0, plane 1 is
 // y = ny-1.  The collide-stream writes them for the step after it (the
@@ -817,28 +1114,117 @@ __global__ void k_plane_moments(View v, const typename Store<P>::T* __restrict__
 using namespace susp_dev;
 
 // Tiles of the collide-stream grid (upper bound of its block count).
-// Collide-stream tiles of one box (32 x 2^tile_lg nodes).
-int lb_blocks(int nx, int ny, int nz, int tile_lg) {
+// Collide-stream tiles of one box: 32 x 2^tile_lg nodes, or the staged
+// kernel's 128 x 4.
+int lb_blocks(int nx, int ny, int nz, int tile_lg, int staged) {
+  if (staged) return tma_tiles(nx, ny, nz);
   const int th = 1 << tile_lg;
   return ((nx + 31) / 32) * ((ny + th - 1) / th) * nz;
 }
 
-// Resident blocks of k_collide_stream<P> per SM (*per) and the SM count.
-void lb_occupancy(int prec, int* per_sm, int* sms_out) {
+// Dynamic shared memory of the staged kernels, set once per device before
+// their first launch or occupancy query (both happen outside graph capture).
+static void tma_attrs() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_collide_stream_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaShape<1>::SMEM);
+  cudaFuncSetAttribute(k_collide_stream_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaShape<2>::SMEM);
+  cudaFuncSetAttribute(k_collide_stream_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaShape<3>::SMEM);
+  done[dev] = true;
+}
+
+// Resident blocks of the collide-stream kernel (direct, or staged: FP32 /
+// FP16 / BF16 only) per SM (*per) and the SM count.
+void lb_occupancy(int prec, int staged, int* per_sm, int* sms_out) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
-  switch (prec) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<0>, 256, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<1>, 256, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<2>, 256, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<3>, 256, 0); break;
+  if (staged && prec >= 1) {
+    tma_attrs();
+    switch (prec) {
+      case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream_tma<1>, 256, TmaShape<1>::SMEM); break;
+      case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream_tma<2>, 256, TmaShape<2>::SMEM); break;
+      default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream_tma<3>, 256, TmaShape<3>::SMEM); break;
+    }
+  } else {
+    switch (prec) {
+      case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<0>, 256, 0); break;
+      case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<1>, 256, 0); break;
+      case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<2>, 256, 0); break;
+      default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_stream<3>, 256, 0); break;
+    }
   }
   if (e != cudaSuccess || per < 1) per = 1;
   if (sms < 1) sms = 1;
   *per_sm = per;
   *sms_out = sms;
+}
+
+// Tensor maps of a box's two population buffers and its owner words for the
+// staged kernel, into host memory out[3][128 bytes]: [19][nz][ny][nx]
+// elements in windows of TmaShape::XB x TmaShape::TH x 1 x 1 (fa, fb), and
+// the [nz][ny][nx] owner words in tiles of TmaShape::TW x TmaShape::TH x 1;
+// zero fill outside.  Returns 0 (and the box
+// pulls from global memory) for FP64 storage, x rows that are not a
+// multiple of 16 bytes, or when the driver offers no encoder.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static std::mutex mu;
+  static bool tried = false;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+int lb_tensor_maps(int prec, int nx, int ny, int nz, void* fa, void* fb, void* owner, void* out) {
+  if (prec < 1 || prec > 3) return 0;
+  const size_t es = prec == 1 ? 4 : 2;
+  const int xb = prec == 1 ? TmaShape<1>::XB : TmaShape<2>::XB;
+  if ((nx * es) % 16 != 0) return 0;
+  if (((uintptr_t)fa | (uintptr_t)fb | (uintptr_t)owner) % 16 != 0) return 0;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return 0;
+  const CUtensorMapDataType dt = prec == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : prec == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 19};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
+  const cuuint32_t box[4] = {(cuuint32_t)xb, (cuuint32_t)TmaShape<1>::TH, 1, 1};
+  static_assert(TmaShape<1>::TH == TmaShape<2>::TH && TmaShape<1>::TW == TmaShape<2>::TW, "one tile shape");
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUtensorMap* m = static_cast<CUtensorMap*>(out);
+  void* bufs[2] = {fa, fb};
+  for (int k = 0; k < 2; ++k)
+    if (enc(m + k, dt, 4, bufs[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return 0;
+  // the owner words [nz][ny][nx] (int32), one tile per copy
+  const cuuint64_t odims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t ostr[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t obox[3] = {(cuuint32_t)TmaShape<1>::TW, (cuuint32_t)TmaShape<1>::TH, 1};
+  if (enc(m + 2, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, owner, odims, ostr, obox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 0;
+  return 1;
 }
 
 void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s) {
@@ -852,7 +1238,16 @@ void launch_plane_moments(int prec, const Batch& B, int total, cudaStream_t s) {
   }
 }
 
-void launch_collide_stream(int prec, const Batch& B, int grid, cudaStream_t s) {
+void launch_collide_stream(int prec, const Batch& B, int grid, int staged, cudaStream_t s) {
+  if (staged && prec >= 1) {
+    tma_attrs();
+    switch (prec) {
+      case 1: k_collide_stream_tma<1><<<grid, 256, TmaShape<1>::SMEM, s>>>(B); break;
+      case 2: k_collide_stream_tma<2><<<grid, 256, TmaShape<2>::SMEM, s>>>(B); break;
+      default: k_collide_stream_tma<3><<<grid, 256, TmaShape<3>::SMEM, s>>>(B); break;
+    }
+    return;
+  }
   switch (prec) {
     case 0: k_collide_stream<0><<<grid, 256, 0, s>>>(B); break;
     case 1: k_collide_stream<1><<<grid, 256, 0, s>>>(B); break;

@@ -131,6 +131,15 @@ struct View {
   int n;
   double *R, *U, *W, *rad, *amap, *mass, *inert, *inv_m, *inv_I;
   double *R2, *U2, *W2;           // second state buffer of the particle sub-steps
+  // FP32 compute: per particle the step-start centre Ro (FP64) and, for each
+  // state buffer, an FP32 mirror [n][12] of (R - Ro, U, W) (pads at 3, 7, 11)
+  // that the partners read; per candidate (canonical pair a < b) the
+  // step-start displacement D = R_b - R_a (minimum image, FP32) with
+  // c0 = |D|^2 - (a_a + a_b)^2 (taken in FP64), and the image index k
+  double* Ro;
+  float* m32[2];
+  float4* pd;                     // [n][PAIR_SLOTS] (D, c0)
+  signed char* pk;                // [n][PAIR_SLOTS]
   int* pcx;                       // [n][8] cell of each particle at the step start (x, y, z, x of the rows across the planes)
   void* plb;                    // [n][12] compute-type copy: R, U, W, radius (and pad)
   double *Fh, *Th, *Fcov, *Tcov, *Fp, *Tp;
@@ -163,6 +172,11 @@ struct View {
   unsigned long long* counters; // [0] samples, [1] contacts
   Proto* proto;
   int* err;
+  // three tensor maps (CUtensorMap, 128 bytes each) for the staged
+  // collide-stream: the population buffers fa, fb as [19][nz][ny][nx] and the
+  // owner words; NULL when the box has none (FP64 storage, or x rows not a
+  // multiple of 16 bytes)
+  const void* tmap;
 };
 
 // ERR_LINKS: a particle has more surface nodes than the link kernel stages.
@@ -174,7 +188,8 @@ constexpr int HSLOTS_DEV = 16;
 // particles instead of through the cell list.
 constexpr int BRUTE_PAIRS_MAX = 4096;
 
-enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8 };
+// ERR_TIMEOUT: a bounded device wait gave up (the step's results are invalid).
+enum ErrBits { ERR_OVERLAP = 1, ERR_UNSTABLE = 2, ERR_LINKS = 4, ERR_PAIRS = 8, ERR_TIMEOUT = 16 };
 
 // Replica r (taken modulo ACC_REP) of a box's step sums.
 __device__ __forceinline__ double* acc_rep(const View& v, int r) {
@@ -255,6 +270,13 @@ __device__ inline T feq(int q, T rho, T jx, T jy, T jz, T inv_rho) {
   T jc = jx * (T)D3Q19::cx(q) + jy * (T)D3Q19::cy(q) + jz * (T)D3Q19::cz(q);
   T jj = jx * jx + jy * jy + jz * jz;
   return (T)D3Q19::w(q) * (rho + (T)3 * jc + (T)4.5 * jc * jc * inv_rho - (T)1.5 * jj * inv_rho);
+}
+
+// Sum over the 32 lanes of a warp (fixed order).
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
 }
 
 // Block-wide sum of NV values held by every thread (blockDim multiple of 32,

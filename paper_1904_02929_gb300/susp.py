@@ -122,6 +122,12 @@ def library() -> C.CDLL:
         for name in ("susp_tune", "susp_batch_tune"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]
+        for name in ("susp_set_launch_shape", "susp_batch_set_launch_shape"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+        for name in ("susp_get_launch_shape", "susp_batch_get_launch_shape"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.susp_destroy.restype = None
         L.susp_destroy.argtypes = [C.c_void_p]
         L.susp_batch_workspace_bytes.restype = C.c_size_t
@@ -298,19 +304,46 @@ def susp_moduli(h):
     return float(gp.value), float(gpp.value)
 
 
-def _tune(fn, handle, where):
+def _get_shape(fn, handle, where) -> dict:
+    rows, bps, staged = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(fn(handle, C.byref(rows), C.byref(bps), C.byref(staged)), where)
+    return {"tile_rows": int(rows.value), "blocks_per_sm": int(bps.value), "staged": bool(staged.value)}
+
+
+def _tune(fn, get, handle, where):
     rows, bps, us = C.c_int(0), C.c_int(0), C.c_double(0.0)
     _check(fn(handle, C.byref(rows), C.byref(bps), C.byref(us)), where)
-    return {"tile_rows": int(rows.value), "blocks_per_sm": int(bps.value), "us": float(us.value)}
+    out = _get_shape(get, handle, where)
+    out["us"] = float(us.value)
+    return out
 
 
 def susp_tune(h) -> dict:
-    """Collide-stream launch shape chosen by timing (tile rows, blocks per SM, us)."""
-    return _tune(library().susp_tune, h, "susp_tune")
+    """Collide-stream launch shape chosen by timing (tile rows, blocks per SM,
+    staged, us)."""
+    return _tune(library().susp_tune, library().susp_get_launch_shape, h, "susp_tune")
 
 
 def susp_batch_tune(b) -> dict:
-    return _tune(library().susp_batch_tune, b, "susp_batch_tune")
+    return _tune(library().susp_batch_tune, library().susp_batch_get_launch_shape, b, "susp_batch_tune")
+
+
+def susp_set_launch_shape(h, tile_rows: int, blocks_per_sm: int, staged: bool) -> None:
+    _check(library().susp_set_launch_shape(h, int(tile_rows), int(blocks_per_sm), int(bool(staged))),
+           "susp_set_launch_shape")
+
+
+def susp_get_launch_shape(h) -> dict:
+    return _get_shape(library().susp_get_launch_shape, h, "susp_get_launch_shape")
+
+
+def susp_batch_set_launch_shape(b, tile_rows: int, blocks_per_sm: int, staged: bool) -> None:
+    _check(library().susp_batch_set_launch_shape(b, int(tile_rows), int(blocks_per_sm), int(bool(staged))),
+           "susp_batch_set_launch_shape")
+
+
+def susp_batch_get_launch_shape(b) -> dict:
+    return _get_shape(library().susp_batch_get_launch_shape, b, "susp_batch_get_launch_shape")
 
 
 def susp_destroy(h) -> None:
@@ -481,6 +514,12 @@ class Suspension:
     def tune(self) -> dict:
         return susp_tune(self.h)
 
+    def set_launch_shape(self, tile_rows: int, blocks_per_sm: int, staged: bool) -> None:
+        susp_set_launch_shape(self.h, tile_rows, blocks_per_sm, staged)
+
+    def launch_shape(self) -> dict:
+        return susp_get_launch_shape(self.h)
+
     def moduli(self):
         return susp_moduli(self.h)
 
@@ -536,6 +575,12 @@ class Batch:
 
     def tune(self) -> dict:
         return susp_batch_tune(self.b)
+
+    def set_launch_shape(self, tile_rows: int, blocks_per_sm: int, staged: bool) -> None:
+        susp_batch_set_launch_shape(self.b, tile_rows, blocks_per_sm, staged)
+
+    def launch_shape(self) -> dict:
+        return susp_batch_get_launch_shape(self.b)
 
     def profile(self, enable: bool):
         susp_batch_profile(self.b, enable)

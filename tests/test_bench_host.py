@@ -18,11 +18,14 @@ def test_peak_is_the_measured_copy_bandwidth():
         assert (peak, src) == (bench.FALLBACK_HBM_GBS, "fallback")
 
 
-def test_traffic_record_only_for_its_workload():
-    t = bench.k1_traffic("dst-96^3-phi0.50-N882")
+def test_traffic_record_only_for_its_workload_and_kernel():
+    t = bench.k1_traffic("dst-96^3-phi0.50-N882", "k_collide_stream<fp32>")
     # the record carries the kernel source's hash: a value means it is current
     assert t is None or 1e6 < t < 2 * 134479872
-    assert bench.k1_traffic("some-other-workload") is None
+    assert bench.k1_traffic("some-other-workload", "k_collide_stream<fp32>") is None
+    assert bench.k1_traffic("dst-96^3-phi0.50-N882", "some-other-kernel<fp32>") is None
+    assert bench.lb_kernel({"staged": True}, "fp16") == "k_collide_stream_tma<fp16>"
+    assert bench.lb_kernel({"staged": False}, "fp32") == "k_collide_stream<fp32>"
 
 
 def test_dominant_stage():
