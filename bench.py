@@ -94,6 +94,21 @@ def k1_traffic(workload_name: str, kernel: str):
         return None
 
 
+# Collide-stream launch shape for every leg: None lets the tuner choose
+# (default); --launch-shape ROWS,BLOCKS,STAGED fixes it (e.g. to profile the
+# shape an unprofiled run chose, since the tuner's timings differ under ncu).
+LAUNCH_SHAPE = None
+
+
+def shape_for(obj) -> dict:
+    """Tune the box or batch obj, or apply the fixed --launch-shape; returns
+    the shape in use."""
+    if LAUNCH_SHAPE is None:
+        return obj.tune()
+    obj.set_launch_shape(*LAUNCH_SHAPE)
+    return dict(obj.launch_shape(), us=None, fixed=True)
+
+
 def lb_kernel(shape: dict, storage: str) -> str:
     """Name of the collide-stream kernel a launch shape runs."""
     return ("k_collide_stream_tma" if shape.get("staged") else "k_collide_stream") + f"<{storage}>"
@@ -272,7 +287,7 @@ def batched_leg(ws, steps: int, warmup: int):
     for w, g in zip(ws, boxes):
         batch.attach(g, S.make_shear(**w.shear))
     batch.step(warmup)
-    tuned = batch.tune()                            # collide-stream launch shape for this batch
+    tuned = shape_for(batch)                        # collide-stream launch shape for this batch
     for g in boxes:
         g.stress_reset()
     batch.step(1)                                   # capture the step graph untimed
@@ -500,7 +515,7 @@ def monolayer_leg(steps: int, warmup: int):
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp16", **w.params)
     sh = S.make_shear(**w.shear)
     g.step(warmup, sh)
-    tuned = g.tune()
+    tuned = shape_for(g)
     g.step(1, sh)                                   # capture the step graph, untimed
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -542,7 +557,7 @@ def variant_leg(w, what: str, steps: int, warmup: int, **over):
     g = S.Suspension(w.nx, w.ny, w.nz, w.radius, w.pos, precision="fp32", **kw)
     sh = S.make_shear(**w.shear)
     g.step(warmup, sh)
-    tuned = g.tune()
+    tuned = shape_for(g)
     g.step(2, sh)                                   # capture the step graph, untimed
     torch.cuda.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -663,9 +678,15 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=5000)
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--launch-shape", default=None,
+                    help="ROWS,BLOCKS,STAGED: fix the collide-stream launch shape of every leg instead of tuning")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the serving horizon (200 for the full sweep horizon)")
     args = ap.parse_args()
+    global LAUNCH_SHAPE
+    if args.launch_shape:
+        r, bps, st = (int(x) for x in args.launch_shape.split(","))
+        LAUNCH_SHAPE = (r, bps, bool(st))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -695,7 +716,7 @@ def main():
     info = g.info()
     sh = S.make_shear(**w.shear)
     g.step(args.warmup, sh)
-    tuned = g.tune()                        # collide-stream launch shape (untimed)
+    tuned = shape_for(g)                        # collide-stream launch shape (untimed)
     torch.cuda.synchronize()
     nfluid = int((g.owner() < 0).sum())
 

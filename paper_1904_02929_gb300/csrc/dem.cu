@@ -352,7 +352,11 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
 // Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
 // the write state, with the pair force and torque (F, T); at the last sub-step
 // the Lees-Edwards wrap of the centre, the speed check and the compute-type copy.
-// Velocities are updated in precision T; positions always in FP64.
+// Velocities are updated in precision T.  FP64 compute steps the FP64 state.
+// FP32 compute steps the FP32 mirror (velocities, spin and the displacement
+// since the step start, with no FP64 arithmetic) and at the last sub-step
+// sets the FP64 centre to the step-start centre plus that displacement, so
+// positions are FP64 at every lattice step.
 template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
                                      double dt, bool last, bool plb_double, const T* k, const double* Ro) {
@@ -360,22 +364,39 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
   const T im = k[6], iI = k[7], dtt = (T)dt;
   // A driven (wall) sphere keeps its velocity and spin whatever the forces.
   const bool driven = v.has_drv && v.drv[i];
-  for (int c = 0; c < 3; ++c) {
-    const T F = k[c] + Fp[c];
-    const T Tq = k[3 + c] + Tp[c];
-    U[c] = driven ? S.U[3 * i + c] : (double)((T)S.U[3 * i + c] + dtt * F * im);
-    W[c] = driven ? S.W[3 * i + c] : (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
-  }
-  if (v.quasi2d && !driven) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
-  for (int c = 0; c < 3; ++c) R[c] = S.R[3 * i + c] + dt * U[c];
   if constexpr (sizeof(T) == 4) {
+    const float* m = S.m + 12 * i;
+    float Uf[3], Wf[3], df[3];
+    for (int c = 0; c < 3; ++c) {
+      Uf[c] = driven ? m[4 + c] : m[4 + c] + dtt * (k[c] + Fp[c]) * im;
+      Wf[c] = driven ? m[8 + c] : m[8 + c] + dtt * (k[3 + c] + Tp[c]) * iI;
+    }
+    if (v.quasi2d && !driven) { Uf[2] = 0.0f; Wf[0] = 0.0f; Wf[1] = 0.0f; }
+    for (int c = 0; c < 3; ++c) df[c] = m[c] + dtt * Uf[c];
     // the partners' FP32 view of this particle for the next sub-step
     float* mm = S.mn + 12 * i;
     for (int c = 0; c < 3; ++c) {
-      mm[c] = (float)(R[c] - Ro[c]);
-      mm[4 + c] = (float)U[c];
-      mm[8 + c] = (float)W[c];
+      mm[c] = df[c];
+      mm[4 + c] = Uf[c];
+      mm[8 + c] = Wf[c];
     }
+    if (!last) return;
+    // the FP64 state at the step's end (a driven sphere's velocity and spin
+    // are its prescribed FP64 values, and it moves by exactly one step of them)
+    for (int c = 0; c < 3; ++c) {
+      U[c] = driven ? v.U[3 * i + c] : (double)Uf[c];
+      W[c] = driven ? v.W[3 * i + c] : (double)Wf[c];
+      R[c] = driven ? Ro[c] + U[c] : Ro[c] + (double)df[c];
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      const T F = k[c] + Fp[c];
+      const T Tq = k[3 + c] + Tp[c];
+      U[c] = driven ? S.U[3 * i + c] : (double)((T)S.U[3 * i + c] + dtt * F * im);
+      W[c] = driven ? S.W[3 * i + c] : (double)((T)S.W[3 * i + c] + dtt * Tq * iI);
+    }
+    if (v.quasi2d && !driven) { U[2] = 0.0; W[0] = 0.0; W[1] = 0.0; }
+    for (int c = 0; c < 3; ++c) R[c] = S.R[3 * i + c] + dt * U[c];
   }
   if (last) {
     const Proto* pr = v.proto;
@@ -863,7 +884,12 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
     grid.sync();
   }
   if (ntot <= nwarps) {
-    // at most one particle per warp: its per-step constants stay in registers
+    // at most one particle per warp: its per-step constants stay in registers.
+    // FP32 compute: the partners' mirrors written by the candidate search
+    // above are read from the first sub-step on (one barrier first)
+    if constexpr (sizeof(T) == 4) {
+      if (!any_odd) grid.sync();
+    }
     const int g = gwarp;
     bool has = false;
     int bx = 0, i = 0, nsub = 0;

@@ -91,3 +91,29 @@ def test_timed_region_is_retaken_once_on_a_void_clock_record():
     runs.clear()
     res, clk, first = bench.timed_with_retake(run, lambda: None, agree=lambda f: len(runs) == 1)
     assert len(runs) == 2
+
+
+def test_fixed_launch_shape():
+    class Fake:
+        def __init__(self):
+            self.set = None
+
+        def tune(self):
+            return {"tile_rows": 8, "blocks_per_sm": 2, "staged": False, "us": 1.0}
+
+        def set_launch_shape(self, rows, bps, staged):
+            self.set = (rows, bps, staged)
+
+        def launch_shape(self):
+            return {"tile_rows": self.set[0], "blocks_per_sm": self.set[1], "staged": self.set[2]}
+
+    old = bench.LAUNCH_SHAPE
+    try:
+        bench.LAUNCH_SHAPE = None
+        assert bench.shape_for(Fake())["us"] == 1.0
+        bench.LAUNCH_SHAPE = (4, 1, True)
+        f = Fake()
+        got = bench.shape_for(f)
+        assert f.set == (4, 1, True) and got["staged"] and got["fixed"] and got["us"] is None
+    finally:
+        bench.LAUNCH_SHAPE = old
