@@ -105,7 +105,8 @@ def shape_for(obj) -> dict:
     the shape in use."""
     if LAUNCH_SHAPE is None:
         return obj.tune()
-    obj.set_launch_shape(*LAUNCH_SHAPE)
+    obj.set_launch_shape(*LAUNCH_SHAPE[:3])
+    obj.set_overlap(LAUNCH_SHAPE[3])
     return dict(obj.launch_shape(), us=None, fixed=True)
 
 
@@ -679,14 +680,15 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=5000)
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--launch-shape", default=None,
-                    help="ROWS,BLOCKS,STAGED: fix the collide-stream launch shape of every leg instead of tuning")
+                    help="ROWS,BLOCKS,STAGED[,OVERLAP]: fix the collide-stream launch shape (and whether it "
+                         "runs beside the particle kernel) of every leg instead of tuning")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the serving horizon (200 for the full sweep horizon)")
     args = ap.parse_args()
     global LAUNCH_SHAPE
     if args.launch_shape:
-        r, bps, st = (int(x) for x in args.launch_shape.split(","))
-        LAUNCH_SHAPE = (r, bps, bool(st))
+        f = [int(x) for x in args.launch_shape.split(",")] + [0]
+        LAUNCH_SHAPE = (f[0], f[1], bool(f[2]), bool(f[3]))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -802,7 +804,10 @@ def main():
             "stage_timing": ("the timed steps replay the plain step graph; stage times and the "
                              "collide-stream launch time come from as many steps right after, L2 "
                              "flushed the same way, timed by event nodes inside the replayed graph "
-                             "on the box's stream"),
+                             "on the streams the kernels run on" +
+                             ("; the step overlaps the collide-stream with the particle kernel: "
+                              "'particles' is the particle time not hidden behind the collide-stream"
+                              if tuned.get("overlap") else "")),
             "dominant_kernel": dominant_stage(stages),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

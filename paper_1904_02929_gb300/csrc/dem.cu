@@ -299,11 +299,15 @@ struct State {
   double *Rn, *Un, *Wn;      // write: after the sub-step
   const float* m;            // FP32 compute: mirror of the read buffer (R - Ro, U, W)
   float* mn;                 //  and of the write buffer
+  void* pw;                  // compute-type copy written at the last sub-step: v.plb, or v.plb_next
+                             // while the collide-stream still reads v.plb beside this kernel
 };
 
+// Particle i's entry of the compute-type copy at base (v.plb, or v.plb_next).
 template <typename TC>
-__device__ inline void write_plb(const View& v, int i, const double* R, const double* U, const double* W) {
-  TC* pp = reinterpret_cast<TC*>(v.plb) + 12 * i;
+__device__ inline void write_plb(void* base, const View& v, int i, const double* R, const double* U,
+                                 const double* W) {
+  TC* pp = reinterpret_cast<TC*>(base) + 12 * i;
   for (int c = 0; c < 3; ++c) {
     pp[c] = (TC)R[c];
     pp[3 + c] = (TC)U[c];
@@ -419,8 +423,8 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
       if (!(R[c] >= 0.0 && R[c] < Ls[c])) R[c] = 0.0;
     }
     if (bad) atomicOr(v.err, ERR_UNSTABLE);
-    if (plb_double) write_plb<double>(v, i, R, U, W);
-    else write_plb<float>(v, i, R, U, W);
+    if (plb_double) write_plb<double>(S.pw, v, i, R, U, W);
+    else write_plb<float>(S.pw, v, i, R, U, W);
   }
   for (int c = 0; c < 3; ++c) {
     S.Rn[3 * i + c] = R[c];
@@ -799,7 +803,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
 
 template <typename TC>
 __device__ inline void write_plb(const View& v, int i) {
-  write_plb<TC>(v, i, v.R + 3 * i, v.U + 3 * i, v.W + 3 * i);
+  write_plb<TC>(v.plb, v, i, v.R + 3 * i, v.U + 3 * i, v.W + 3 * i);
 }
 
 // All particle sub-steps of one lattice step, for every box, in one
@@ -808,16 +812,22 @@ __device__ inline void write_plb(const View& v, int i) {
 // integrates the particle into the other buffer, so one grid-wide barrier per
 // sub-step suffices; boxes with fewer sub-steps idle in the later rounds.  The
 // final state ends in the canonical buffer (R, U, W).
-// Warps (particles in flight) per block of the cooperative particle kernel.
+// Warps (particles in flight) per block of the cooperative particle kernel:
+// six warps at the FP32 path's 168 registers take 32 256 of an SM's 65 536,
+// so one block fits beside one 256-thread collide-stream block of 128
+// registers when the two kernels overlap.
 #ifndef DEM_WARPS
-#define DEM_WARPS 4
+#define DEM_WARPS 6
 #endif
 
 // End of the lattice step for every box of the batch, once every sub-step's
 // forces and virials are in: one block per box (a block takes several boxes
 // when the grid is smaller than the batch).  Saves the separate finalisation
-// launch whenever particles move.
+// launch whenever particles move -- unless the collide-stream runs beside
+// this kernel (B.dem_fin = 0): its viscous sums are then still coming and
+// the finalisation is a launch of its own after both.
 __device__ __forceinline__ void finalize_boxes(const Batch& B, cooperative_groups::grid_group& grid) {
+  if (!B.dem_fin) return;
   grid.sync();
   for (int b = blockIdx.x; b < B.nbox; b += gridDim.x) {
     finalize_box(B.views[b]);
@@ -826,7 +836,7 @@ __device__ __forceinline__ void finalize_boxes(const Batch& B, cooperative_group
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
+__global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_step(Batch B) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int wib = threadIdx.x >> 5;
@@ -908,8 +918,9 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       if ((threadIdx.x & 31) == 0) load_step_const<T>(v, i, sc);
       __syncwarp();
       nxt = spring_table(v, v.proto->t + 1);
-      toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0]};
-      toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1]};
+      void* pw = B.dem_fin ? v.plb : v.plb_next;
+      toA = State{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0], pw};
+      toB = State{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1], pw};
     }
     const T dt = has ? (T)v.dt_sub : (T)0;
     PairRegs<T> rg;
@@ -959,8 +970,9 @@ __global__ void __launch_bounds__(32 * DEM_WARPS) k_dem_step(Batch B) {
       const int nsub = v.nsub;
       valid = valid && v.move && sub < nsub;
       // sub-step s reads A when (nsub - s) is even, so the last write lands in A
-      const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0]};
-      const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1]};
+      void* pw = B.dem_fin ? v.plb : v.plb_next;
+      const State toA{v.R2, v.U2, v.W2, v.R, v.U, v.W, v.m32[1], v.m32[0], pw};
+      const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1], pw};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T, 16>(v, i, valid ? v.pcnt[i] : 0, valid, S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
                       spring_table(v, v.proto->t + 1), nullptr, nullptr);

@@ -177,6 +177,10 @@ struct View {
   // owner words; NULL when the box has none (FP64 storage, or x rows not a
   // multiple of 16 bytes)
   const void* tmap;
+  // [n][12] the compute-type copy of the next step, written by the particle
+  // kernel while the collide-stream still reads plb beside it (the
+  // finalisation then copies it into plb)
+  void* plb_next;
 };
 
 // ERR_LINKS: a particle has more surface nodes than the link kernel stages.
@@ -208,6 +212,7 @@ struct Batch {
   int nbox;
   int max_nsub;
   int tile_lg;                        // collide-stream tile height: 2^tile_lg rows
+  int dem_fin;                        // the particle kernel ends with the step's finalisation
 };
 
 // Box owning global work index g (off is an ascending prefix table).

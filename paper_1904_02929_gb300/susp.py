@@ -54,7 +54,7 @@ class susp_params(C.Structure):
 class susp_info(C.Structure):
     _fields_ = [("dem_substeps", C.c_int), ("launches_per_step", C.c_int),
                 ("brute_force_pairs", C.c_int), ("ncell", C.c_longlong),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("overlap", C.c_int)]
 
 
 class susp_shear(C.Structure):
@@ -125,6 +125,11 @@ def library() -> C.CDLL:
         for name in ("susp_set_launch_shape", "susp_batch_set_launch_shape"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+        for name in ("susp_set_overlap", "susp_batch_set_overlap"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [C.c_void_p, C.c_int]
+        L.susp_batch_get_overlap.restype = C.c_int
+        L.susp_batch_get_overlap.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
         for name in ("susp_get_launch_shape", "susp_batch_get_launch_shape"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -320,12 +325,34 @@ def _tune(fn, get, handle, where):
 
 def susp_tune(h) -> dict:
     """Collide-stream launch shape chosen by timing (tile rows, blocks per SM,
-    staged, us)."""
-    return _tune(library().susp_tune, library().susp_get_launch_shape, h, "susp_tune")
+    staged, us) and whether the step overlaps it with the particle kernel."""
+    out = _tune(library().susp_tune, library().susp_get_launch_shape, h, "susp_tune")
+    out["overlap"] = susp_get_overlap(h)
+    return out
 
 
 def susp_batch_tune(b) -> dict:
-    return _tune(library().susp_batch_tune, library().susp_batch_get_launch_shape, b, "susp_batch_tune")
+    out = _tune(library().susp_batch_tune, library().susp_batch_get_launch_shape, b, "susp_batch_tune")
+    out["overlap"] = susp_batch_get_overlap(b)
+    return out
+
+
+def susp_set_overlap(h, enable: bool) -> None:
+    _check(library().susp_set_overlap(h, int(bool(enable))), "susp_set_overlap")
+
+
+def susp_get_overlap(h) -> bool:
+    return bool(susp_get_info(h).overlap)
+
+
+def susp_batch_set_overlap(b, enable: bool) -> None:
+    _check(library().susp_batch_set_overlap(b, int(bool(enable))), "susp_batch_set_overlap")
+
+
+def susp_batch_get_overlap(b) -> bool:
+    v = C.c_int(0)
+    _check(library().susp_batch_get_overlap(b, C.byref(v)), "susp_batch_get_overlap")
+    return bool(v.value)
 
 
 def susp_set_launch_shape(h, tile_rows: int, blocks_per_sm: int, staged: bool) -> None:
@@ -518,7 +545,10 @@ class Suspension:
         susp_set_launch_shape(self.h, tile_rows, blocks_per_sm, staged)
 
     def launch_shape(self) -> dict:
-        return susp_get_launch_shape(self.h)
+        return dict(susp_get_launch_shape(self.h), overlap=susp_get_overlap(self.h))
+
+    def set_overlap(self, enable: bool) -> None:
+        susp_set_overlap(self.h, enable)
 
     def moduli(self):
         return susp_moduli(self.h)
@@ -580,7 +610,10 @@ class Batch:
         susp_batch_set_launch_shape(self.b, tile_rows, blocks_per_sm, staged)
 
     def launch_shape(self) -> dict:
-        return susp_batch_get_launch_shape(self.b)
+        return dict(susp_batch_get_launch_shape(self.b), overlap=susp_batch_get_overlap(self.b))
+
+    def set_overlap(self, enable: bool) -> None:
+        susp_batch_set_overlap(self.b, enable)
 
     def profile(self, enable: bool):
         susp_batch_profile(self.b, enable)

@@ -104,6 +104,9 @@ def test_fixed_launch_shape():
         def set_launch_shape(self, rows, bps, staged):
             self.set = (rows, bps, staged)
 
+        def set_overlap(self, on):
+            self.ov = on
+
         def launch_shape(self):
             return {"tile_rows": self.set[0], "blocks_per_sm": self.set[1], "staged": self.set[2]}
 
@@ -111,9 +114,9 @@ def test_fixed_launch_shape():
     try:
         bench.LAUNCH_SHAPE = None
         assert bench.shape_for(Fake())["us"] == 1.0
-        bench.LAUNCH_SHAPE = (4, 1, True)
+        bench.LAUNCH_SHAPE = (4, 1, True, False)
         f = Fake()
         got = bench.shape_for(f)
-        assert f.set == (4, 1, True) and got["staged"] and got["fixed"] and got["us"] is None
+        assert f.set == (4, 1, True) and not f.ov and got["staged"] and got["fixed"] and got["us"] is None
     finally:
         bench.LAUNCH_SHAPE = old
