@@ -166,12 +166,46 @@ __device__ inline bool pair_geometry(const View& v, const double* Rs, int a, int
 }
 
 // uab = U_a - U_b (with the image velocity of b), wa, wb: the spins.
+// The factors of a pair's lubrication terms that depend on the two radii
+// only (the resistance functions of the gap aside): taken once per lattice
+// step for the pairs a warp holds in registers, else in line.  Both give the
+// same bits: the products and quotients are formed in the same order.
+template <typename T>
+struct LubK {
+  T ra, rb;                                // the radii of a and b
+  T xa, ya, yba, ybb, ycaa, ycbb, ycab;    // XA / inv, YA / lg, YB_a / lg, ... (radius factors)
+  T sc, dl, xcdl, cinv;                    // 2 / (a_a + a_b), scaled roughness, xi_c + dl, 1 / (xi_c + dl)
+};
+
+template <typename T>
+__device__ __forceinline__ void lub_factors(T ra, T rb, const PairConst<T>& pc, LubK<T>& k) {
+  k.ra = ra;
+  k.rb = rb;
+  k.sc = (T)2 / (ra + rb);
+  const T xc = k.sc * pc.lub_cut;
+  k.dl = k.sc * pc.lub_delta;
+  k.xcdl = xc + k.dl;
+  k.cinv = (T)1 / (xc + k.dl);
+  const T be = rb / ra, bj = ra / rb;
+  const T pi = (T)3.14159265358979323846;
+  const T e0 = pc.eta0;
+  const T op = (T)1 + be, oq = (T)1 + bj;
+  k.xa = e0 * (T)6 * pi * ra * ((T)2 * be * be / (op * op * op));
+  k.ya = e0 * (T)6 * pi * ra * ((T)4 * be * ((T)2 + be + (T)2 * be * be) / ((T)15 * op * op * op));
+  k.yba = e0 * (T)4 * pi * ra * ra * (be * ((T)4 + be) / ((T)5 * op * op));
+  k.ybb = e0 * (T)4 * pi * rb * rb * (bj * ((T)4 + bj) / ((T)5 * oq * oq));
+  k.ycaa = e0 * (T)8 * pi * ra * ra * ra * ((T)2 * be / ((T)5 * op));
+  k.ycbb = e0 * (T)8 * pi * rb * rb * rb * ((T)2 * bj / ((T)5 * oq));
+  k.ycab = e0 * (T)8 * pi * ra * ra * ra * (be * be / ((T)10 * op));
+}
+
+// lk: the pair's radius factors taken for the step, or NULL (in line).
 template <typename T>
 __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, const T uab[3], const T wa[3],
                               const T wb[3], const T spring[3], T dt, const PairConst<T>& pc, PairOut<T>& o,
-                              bool want_s) {
+                              bool want_s, const LubK<T>* lk) {
   const T* pl = reinterpret_cast<const T*>(v.plb);
-  const T ra = pl[12 * a + 9], rb = pl[12 * b + 9];
+  const T ra = lk ? lk->ra : pl[12 * a + 9], rb = lk ? lk->rb : pl[12 * b + 9];
   const T dist = sqrt(dot3(d, d));
   const T n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
   for (int c = 0; c < 3; ++c) {
@@ -227,21 +261,19 @@ __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, co
   // ---- lubrication correction
   if (pc.lub && h < pc.lub_cut) {
     const T hh = h < (T)0 ? (T)0 : h;
-    const T sc = (T)2 / (ra + rb);
-    const T xi = sc * hh, xc = sc * pc.lub_cut, dl = sc * pc.lub_delta;
-    const T inv = (T)1 / (xi + dl) - (T)1 / (xc + dl);
-    const T lg = log((xc + dl) / (xi + dl));
-    const T be = rb / ra, bj = ra / rb;
-    const T pi = (T)3.14159265358979323846;
-    const T e0 = pc.eta0;
-    const T op = (T)1 + be, oq = (T)1 + bj;
-    const T XA = e0 * (T)6 * pi * ra * ((T)2 * be * be / (op * op * op)) * inv;
-    const T YA = e0 * (T)6 * pi * ra * ((T)4 * be * ((T)2 + be + (T)2 * be * be) / ((T)15 * op * op * op)) * lg;
-    const T YBa = e0 * (T)4 * pi * ra * ra * (be * ((T)4 + be) / ((T)5 * op * op)) * lg;
-    const T YBb = e0 * (T)4 * pi * rb * rb * (bj * ((T)4 + bj) / ((T)5 * oq * oq)) * lg;
-    const T YCaa = e0 * (T)8 * pi * ra * ra * ra * ((T)2 * be / ((T)5 * op)) * lg;
-    const T YCbb = e0 * (T)8 * pi * rb * rb * rb * ((T)2 * bj / ((T)5 * oq)) * lg;
-    const T YCab = e0 * (T)8 * pi * ra * ra * ra * (be * be / ((T)10 * op)) * lg;
+    LubK<T> kl;
+    if (!lk) lub_factors<T>(ra, rb, pc, kl);
+    const LubK<T>& K = lk ? *lk : kl;
+    const T xi = K.sc * hh, dl = K.dl;
+    const T inv = (T)1 / (xi + dl) - K.cinv;
+    const T lg = log(K.xcdl / (xi + dl));
+    const T XA = K.xa * inv;
+    const T YA = K.ya * lg;
+    const T YBa = K.yba * lg;
+    const T YBb = K.ybb * lg;
+    const T YCaa = K.ycaa * lg;
+    const T YCbb = K.ycbb * lg;
+    const T YCab = K.ycab * lg;
     const T un = dot3(uab, n);
     T wan[3], wbn[3], nxu[3];
     cross3(wa, n, wan);
@@ -256,6 +288,10 @@ __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, co
       o.Tb[c] += -YBb * nxu[c] - YCbb * wbt - YCab * wat;
     }
     if (want_s) {
+      const T be = rb / ra, bj = ra / rb;
+      const T pi = (T)3.14159265358979323846;
+      const T e0 = pc.eta0;
+      const T op = (T)1 + be, oq = (T)1 + bj;
       // stresslets of both spheres (G and H blocks), each with its own radius
       // and beta = partner / own radius; the G terms are odd in (n, U_a - U_b)
       // and the H terms even in n, so both take n and uab:
@@ -340,6 +376,7 @@ struct StepConst {
   T k[8];           // integ_const
   double dt;        // 1 / n_sub
   PairConst<T> pc;
+  float me[12];     // FP32 compute: the warp's own mirror (R - Ro, U, W at 0, 4, 8) of the current sub-step
 };
 
 template <typename T>
@@ -351,6 +388,12 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
   integ_const<T>(v, i, c.k);
   c.dt = v.dt_sub;
   load_pair_const<T>(v, c.pc);
+  // the mirror as the candidate search writes it for the first sub-step
+  for (int q = 0; q < 3; ++q) {
+    c.me[q] = 0.0f;
+    c.me[4 + q] = (float)v.U[3 * i + q];
+    c.me[8 + q] = (float)v.W[3 * i + q];
+  }
 }
 
 // Semi-implicit Euler sub-step of particle i (Eq. 1) from the read state to
@@ -363,13 +406,16 @@ __device__ inline void load_step_const(const View& v, int i, StepConst<T>& c) {
 // positions are FP64 at every lattice step.
 template <typename T>
 __device__ inline void integrate_one(const View& v, int i, const State& S, const T Fp[3], const T Tp[3],
-                                     double dt, bool last, bool plb_double, const T* k, const double* Ro) {
+                                     double dt, bool last, bool plb_double, const T* k, const double* Ro,
+                                     float* me) {
   double R[3], U[3], W[3];
   const T im = k[6], iI = k[7], dtt = (T)dt;
   // A driven (wall) sphere keeps its velocity and spin whatever the forces.
   const bool driven = v.has_drv && v.drv[i];
   if constexpr (sizeof(T) == 4) {
-    const float* m = S.m + 12 * i;
+    // this particle's mirror: the warp's copy in shared memory when it holds
+    // the particle for the whole step (the same values as the read buffer)
+    const float* m = me ? me : S.m + 12 * i;
     float Uf[3], Wf[3], df[3];
     for (int c = 0; c < 3; ++c) {
       Uf[c] = driven ? m[4 + c] : m[4 + c] + dtt * (k[c] + Fp[c]) * im;
@@ -384,6 +430,12 @@ __device__ inline void integrate_one(const View& v, int i, const State& S, const
       mm[4 + c] = Uf[c];
       mm[8 + c] = Wf[c];
     }
+    if (me)
+      for (int c = 0; c < 3; ++c) {
+        me[c] = df[c];
+        me[4 + c] = Uf[c];
+        me[8 + c] = Wf[c];
+      }
     if (!last) return;
     // the FP64 state at the step's end (a driven sphere's velocity and spin
     // are its prescribed FP64 values, and it moves by exactly one step of them)
@@ -624,7 +676,7 @@ __device__ __forceinline__ T group_sum(T x) {
 template <typename T, int LANES>
 __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool valid, const State& S, T dt,
                                          int sample, bool last, const SpringTable& next,
-                                         const StepConst<T>* sc, PairRegs<T>* rg) {
+                                         StepConst<T>* sc, PairRegs<T>* rg, const LubK<T>* lkw) {
   constexpr int NS = PAIR_SLOTS / LANES;   // candidate slots per lane
   const int lane = threadIdx.x & (LANES - 1);
   const int grp_shift = (threadIdx.x & 31) & ~(LANES - 1);   // first lane of the group
@@ -670,22 +722,23 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
       // the accuracy of the step's FP64 constants (no cancellation in FP32)
       const float4 D = rg ? rg->D[slot] : v.pd[(long long)i * PAIR_SLOTS + c];
       const int k = rg ? rg->k[slot] : (int)v.pk[(long long)i * PAIR_SLOTS + c];
-      const float* ma = S.m + 12 * a;
-      const float* mb = S.m + 12 * b;
-      const float ex = mb[0] - ma[0], ey = mb[1] - ma[1], ez = mb[2] - ma[2];
+      // both mirrors, 16-byte aligned rows of 12 (d, U, W and pads), all six
+      // loads issued together
+      const float4* qa = reinterpret_cast<const float4*>(S.m + 12 * a);
+      const float4* qb = reinterpret_cast<const float4*>(S.m + 12 * b);
+      const float4 da = qa[0], db = qb[0], ua4 = qa[1], ub4 = qb[1], wa4 = qa[2], wb4 = qb[2];
+      const float ex = db.x - da.x, ey = db.y - da.y, ez = db.z - da.z;
       const float num = D.w + ((2.0f * D.x + ex) * ex + ((2.0f * D.y + ey) * ey + (2.0f * D.z + ez) * ez));
       const float* pl = reinterpret_cast<const float*>(v.plb);
-      const float rsum = pl[12 * a + 9] + pl[12 * b + 9];
+      const float rsum = lkw ? lkw[c].ra + lkw[c].rb : pl[12 * a + 9] + pl[12 * b + 9];
       inr = num < pc.hrange * (2.0f * rsum + pc.hrange) + 1e-5f;
       if (inr) {
         d[0] = D.x + ex; d[1] = D.y + ey; d[2] = D.z + ez;
         h = __fdividef(num, sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) + rsum);
         inr = (h < pc.hrange) || (h < 0.0f);
-        for (int x = 0; x < 3; ++x) {
-          uab[x] = ma[4 + x] - mb[4 + x];
-          wa[x] = ma[8 + x];
-          wb[x] = mb[8 + x];
-        }
+        uab[0] = ua4.x - ub4.x; uab[1] = ua4.y - ub4.y; uab[2] = ua4.z - ub4.z;
+        wa[0] = wa4.x; wa[1] = wa4.y; wa[2] = wa4.z;
+        wb[0] = wb4.x; wb[1] = wb4.y; wb[2] = wb4.z;
         uab[0] -= (float)k * ule;
       }
     }
@@ -693,7 +746,7 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
       T spring[3];
       for (int x = 0; x < 3; ++x) spring[x] = rg ? rg->h[slot][x] : ph[3 * c + x];
       PairOut<T> o;
-      pair_interact<T>(v, a, b, d, h, uab, wa, wb, spring, dt, pc, o, sample && i == a);
+      pair_interact<T>(v, a, b, d, h, uab, wa, wb, spring, dt, pc, o, sample && i == a, lkw ? lkw + c : nullptr);
       touching = o.touching != 0;
       for (int x = 0; x < 3; ++x) {
         if (rg) rg->h[slot][x] = touching ? o.ht[x] : (T)0;
@@ -787,7 +840,8 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
   __syncwarp();
   if (lane == 0 && valid) {
     integrate_one<T>(v, i, S, F, Tq, sc ? sc->dt : v.dt_sub, last, sizeof(T) == 8,
-                     sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i, sc ? sc->Ro : v.Ro + 3 * i);
+                     sc ? sc->k : reinterpret_cast<const T*>(v.pconst) + 8 * i, sc ? sc->Ro : v.Ro + 3 * i,
+                     sc ? sc->me : nullptr);
     if (sample) {
       for (int c = 0; c < 9; ++c) {
         atomicAdd(acc_rep(v, i) + 15 + c, (double)cv[c]);
@@ -911,6 +965,8 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
     const View& v = B.views[bx];
     __shared__ StepConst<T> s_sc[DEM_WARPS];
     StepConst<T>& sc = s_sc[wib];
+    // FP32 compute: each warp's pairs' radius factors for the step
+    __shared__ LubK<T> s_lk[sizeof(T) == 4 ? DEM_WARPS : 1][sizeof(T) == 4 ? PAIR_SLOTS : 1];
     SpringTable nxt{};
     State toA{}, toB{};
     if (has) {
@@ -938,6 +994,10 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
         if constexpr (sizeof(T) == 4) {
           rg.D[slot] = v.pd[(long long)i * PAIR_SLOTS + c];
           rg.k[slot] = v.pk[(long long)i * PAIR_SLOTS + c];
+          // the pair's radius factors for the step (the lane that takes the slot)
+          const int j = rg.j[slot], a = i < j ? i : j, b = i < j ? j : i;
+          const float* pl = reinterpret_cast<const float*>(v.plb);
+          lub_factors<float>(pl[12 * a + 9], pl[12 * b + 9], sc.pc, s_lk[wib][c]);
         }
       }
     }
@@ -945,7 +1005,8 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
       if (has && sub < nsub) {
         // sub-step s reads A when (nsub - s) is even, so the last write lands in A
         const State& S = ((nsub - sub) & 1) ? toA : toB;
-        pairs_of<T, 32>(v, i, my_np, true, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg);
+        pairs_of<T, 32>(v, i, my_np, true, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg,
+                        sizeof(T) == 4 ? s_lk[wib] : nullptr);
       }
       if (sub + 1 < B.max_nsub) grid.sync();
     }
@@ -975,7 +1036,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1], pw};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T, 16>(v, i, valid ? v.pcnt[i] : 0, valid, S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
-                      spring_table(v, v.proto->t + 1), nullptr, nullptr);
+                      spring_table(v, v.proto->t + 1), nullptr, nullptr, nullptr);
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }
