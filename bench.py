@@ -305,7 +305,12 @@ def batched_leg(ws, steps: int, warmup: int):
     stages, k1_n = S.susp_batch_profile_stages(batch.b)
     k1_ms = stages["collide_stream"]
     batch.profile(False)
-    launches_b = 1 + 5 + 3                           # collide, cell list + particles (+ finalisation), node map + links
+    # kernels per batched step: collide-stream, the cell-list build (four,
+    # only when a box is too large for the brute-force pair search), the
+    # particle kernel (which ends with the finalisation), node map (two) and
+    # links
+    any_cells = any(g.info().brute_force_pairs == 0 for g in boxes if g.n > 0)
+    launches_b = 1 + (4 if any_cells else 0) + 1 + 2 + 1
     mem_b = sum(g.nbytes for g in boxes)
     batch.close()
     for g in boxes:
