@@ -168,6 +168,30 @@ susp_status susp_get_particles(susp *h, double *pos, double *vel, double *omega)
 /* Hydrodynamic link force and torque [3n] that the next step applies. Synchronises. */
 susp_status susp_get_hydro(susp *h, double *force, double *torque);
 
+/* A step's results in one transfer (no counterpart in the paper): the device
+ * gathers the error word, the stress sums and sample counters, the angular
+ * histogram and the particles' centres, velocities and spins into a block of
+ * susp_results_bytes(h) bytes in the workspace and copies it to host_buf
+ * with one copy on the handle's stream.  async = 0: synchronises and returns
+ * the device status as susp_get_particles does.  async = 1: only enqueues
+ * the gather and the copy and returns SUSP_OK; host_buf must then be pinned
+ * host memory, and holds the block once the stream has passed the copy (the
+ * caller waits on an event recorded after the call, or synchronises); a
+ * later call may reuse host_buf only after that.  The block's status and
+ * contents are read on the host by susp_results_particles and
+ * susp_results_stress, which touch no device memory: the centres,
+ * velocities and spins (any may be NULL) and the time-averaged stress of
+ * one kind with the histogram, exactly as susp_get_particles and
+ * susp_stress give them at that point of the stream.  Both return the
+ * block's device status (SUSP_EOVERLAP, SUSP_EUNSTABLE, ...).  Errors:
+ * SUSP_EINVAL (NULL argument, bytes below susp_results_bytes, async not 0 or
+ * 1), SUSP_ECUDA. */
+size_t susp_results_bytes(susp *h);
+susp_status susp_read_results(susp *h, void *host_buf, size_t bytes, int async);
+susp_status susp_results_particles(susp *h, const void *buf, double *pos, double *vel, double *omega);
+susp_status susp_results_stress(susp *h, const void *buf, susp_stress_kind kind, double out[9], double *hist,
+                                int nbins);
+
 /* Populations to / from FP64 host arrays [19*nx*ny*nz] in the layout above.
  * Set converts to the storage precision and recomputes the link forces.
  * Both synchronise. */

@@ -57,7 +57,7 @@ struct Layout {
   size_t Ro, m32a, m32b, pd, pk;
   size_t cstart, ccnt, cids, pcell, pj, ph, pcnt, pconst, drv;
   size_t hc0, hp0, hv0, hc1, hp1, hv1;
-  size_t sums, hist, counters, proto, err, tmap, plbn;
+  size_t sums, hist, counters, proto, err, tmap, plbn, res;
   size_t total;
   int ncx, ncy, ncz, brute, ncells;
   double csx, csy, csz, hrange;
@@ -99,6 +99,16 @@ double hrange_of(const susp_params* p) {
   if (p->F0 > 0.0 && 10.0 * p->debye > h) h = 10.0 * p->debye;
   return h;
 }
+
+// The block of susp_read_results: the error word (padded to 8 bytes), the
+// two sample counters, the NSUMS stress sums, the 3 nbins histogram, then
+// the centres, velocities and spins (3 n doubles each).
+static size_t results_bytes(int n, int nbins) {
+  return 8 + 16 + 8 * (size_t)NSUMS + 24 * (size_t)nbins + 72 * (size_t)n;
+}
+static const size_t RES_CNT = 8, RES_SUMS = 24;
+static size_t res_hist() { return RES_SUMS + 8 * (size_t)NSUMS; }
+static size_t res_parts(int nbins) { return res_hist() + 24 * (size_t)nbins; }
 
 void make_layout(const susp_params* p, Layout& L) {
   const long long nc = (long long)p->nx * p->ny * p->nz;
@@ -149,6 +159,7 @@ void make_layout(const susp_params* p, Layout& L) {
   L.err = take(4);
   L.tmap = take(384);   // three 128-byte tensor maps (256-byte aligned, as they must be 64)
   L.plbn = take(12 * csize(prec) * nn);   // the next step's copy (overlapped step)
+  L.res = take(results_bytes(n, nb));     // staging block of susp_read_results
   L.total = o;
 }
 
@@ -181,6 +192,26 @@ __global__ void __launch_bounds__(64) k_finalize(Batch B, int plb16) {
     for (int k = threadIdx.x; k < plb16 * v.n; k += blockDim.x) dst[k] = src[k];
   }
   finalize_box(v);
+}
+
+// The results block of one box (see results_bytes), gathered in 8-byte words.
+__global__ void k_gather_results(View v, unsigned long long* __restrict__ dst) {
+  const long long nsw = NSUMS, nhw = 3LL * v.nbins, npw = 3LL * v.n;
+  const long long total = 3 + nsw + nhw + 3 * npw;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    unsigned long long w;
+    if (k == 0) w = (unsigned long long)(unsigned)*v.err;
+    else if (k < 3) w = v.counters[k - 1];
+    else if (k < 3 + nsw) w = __double_as_longlong(v.sums[k - 3]);
+    else if (k < 3 + nsw + nhw) w = __double_as_longlong(v.hist[k - 3 - nsw]);
+    else {
+      const long long j = k - 3 - nsw - nhw;
+      const double* src = j < npw ? v.R : (j < 2 * npw ? v.U : v.W);
+      w = __double_as_longlong(src[j % npw]);
+    }
+    dst[k] = w;
+  }
 }
 
 // Error words of the boxes of a batch, in batch order.
@@ -882,19 +913,11 @@ susp_status susp_stress_reset(susp* h) {
   return cuda_check(cudaGetLastError(), "stress reset");
 }
 
-susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* hist, int nbins) {
-  if (!h || !out) return fail(SUSP_EINVAL, "NULL argument");
-  susp_status st = device_status(h);
-  if (st) return st;
-  double sums[NSUMS];
-  unsigned long long cnt[2];
-  std::vector<double> hs(3 * h->v.nbins);
-  cudaMemcpy(sums, h->v.sums, sizeof sums, cudaMemcpyDeviceToHost);
-  cudaMemcpy(cnt, h->v.counters, sizeof cnt, cudaMemcpyDeviceToHost);
-  cudaMemcpy(hs.data(), h->v.hist, 8 * hs.size(), cudaMemcpyDeviceToHost);
-  st = cuda_check(cudaGetLastError(), "read stress");
-  if (st) return st;
-  if (hist && nbins == h->v.nbins) memcpy(hist, hs.data(), 8 * hs.size());
+// Time-averaged stresses (and the histogram) from the stress sums, sample
+// counters and histogram read from the device (host arithmetic only).
+static susp_status stress_from(const susp* h, const double* sums, const unsigned long long* cnt,
+                               const double* hs, susp_stress_kind kind, double out[9], double* hist, int nbins) {
+  if (hist && nbins == h->v.nbins) memcpy(hist, hs, 8 * 3 * (size_t)h->v.nbins);
   for (int k = 0; k < 9; ++k) out[k] = 0.0;
   if (cnt[0] == 0) return SUSP_OK;
   const double V = (double)h->v.nx * h->v.ny * h->v.nz;
@@ -944,6 +967,71 @@ susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* h
     default: return fail(SUSP_EINVAL, "bad stress kind");
   }
   return SUSP_OK;
+}
+
+susp_status susp_stress(susp* h, susp_stress_kind kind, double out[9], double* hist, int nbins) {
+  if (!h || !out) return fail(SUSP_EINVAL, "NULL argument");
+  susp_status st = device_status(h);
+  if (st) return st;
+  double sums[NSUMS];
+  unsigned long long cnt[2];
+  std::vector<double> hs(3 * h->v.nbins);
+  cudaMemcpy(sums, h->v.sums, sizeof sums, cudaMemcpyDeviceToHost);
+  cudaMemcpy(cnt, h->v.counters, sizeof cnt, cudaMemcpyDeviceToHost);
+  cudaMemcpy(hs.data(), h->v.hist, 8 * hs.size(), cudaMemcpyDeviceToHost);
+  st = cuda_check(cudaGetLastError(), "read stress");
+  if (st) return st;
+  return stress_from(h, sums, cnt, hs.data(), kind, out, hist, nbins);
+}
+
+size_t susp_results_bytes(susp* h) { return h ? results_bytes(h->v.n, h->v.nbins) : 0; }
+
+susp_status susp_read_results(susp* h, void* host_buf, size_t bytes, int async) {
+  if (!h || !host_buf) return fail(SUSP_EINVAL, "NULL argument");
+  if (async != 0 && async != 1) return fail(SUSP_EINVAL, "async must be 0 or 1");
+  const size_t need = results_bytes(h->v.n, h->v.nbins);
+  if (bytes < need) return fail(SUSP_EINVAL, "results buffer smaller than susp_results_bytes()");
+  cudaStream_t s = stream_of(h);
+  unsigned long long* stage = (unsigned long long*)(h->ws + h->L.res);
+  const int words = (int)(need / 8);
+  k_gather_results<<<(words + 255) / 256, 256, 0, s>>>(h->v, stage);
+  cudaError_t e = cudaMemcpyAsync(host_buf, stage, need, cudaMemcpyDeviceToHost, s);
+  susp_status st = cuda_check(e == cudaSuccess ? cudaGetLastError() : e, "read results");
+  if (st || async) return st;
+  st = cuda_check(cudaStreamSynchronize(s), "read results");
+  if (st) return st;
+  int err = 0;
+  memcpy(&err, host_buf, sizeof(int));
+  return err_status(err);
+}
+
+susp_status susp_results_particles(susp* h, const void* buf, double* pos, double* vel, double* omega) {
+  if (!h || !buf) return fail(SUSP_EINVAL, "NULL argument");
+  const char* b = (const char*)buf;
+  int err = 0;
+  memcpy(&err, b, sizeof(int));
+  const size_t n3 = 24 * (size_t)h->v.n, o = res_parts(h->v.nbins);
+  if (pos) memcpy(pos, b + o, n3);
+  if (vel) memcpy(vel, b + o + n3, n3);
+  if (omega) memcpy(omega, b + o + 2 * n3, n3);
+  return err_status(err);
+}
+
+susp_status susp_results_stress(susp* h, const void* buf, susp_stress_kind kind, double out[9], double* hist,
+                                int nbins) {
+  if (!h || !buf || !out) return fail(SUSP_EINVAL, "NULL argument");
+  const char* b = (const char*)buf;
+  int err = 0;
+  memcpy(&err, b, sizeof(int));
+  susp_status st = err_status(err);
+  if (st) return st;
+  double sums[NSUMS];
+  unsigned long long cnt[2];
+  std::vector<double> hs(3 * h->v.nbins);
+  memcpy(cnt, b + RES_CNT, sizeof cnt);
+  memcpy(sums, b + RES_SUMS, sizeof sums);
+  memcpy(hs.data(), b + res_hist(), 8 * hs.size());
+  return stress_from(h, sums, cnt, hs.data(), kind, out, hist, nbins);
 }
 
 susp_status susp_moduli(susp* h, double* Gp, double* Gpp) {

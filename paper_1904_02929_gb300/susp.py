@@ -125,6 +125,14 @@ def library() -> C.CDLL:
         for name in ("susp_set_launch_shape", "susp_batch_set_launch_shape"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+        L.susp_results_bytes.restype = C.c_size_t
+        L.susp_results_bytes.argtypes = [C.c_void_p]
+        L.susp_read_results.restype = C.c_int
+        L.susp_read_results.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        L.susp_results_particles.restype = C.c_int
+        L.susp_results_particles.argtypes = [C.c_void_p, C.c_void_p, _D, _D, _D]
+        L.susp_results_stress.restype = C.c_int
+        L.susp_results_stress.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _D, _D, C.c_int]
         for name in ("susp_set_overlap", "susp_batch_set_overlap"):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = [C.c_void_p, C.c_int]
@@ -207,6 +215,32 @@ def susp_get_particles(h, n: int):
     _check(library().susp_get_particles(h, R.ctypes.data_as(_D), U.ctypes.data_as(_D),
                                         W.ctypes.data_as(_D)), "susp_get_particles")
     return R[:3 * n].reshape(n, 3), U[:3 * n].reshape(n, 3), W[:3 * n].reshape(n, 3)
+
+
+def susp_results_bytes(h) -> int:
+    return int(library().susp_results_bytes(h))
+
+
+def susp_read_results(h, buf_ptr: int, nbytes: int, asynchronous: bool) -> None:
+    """Gather the step's results and copy them to the host buffer at buf_ptr
+    (pinned memory when asynchronous)."""
+    _check(library().susp_read_results(h, C.c_void_p(buf_ptr), int(nbytes), int(bool(asynchronous))),
+           "susp_read_results")
+
+
+def susp_results_particles(h, buf_ptr: int, n: int):
+    R, U, W = np.zeros(3 * max(n, 1)), np.zeros(3 * max(n, 1)), np.zeros(3 * max(n, 1))
+    _check(library().susp_results_particles(h, C.c_void_p(buf_ptr), R.ctypes.data_as(_D), U.ctypes.data_as(_D),
+                                            W.ctypes.data_as(_D)), "susp_results_particles")
+    return R[:3 * n].reshape(n, 3), U[:3 * n].reshape(n, 3), W[:3 * n].reshape(n, 3)
+
+
+def susp_results_stress(h, buf_ptr: int, kind: int, nbins: int):
+    out = np.zeros(9)
+    hist = np.zeros(3 * nbins)
+    _check(library().susp_results_stress(h, C.c_void_p(buf_ptr), int(kind), out.ctypes.data_as(_D),
+                                         hist.ctypes.data_as(_D), int(nbins)), "susp_results_stress")
+    return out.reshape(3, 3), hist.reshape(nbins, 3)
 
 
 def susp_get_hydro(h, n: int):
@@ -549,6 +583,22 @@ class Suspension:
 
     def set_overlap(self, enable: bool) -> None:
         susp_set_overlap(self.h, enable)
+
+    def results_buffer(self):
+        """A pinned host buffer for read_results."""
+        import torch
+        return torch.empty(susp_results_bytes(self.h), dtype=torch.uint8).pin_memory()
+
+    def read_results(self, buf, asynchronous: bool = False) -> None:
+        """Copy the step's results into buf (a results_buffer) with one transfer;
+        asynchronous: only enqueue it on self.stream."""
+        susp_read_results(self.h, buf.data_ptr(), buf.numel(), asynchronous)
+
+    def results_particles(self, buf):
+        return susp_results_particles(self.h, buf.data_ptr(), self.n)
+
+    def results_stress(self, buf, kind=TOTAL):
+        return susp_results_stress(self.h, buf.data_ptr(), kind, self.nbins)
 
     def moduli(self):
         return susp_moduli(self.h)
