@@ -70,11 +70,11 @@ def peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def k1_traffic(workload_name: str, kernel: str):
-    """DRAM bytes per collide-stream launch from the committed ncu summary,
-    valid only for the kernel captured and while its source is unchanged
-    since the capture."""
-    path = os.path.join(ROOT, "profiles", "k_collide_stream_dst96_traffic.txt")
+def k1_traffic(workload_name: str, kernel: str, record: str = "k_collide_stream_dst96_traffic.txt"):
+    """DRAM bytes per collide-stream launch from a committed ncu summary,
+    valid only for the workload and kernel captured and while its source is
+    unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     src = open(os.path.join(ROOT, "paper_1904_02929_gb300", "csrc", "lbm.cu"), "rb").read()
@@ -363,7 +363,9 @@ def batched_leg(ws, steps: int, warmup: int):
         "k_collide_stream_avg_ms": k1,
         "roofline": {"bound": "hbm", "kernel": lb_kernel(tuned, "bf16"), "achieved": alg / (k1 / 1e3) / 1e9,
                      "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
-                     "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+                     "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1,
+                     "traffic": k1_traffic("batch64-bf16", lb_kernel(tuned, "bf16"),
+                                           "k_collide_stream_bf16_batch64_traffic.txt") if len(ws) == 64 else None},
         "launch_shape": tuned,
         "stage_us": {k: round(1e3 * v / max(k1_n, 1), 1) for k, v in stages.items()},
         "gpu_launches_per_step": launches_b, "workspace_bytes": mem_b,

@@ -24,6 +24,9 @@ def test_traffic_record_only_for_its_workload_and_kernel():
     assert t is None or 1e6 < t < 2 * 134479872
     assert bench.k1_traffic("some-other-workload", "k_collide_stream<fp32>") is None
     assert bench.k1_traffic("dst-96^3-phi0.50-N882", "some-other-kernel<fp32>") is None
+    tb = bench.k1_traffic("batch64-bf16", "k_collide_stream<bf16>", "k_collide_stream_bf16_batch64_traffic.txt")
+    assert tb is None or 1e9 < tb < 2 * 2041593168
+    assert bench.k1_traffic("batch64-bf16", "k_collide_stream<fp32>", "k_collide_stream_bf16_batch64_traffic.txt") is None
     assert bench.lb_kernel({"staged": True}, "fp16") == "k_collide_stream_tma<fp16>"
     assert bench.lb_kernel({"staged": False}, "fp32") == "k_collide_stream<fp32>"
 
