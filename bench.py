@@ -547,7 +547,9 @@ def monolayer_leg(steps: int, warmup: int):
             "stage_us": {k: round(1e3 * v / n, 1) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": lb_kernel(tuned, "fp16"), "achieved": alg / (k1 / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": alg / (k1 / 1e3) / 1e9 / peak,
-                         "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1},
+                         "peak_source": kind, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": k1,
+                         "traffic": k1_traffic(w.name, lb_kernel(tuned, "fp16"),
+                                               "k_collide_stream_fp16_monolayer_traffic.txt")},
             "launch_shape": tuned,
             "l2": "not flushed: 560 MB of populations per buffer, above L2"}
 
