@@ -17,6 +17,14 @@ on the time average can be read against it.
 
     python tests/golden/make_long_run.py slow
     python tests/golden/make_long_run.py chaotic
+
+A stored case can be extended with runs perturbed at another scale, without
+running its reference again (the FP64 oracle is deterministic): the spread
+of those runs is stored beside the first as chaos_spread_<eps>.  The FP32
+and 16-bit paths round at ~1e-7 of a value every step, so the chaotic case
+also carries the spread of centres perturbed by 1e-7:
+
+    python tests/golden/make_long_run.py chaotic --extend 1e-7 6
 """
 from __future__ import annotations
 
@@ -88,5 +96,31 @@ def main(case: str) -> None:
     print(path, json.dumps(spread))
 
 
+def extend(case: str, eps: float, seeds: int) -> None:
+    path = os.path.join(HERE, f"long_run_{case}.json")
+    with open(path) as f:
+        doc = json.load(f)
+    c = CASES[case]
+    # seeds beyond those of the first perturbed runs
+    first = 1 + c["seeds"]
+    jobs = [(case, eps, k) for k in range(first, first + seeds)]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(run, jobs)
+    spread = {}
+    for name in KINDS:
+        a = np.array(doc["stress"][name])
+        dev = [np.abs(np.array(r["stress"][name]) - a).max() / np.abs(a).max() for r in res]
+        dxy = [abs(r["stress"][name][0][1] - a[0, 1]) / abs(a[0, 1]) for r in res]
+        spread[name] = {"tensor": max(dev), "xy": max(dxy)}
+    doc[f"chaos_spread_{eps:g}"] = spread
+    doc[f"perturbed_runs_{eps:g}"] = seeds
+    with open(path, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(path, json.dumps(spread))
+
+
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "slow")
+    if len(sys.argv) > 3 and sys.argv[2] == "--extend":
+        extend(sys.argv[1], float(sys.argv[3]), int(sys.argv[4]) if len(sys.argv) > 4 else 6)
+    else:
+        main(sys.argv[1] if len(sys.argv) > 1 else "slow")

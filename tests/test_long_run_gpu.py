@@ -17,8 +17,11 @@ the FP64 runs themselves differ by up to 8 % in the total shear stress, 11 %
 in the contact shear stress and 1 % in the total tensor (a 110-sphere box is
 not averaged to 2 % by strain 10), so there each component is held to the
 larger of 2 % and three times that spread: a GPU run must stay about as
-close to the reference as another FP64 run.  The measured errors are
-printed beside the spread.
+close to the reference as another FP64 run.  The FP32 and 16-bit paths
+round at ~1e-7 of a value in every step, not once at 1e-9, so the chaotic
+case also records the spread of FP64 runs whose centres differ by 1e-7
+(six runs); the spread used is the larger of the two.  The measured
+errors are printed beside the spread.
 """
 import json
 import os
@@ -55,7 +58,9 @@ def test_time_averaged_stress_of_a_long_dense_run(case, prec):
         so = np.array(ref["stress"][name])
         sg, _ = g.stress(kind)
         errs[name] = (np.abs(sg - so).max() / np.abs(so).max(), abs(sg[0, 1] - so[0, 1]) / abs(so[0, 1]))
-    spread = ref["chaos_spread_1e-9"]
+    # the larger spread of the perturbation scales on record
+    scales = [ref[k] for k in ref if k.startswith("chaos_spread_")]
+    spread = {name: {c: max(sc[name][c] for sc in scales) for c in ("tensor", "xy")} for name in scales[0]}
     print(f"{case} {prec}: " + ", ".join(
         f"{k} tensor {e[0]:.2e} xy {e[1]:.2e} (FP64 spread {spread[k]['tensor']:.1e} / {spread[k]['xy']:.1e})"
         for k, e in errs.items()))
