@@ -207,7 +207,16 @@ __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, co
   const T* pl = reinterpret_cast<const T*>(v.plb);
   const T ra = lk ? lk->ra : pl[12 * a + 9], rb = lk ? lk->rb : pl[12 * b + 9];
   const T dist = sqrt(dot3(d, d));
-  const T n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+  // FP32 compute takes its quotients and the lubrication logarithm from the
+  // fast hardware forms (a few units in the last place; the FP64 path keeps
+  // correctly rounded ones)
+  T n[3];
+  if constexpr (sizeof(T) == 4) {
+    const float id = __fdividef(1.0f, dist);
+    n[0] = d[0] * id; n[1] = d[1] * id; n[2] = d[2] * id;
+  } else {
+    n[0] = d[0] / dist; n[1] = d[1] / dist; n[2] = d[2] / dist;
+  }
   for (int c = 0; c < 3; ++c) {
     o.Fa[c] = o.Ta[c] = o.Tb[c] = o.Fc[c] = o.Fr[c] = o.ht[c] = (T)0;
     o.d[c] = d[c];
@@ -233,9 +242,17 @@ __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, co
     const T ftm = sqrt(dot3(ft, ft));
     const T cap = pc.mu * fabs(fn);
     if (ftm >= cap && ftm > (T)0) {
-      for (int c = 0; c < 3; ++c) {
-        ft[c] = cap * ft[c] / ftm;
-        ht[c] = -ft[c] / kt;
+      if constexpr (sizeof(T) == 4) {
+        const float sc = __fdividef(cap, ftm), ikt = __fdividef(1.0f, kt);
+        for (int c = 0; c < 3; ++c) {
+          ft[c] = ft[c] * sc;
+          ht[c] = -ft[c] * ikt;
+        }
+      } else {
+        for (int c = 0; c < 3; ++c) {
+          ft[c] = cap * ft[c] / ftm;
+          ht[c] = -ft[c] / kt;
+        }
       }
     }
     T tq[3];
@@ -265,8 +282,15 @@ __device__ void pair_interact(const View& v, int a, int b, const T d[3], T h, co
     if (!lk) lub_factors<T>(ra, rb, pc, kl);
     const LubK<T>& K = lk ? *lk : kl;
     const T xi = K.sc * hh, dl = K.dl;
-    const T inv = (T)1 / (xi + dl) - K.cinv;
-    const T lg = log(K.xcdl / (xi + dl));
+    T inv, lg;
+    if constexpr (sizeof(T) == 4) {
+      const float ix = __fdividef(1.0f, xi + dl);
+      inv = ix - K.cinv;
+      lg = __logf(K.xcdl * ix);
+    } else {
+      inv = (T)1 / (xi + dl) - K.cinv;
+      lg = log(K.xcdl / (xi + dl));
+    }
     const T XA = K.xa * inv;
     const T YA = K.ya * lg;
     const T YBa = K.yba * lg;
