@@ -913,7 +913,10 @@ __device__ __forceinline__ void finalize_boxes(const Batch& B, cooperative_group
   }
 }
 
-template <typename T>
+// SINGLE: the form for at most one particle per warp (the host launches it
+// only when the grid's warps cover every particle), the other for more;
+// two kernels keep each one's code small.
+template <typename T, bool SINGLE>
 __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_step(Batch B) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
@@ -971,7 +974,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
     }
     grid.sync();
   }
-  if (ntot <= nwarps) {
+  if constexpr (SINGLE) {
     // at most one particle per warp: its per-step constants stay in registers.
     // FP32 compute: the partners' mirrors written by the candidate search
     // above are read from the first sub-step on (one barrier first)
@@ -1088,8 +1091,16 @@ int dem_grid_blocks(int plb_double, int n) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (plb_double) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<double>, 32 * DEM_WARPS, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dem_step<float>, 32 * DEM_WARPS, 0);
+  // both forms must fit: the one launched depends on the grid this returns
+  int p1 = 0, p2 = 0;
+  if (plb_double) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_dem_step<double, true>, 32 * DEM_WARPS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_dem_step<double, false>, 32 * DEM_WARPS, 0);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_dem_step<float, true>, 32 * DEM_WARPS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_dem_step<float, false>, 32 * DEM_WARPS, 0);
+  }
+  per = p1 < p2 ? p1 : p2;
   if (per < 1) per = 1;
   if (sms < 1) sms = 1;
   const int want = (n + DEM_WARPS - 1) / DEM_WARPS;
@@ -1112,7 +1123,8 @@ cudaError_t launch_dem_step(const Batch& B, int nparts, int ncells, int plb_doub
   }
   Batch bb = B;
   void* args[] = {&bb};
-  if (plb_double)
-    return cudaLaunchCooperativeKernel((const void*)k_dem_step<double>, dim3(grid), dim3(32 * DEM_WARPS), args, 0, s);
-  return cudaLaunchCooperativeKernel((const void*)k_dem_step<float>, dim3(grid), dim3(32 * DEM_WARPS), args, 0, s);
+  const bool single = nparts <= grid * DEM_WARPS;   // one particle per warp at most
+  const void* fn = plb_double ? (single ? (const void*)k_dem_step<double, true> : (const void*)k_dem_step<double, false>)
+                              : (single ? (const void*)k_dem_step<float, true> : (const void*)k_dem_step<float, false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(32 * DEM_WARPS), args, 0, s);
 }
