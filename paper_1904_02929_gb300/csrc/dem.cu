@@ -700,7 +700,7 @@ __device__ __forceinline__ T group_sum(T x) {
 template <typename T, int LANES>
 __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool valid, const State& S, T dt,
                                          int sample, bool last, const SpringTable& next,
-                                         StepConst<T>* sc, PairRegs<T>* rg, const LubK<T>* lkw) {
+                                         StepConst<T>* sc, PairRegs<T>* rg, const LubK<T>* lkw, bool fresh) {
   constexpr int NS = PAIR_SLOTS / LANES;   // candidate slots per lane
   const int lane = threadIdx.x & (LANES - 1);
   const int grp_shift = (threadIdx.x & 31) & ~(LANES - 1);   // first lane of the group
@@ -748,9 +748,21 @@ __device__ __forceinline__ void pairs_of(const View& v, int i, int npairs, bool 
       const int k = rg ? rg->k[slot] : (int)v.pk[(long long)i * PAIR_SLOTS + c];
       // both mirrors, 16-byte aligned rows of 12 (d, U, W and pads), all six
       // loads issued together
-      const float4* qa = reinterpret_cast<const float4*>(S.m + 12 * a);
-      const float4* qb = reinterpret_cast<const float4*>(S.m + 12 * b);
-      const float4 da = qa[0], db = qb[0], ua4 = qa[1], ub4 = qb[1], wa4 = qa[2], wb4 = qb[2];
+      float4 da, db, ua4, ub4, wa4, wb4;
+      if (fresh) {
+        // the first sub-step: the mirrors' step-start values (no
+        // displacement, U and Omega of the FP64 state), read from the state
+        // itself rather than from the mirrors the candidate search writes
+        da = db = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        ua4 = make_float4((float)v.U[3 * a], (float)v.U[3 * a + 1], (float)v.U[3 * a + 2], 0.0f);
+        ub4 = make_float4((float)v.U[3 * b], (float)v.U[3 * b + 1], (float)v.U[3 * b + 2], 0.0f);
+        wa4 = make_float4((float)v.W[3 * a], (float)v.W[3 * a + 1], (float)v.W[3 * a + 2], 0.0f);
+        wb4 = make_float4((float)v.W[3 * b], (float)v.W[3 * b + 1], (float)v.W[3 * b + 2], 0.0f);
+      } else {
+        const float4* qa = reinterpret_cast<const float4*>(S.m + 12 * a);
+        const float4* qb = reinterpret_cast<const float4*>(S.m + 12 * b);
+        da = qa[0]; db = qb[0]; ua4 = qa[1]; ub4 = qb[1]; wa4 = qa[2]; wb4 = qb[2];
+      }
       const float ex = db.x - da.x, ey = db.y - da.y, ez = db.z - da.z;
       const float num = D.w + ((2.0f * D.x + ex) * ex + ((2.0f * D.y + ey) * ey + (2.0f * D.z + ez) * ez));
       const float* pl = reinterpret_cast<const float*>(v.plb);
@@ -976,11 +988,10 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
   }
   if constexpr (SINGLE) {
     // at most one particle per warp: its per-step constants stay in registers.
-    // FP32 compute: the partners' mirrors written by the candidate search
-    // above are read from the first sub-step on (one barrier first)
-    if constexpr (sizeof(T) == 4) {
-      if (!any_odd) grid.sync();
-    }
+    // A warp takes the same particle as in the candidate search above, and
+    // the first sub-step reads its partners' step-start values from the
+    // state rather than from the mirrors that search writes, so no barrier
+    // comes between the two.
     const int g = gwarp;
     bool has = false;
     int bx = 0, i = 0, nsub = 0;
@@ -1033,7 +1044,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
         // sub-step s reads A when (nsub - s) is even, so the last write lands in A
         const State& S = ((nsub - sub) & 1) ? toA : toB;
         pairs_of<T, 32>(v, i, my_np, true, S, dt, sub == 0, sub == nsub - 1, nxt, &sc, &rg,
-                        sizeof(T) == 4 ? s_lk[wib] : nullptr);
+                        sizeof(T) == 4 ? s_lk[wib] : nullptr, sub == 0);
       }
       if (sub + 1 < B.max_nsub) grid.sync();
     }
@@ -1063,7 +1074,7 @@ __global__ void __launch_bounds__(32 * DEM_WARPS, sizeof(T) == 4 ? 2 : 1) k_dem_
       const State toB{v.R, v.U, v.W, v.R2, v.U2, v.W2, v.m32[0], v.m32[1], pw};
       const State& S = ((nsub - sub) & 1) ? toA : toB;
       pairs_of<T, 16>(v, i, valid ? v.pcnt[i] : 0, valid, S, (T)v.dt_sub, sub == 0, sub == nsub - 1,
-                      spring_table(v, v.proto->t + 1), nullptr, nullptr, nullptr);
+                      spring_table(v, v.proto->t + 1), nullptr, nullptr, nullptr, false);
     }
     if (sub + 1 < B.max_nsub) grid.sync();
   }
