@@ -187,8 +187,10 @@ __device__ __forceinline__ bool band_push(BandList<TC>& L, long long c, TC dx, T
   return true;
 }
 
-template <int P>
-__global__ void __launch_bounds__(256, P == 0 ? 2 : 3) k_uncover(Batch B) {
+// WIDE: at most 64 registers (a few spilled) so that more blocks share an
+// SM, for launches of many waves (large batches).
+template <int P, bool WIDE>
+__global__ void __launch_bounds__(256, P == 0 ? 2 : (WIDE ? 4 : 3)) k_uncover(Batch B) {
   using TC = typename Store<P>::C;
   using S = Store<P>;
   __shared__ TC red[32 * 6];
@@ -591,11 +593,32 @@ void launch_claim(int prec, const Batch& B, int nparts, cudaStream_t s) {
 // every particle's block be resident at once on the 96^3 box).
 void launch_node_update(int prec, const Batch& B, int nparts, cudaStream_t s) {
   if (nparts == 0) return;
+  // the 64-register uncover form beyond eight waves of six blocks per SM
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  const bool wide = nparts > 8 * 6 * sms;
   switch (prec) {
-    case 0: k_uncover<0><<<nparts, 128, 0, s>>>(B); k_cover<0><<<nparts, 128, 0, s>>>(B); break;
-    case 1: k_uncover<1><<<nparts, 128, 0, s>>>(B); k_cover<1><<<nparts, 128, 0, s>>>(B); break;
-    case 2: k_uncover<2><<<nparts, 128, 0, s>>>(B); k_cover<2><<<nparts, 128, 0, s>>>(B); break;
-    default: k_uncover<3><<<nparts, 128, 0, s>>>(B); k_cover<3><<<nparts, 128, 0, s>>>(B); break;
+    case 0: k_uncover<0, false><<<nparts, 128, 0, s>>>(B); k_cover<0><<<nparts, 128, 0, s>>>(B); break;
+    case 1:
+      if (wide) k_uncover<1, true><<<nparts, 128, 0, s>>>(B);
+      else k_uncover<1, false><<<nparts, 128, 0, s>>>(B);
+      k_cover<1><<<nparts, 128, 0, s>>>(B);
+      break;
+    case 2:
+      if (wide) k_uncover<2, true><<<nparts, 128, 0, s>>>(B);
+      else k_uncover<2, false><<<nparts, 128, 0, s>>>(B);
+      k_cover<2><<<nparts, 128, 0, s>>>(B);
+      break;
+    default:
+      if (wide) k_uncover<3, true><<<nparts, 128, 0, s>>>(B);
+      else k_uncover<3, false><<<nparts, 128, 0, s>>>(B);
+      k_cover<3><<<nparts, 128, 0, s>>>(B);
+      break;
   }
 }
 
