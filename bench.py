@@ -255,6 +255,19 @@ def cpu_baseline(w, budget_s: float = 15.0, keep=None):
     }
 
 
+def batched_launches(boxes) -> int:
+    """Kernels per batched step for boxes given as (particles, brute-force
+    pair search): the collide-stream, the cell-list build (four kernels, only
+    when a box with particles is too large for the brute-force search), the
+    particle kernel (which ends with the finalisation), the node map (two)
+    and the links; a batch without particles runs the collide-stream and the
+    finalisation only."""
+    if not any(n > 0 for n, _ in boxes):
+        return 2
+    any_cells = any(n > 0 and not brute for n, brute in boxes)
+    return 1 + (4 if any_cells else 0) + 1 + 2 + 1
+
+
 def batched_leg(ws, steps: int, warmup: int):
     """The 64-box sweep (edges 48-96, phi_3 0.45-0.58, mixed constant and
     oscillatory shear): BF16 deviation storage stepped as one batch (one
@@ -305,12 +318,7 @@ def batched_leg(ws, steps: int, warmup: int):
     stages, k1_n = S.susp_batch_profile_stages(batch.b)
     k1_ms = stages["collide_stream"]
     batch.profile(False)
-    # kernels per batched step: collide-stream, the cell-list build (four,
-    # only when a box is too large for the brute-force pair search), the
-    # particle kernel (which ends with the finalisation), node map (two) and
-    # links
-    any_cells = any(g.info().brute_force_pairs == 0 for g in boxes if g.n > 0)
-    launches_b = 1 + (4 if any_cells else 0) + 1 + 2 + 1
+    launches_b = batched_launches([(g.n, g.info().brute_force_pairs) for g in boxes])
     mem_b = sum(g.nbytes for g in boxes)
     batch.close()
     for g in boxes:

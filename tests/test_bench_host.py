@@ -123,3 +123,9 @@ def test_fixed_launch_shape():
         assert f.set == (4, 1, True) and not f.ov and got["staged"] and got["fixed"] and got["us"] is None
     finally:
         bench.LAUNCH_SHAPE = old
+
+
+def test_batched_launch_count():
+    assert bench.batched_launches([(100, 1), (800, 1)]) == 5      # brute-force pair search everywhere
+    assert bench.batched_launches([(100, 1), (5000, 0)]) == 9     # one box builds a cell list
+    assert bench.batched_launches([(0, 1), (0, 1)]) == 2          # fluid only
